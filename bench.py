@@ -1,0 +1,415 @@
+"""Benchmark of the Wedge hot path on one GB300 (or N replicas).
+
+One step = BFS (root 0), CC (HCC on the symmetrised graph), SSSP (root 0,
+weights in [1,255]) and PageRank (20 iterations, d = 0.85) on R-MAT scale 22,
+edge factor 16 (a=0.57, b=c=0.19, seeded, self-loops and duplicates removed),
+uint32 CSC resident in HBM, through the C ABI with default options (fullness
+threshold 1% / 20%, 256 / 128 edges per Wedge bit).
+
+`value` is whole-job GTEPS over the step: traversed edges of every run
+(BFS, SSSP: sum of out-degrees of reached vertices; CC: |E_sym|; PR: 20*|E|)
+divided by the step time.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SCALE, EF = 22, 16
+PR_ITERS, DAMPING = 20, 0.85
+WMAX = 255
+METRIC = "GTEPS (BFS+CC+SSSP+PR) on R-MAT s22 ef16, Wedge pull vs dense pull, % of HBM roofline"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def make_inputs(scale=SCALE):
+    import graphgen as gg
+    g = gg.rmat(scale, EF).with_weights(WMAX)
+    s = gg.symmetrize(gg.Graph(g.V, g.offsets, g.src))
+    return g, s
+
+
+def credited_edges(outdeg, reached_mask):
+    return int(outdeg[reached_mask].sum())
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, x in enumerate(r[2]) if x.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# Reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    g, s = make_inputs(args.scale)
+    od = oracle.outdeg(g)
+    oracle.build()
+
+    def step():
+        t0 = time.perf_counter()
+        lvl = oracle.bfs_push(g, 0)
+        lab = oracle.cc_union_find(s)
+        dist = oracle.sssp_dijkstra(g, 0)
+        pr = oracle.pr_pull(g, DAMPING, args.ref_pr_iters)
+        t = time.perf_counter() - t0
+        edges = (credited_edges(od, lvl != 0xFFFFFFFF) + s.E + credited_edges(od, dist != 0xFFFFFFFF)
+                 + args.ref_pr_iters * g.E)
+        return t, edges, (lvl, lab, dist, pr)
+
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        step()
+    times, edges = [], 0
+    for _ in range(args.steps):
+        t, e, _ = step()
+        times.append(t)
+        edges += e
+    total = sum(times)
+    value = edges / total / 1e9
+    sample = (f"oracle (single-threaded C) on the full workload: push BFS, union-find CC, Dijkstra SSSP, "
+              f"FP64 pull PageRank with {args.ref_pr_iters} iterations; {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+            "data": "synthetic", "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc+sssp+pr"},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# Our arm
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--ref-pr-iters", type=int, default=PR_ITERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_1903_07754_gb300 import wedge
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    from paper_1903_07754_gb300 import build as wbuild
+    wbuild.build()
+    wedge.load()
+
+    g, s = make_inputs(args.scale)
+    od = oracle.outdeg(g)
+    G = wedge.Graph.from_csc(g)
+    S = wedge.Graph.from_csc(s, with_weights=False)
+    V = g.V
+    lvl = torch.empty(V, dtype=torch.int32, device=dev)
+    lab = torch.empty(V, dtype=torch.int32, device=dev)
+    dist_ = torch.empty(V, dtype=torch.int32, device=dev)
+    rank_t = torch.empty(V, dtype=torch.float32, device=dev)
+    o_bfs, o_cc, o_sssp = (wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp"))
+
+    def step(want_stats=False):
+        sb = wedge.wedge_run_bfs(G.handle, 0, lvl, o_bfs, want_stats)
+        sc = wedge.wedge_run_cc(S.handle, lab, o_cc, want_stats)
+        ss = wedge.wedge_run_sssp(G.handle, 0, dist_, o_sssp, want_stats)
+        sp = wedge.wedge_run_pr(G.handle, rank_t, PR_ITERS, DAMPING, None, want_stats)
+        return sb, sc, ss, sp
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # credited edges are fixed by the result (checked once)
+    step()
+    torch.cuda.synchronize()
+    lv = lvl.cpu().numpy().view(np.uint32)
+    dv = dist_.cpu().numpy().view(np.uint32)
+    edges = {"bfs": credited_edges(od, lv != 0xFFFFFFFF), "cc": s.E,
+             "sssp": credited_edges(od, dv != 0xFFFFFFFF), "pr": PR_ITERS * g.E}
+    step_edges = sum(edges.values())
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    launches0 = wedge.wedge_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    launches = wedge.wedge_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms = float(t_local.item())
+    ms_per_step = ms / args.steps
+    value = world * step_edges * args.steps / (ms / 1e3) / 1e9
+
+    # per-app times, Wedge (default options) against dense pull every iteration
+    per_app = {}
+    dense = {a: wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")}
+    for a in dense.values():
+        a.switch_mode = wedge.SWITCH_ALWAYS_DENSE
+
+    def time_fn(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    runs = {
+        "bfs": (lambda o: wedge.wedge_run_bfs(G.handle, 0, lvl, o, False), o_bfs, dense["bfs"]),
+        "cc": (lambda o: wedge.wedge_run_cc(S.handle, lab, o, False), o_cc, dense["cc"]),
+        "sssp": (lambda o: wedge.wedge_run_sssp(G.handle, 0, dist_, o, False), o_sssp, dense["sssp"]),
+    }
+    for name, (fn, ow, odn) in runs.items():
+        t_w = time_fn(lambda: fn(ow))
+        t_d = time_fn(lambda: fn(odn))
+        per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "dense_pull_ms": t_d,
+                         "speedup_vs_dense_pull": t_d / t_w}
+    t_pr = time_fn(lambda: wedge.wedge_run_pr(G.handle, rank_t, PR_ITERS, DAMPING, None, False))
+    per_app["pr"] = {"ms": t_pr, "gteps": edges["pr"] / (t_pr / 1e3) / 1e9}
+    st = step(want_stats=True)
+    for name, sx in zip(("bfs", "cc", "sssp", "pr"), st):
+        per_app[name]["iters"] = sx.iters
+        per_app[name]["sparse_iters"] = sx.sparse_iters
+
+    # roofline of the dominant kernel: the dense pull, measured on the
+    # PageRank pull (20 of them per step) with CUDA events around single
+    # launches through the pull entry point on the same stream
+    roof = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
+
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+            "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp+pr{PR_ITERS}",
+                       "V": V, "E": g.E, "E_sym": s.E, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20)},
+            "per_app": per_app, "roofline": roof, "gpu_launches": int(launches),
+            "clocks": clk.summary()}
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_measure(wedge, torch, g, s, od, edges, args, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, s, od)
+    G.close()
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
+    """Dense CC pull on the symmetric graph from the initial labels (every
+    destination changes), one launch per CUDA-event pair."""
+    V, E = s.V, s.E
+    init = torch.arange(V, dtype=torch.int32, device=dev)
+    vals = torch.empty_like(init)
+    words = (V + 31) // 32
+    nxt = torch.zeros(words, dtype=torch.int32, device=dev)
+    full = torch.zeros(1, dtype=torch.int64, device=dev)
+    nf = torch.zeros(1, dtype=torch.int32, device=dev)
+    times = []
+    for r in range(12):
+        vals.copy_(init)
+        nxt.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wedge.wedge_pull_iterate(S.handle, "cc", vals, 0, None, None, None, 0, nxt, full, nf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    t = float(np.mean(times)) / 1e3
+    nchanged = int(nf.item())
+    # algorithmic bytes of one dense CC pull: offsets 4(V+1), sources 4E, each
+    # label gathered once 4V (V*4 <= L2), destination labels read 4V,
+    # changed labels written 4*changed, next-frontier bitmap V/8
+    alg = 4 * (V + 1) + 4 * E + 4 * V + 4 * V + 4 * nchanged + V / 8
+    peak, kind = peaks()
+    achieved = alg / t / 1e9
+    return {"kernel": "k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "alg_bytes": alg, "ms": t * 1e3}
+
+
+def e2e_measure(wedge, torch, g, s, od, edges, args, dev):
+    """Host buffers through the public API: pinned host CSC -> device, graph
+    creation (edge index build), the four runs, results back to the host."""
+    host = {}
+    for name, arr in (("off", g.offsets), ("src", g.src), ("w", g.w), ("soff", s.offsets), ("ssrc", s.src)):
+        t = torch.from_numpy(np.ascontiguousarray(arr).view(np.int32)).pin_memory()
+        host[name] = t
+    h2d = sum(t.numel() * 4 for t in host.values())
+    outs = {n: torch.empty(g.V, dtype=torch.int32).pin_memory() for n in ("lvl", "lab", "dist")}
+    outs["pr"] = torch.empty(g.V, dtype=torch.float32).pin_memory()
+    d2h = sum(t.numel() * 4 for t in outs.values())
+    stream = torch.cuda.current_stream()
+
+    def one():
+        d = {n: t.to(dev, non_blocking=True) for n, t in host.items()}
+        G = wedge.Graph(wedge.wedge_graph_create(g.V, g.E, d["off"], d["src"], d["w"]), keep=list(d.values()))
+        S = wedge.Graph(wedge.wedge_graph_create(s.V, s.E, d["soff"], d["ssrc"]), keep=list(d.values()))
+        lvl = torch.empty(g.V, dtype=torch.int32, device=dev)
+        lab, dst = torch.empty_like(lvl), torch.empty_like(lvl)
+        pr = torch.empty(g.V, dtype=torch.float32, device=dev)
+        wedge.wedge_run_bfs(G.handle, 0, lvl, None, False)
+        wedge.wedge_run_cc(S.handle, lab, None, False)
+        wedge.wedge_run_sssp(G.handle, 0, dst, None, False)
+        wedge.wedge_run_pr(G.handle, pr, PR_ITERS, DAMPING, None, False)
+        outs["lvl"].copy_(lvl, non_blocking=True)
+        outs["lab"].copy_(lab, non_blocking=True)
+        outs["dist"].copy_(dst, non_blocking=True)
+        outs["pr"].copy_(pr, non_blocking=True)
+        torch.cuda.synchronize()
+        G.close()
+        S.close()
+
+    one()
+    reps = 3
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"value": sum(edges.values()) / (ms / 1e3) / 1e9, "unit": "GTEPS", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "includes": "H2D of both CSCs, two wedge_graph_create (edge index build), 4 runs, D2H of results"}
+
+
+def cpu_baseline(g, s, od):
+    """The oracle as it stands, single-threaded on the host, on a bounded
+    sample of the step: BFS, CC and PageRank (2 of the 20 iterations) on the
+    full graphs; SSSP (Dijkstra) on the full graph."""
+    import oracle
+    t0 = time.perf_counter()
+    lvl = oracle.bfs_push(g, 0)
+    t1 = time.perf_counter()
+    oracle.cc_union_find(s)
+    t2 = time.perf_counter()
+    dist = oracle.sssp_dijkstra(g, 0)
+    t3 = time.perf_counter()
+    oracle.pr_pull(g, DAMPING, 2)
+    t4 = time.perf_counter()
+    edges = credited_edges(od, lvl != 0xFFFFFFFF) + s.E + credited_edges(od, dist != 0xFFFFFFFF) + 2 * g.E
+    secs = t4 - t0
+    return {"value": edges / secs / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": "full-size BFS (push), CC (union-find), SSSP (Dijkstra) and 2 of 20 PageRank "
+                      f"iterations (FP64 pull) on the same graphs; {secs:.1f} s on 1 host core",
+            "seconds": {"bfs": t1 - t0, "cc": t2 - t1, "sssp": t3 - t2, "pr2": t4 - t3},
+            "host_cores_available": os.cpu_count()}
+
+
+if __name__ == "__main__":
+    main()

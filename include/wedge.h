@@ -1,0 +1,227 @@
+/*
+ * wedge.h - C ABI of the GB300 Wedge engine (libwedge.so).
+ *
+ * Wedge (Grossman & Kozyrakis, "A New Frontier for Pull-Based Graph
+ * Processing", arXiv 1903.07754) is a pull-only graph engine.  Each
+ * iteration pulls values along in-edges and produces the traditional
+ * source-oriented vertex frontier (Section 3.2, Requirement 1).  When that
+ * frontier is sparse enough (the fullness threshold, Section 3.4) it is
+ * transformed into the Wedge Frontier: the set of edge groups ("chunks") of
+ * the destination-sorted in-edge array that hold an edge from an active
+ * source (Sections 3.3, 4), and the next iteration pulls only over those
+ * chunks; otherwise it pulls over all edges.
+ *
+ * Conventions for every entry point:
+ *  - Graph layout (Section 2.2): CSC.  offsets[V+1] (uint32) and src[E]
+ *    (uint32): the in-edges of v are src[offsets[v] .. offsets[v+1]) (any
+ *    order within a destination); w[E] (uint32, SSSP only) in the same
+ *    order.  E < 2^32-256.  wedge_graph_create checks offsets and source
+ *    ids on the device and rejects malformed input.
+ *  - A chunk is 32 consecutive CSC positions: chunk c holds positions
+ *    32c .. 32c+31 (the last one may be short).  With coarsening k
+ *    (log2_coarsen, 0..7) one Wedge Frontier bit / list entry b stands for
+ *    the 2^k chunks b*2^k .. b*2^k + 2^k - 1, i.e. 32*2^k edges
+ *    (Section 3.4, "Frontier Precision").  NC = ceil(E/32).
+ *  - Vertex bitmaps are uint32 words, bit (v & 31) of word v >> 5, with
+ *    ceil(V/32) words.
+ *  - Pointers: arguments named d_* may point to device memory of the graph's
+ *    device or, where stated, to host memory.  Device pointers are BORROWED:
+ *    the caller keeps them valid until the stream work that uses them has
+ *    finished (for the CSC arrays given to wedge_graph_create: until
+ *    wedge_graph_destroy).  The library OWNS the edge index it builds, the
+ *    per-chunk metadata and all scratch.  src and w device arrays must be
+ *    16-byte aligned.
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    Work is enqueued asynchronously on it unless stated otherwise.  A graph
+ *    object is not thread-safe: calls that use the same graph must be
+ *    ordered (same stream, or synchronised by the caller).
+ *  - Errors: every call returns a wedge_status; on failure wedge_last_error()
+ *    gives a message (per calling thread).  Nothing aborts or exits.
+ *  - Unreached BFS levels and SSSP distances are 0xFFFFFFFF; finite SSSP
+ *    distances saturate at 0xFFFFFFFE.
+ */
+#ifndef WEDGE_H
+#define WEDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WEDGE_OK = 0,
+    WEDGE_ERR_INVALID_ARG = 1,   /* bad pointer, size, id or option */
+    WEDGE_ERR_OUT_OF_MEMORY = 2, /* a device or pinned allocation failed */
+    WEDGE_ERR_CUDA = 3,          /* a CUDA call failed (message has the code) */
+    WEDGE_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    WEDGE_ERR_NOT_SUPPORTED = 5, /* feature unavailable in this build/device */
+    WEDGE_ERR_MAX_ITERS = 6      /* the frontier was still non-empty at max_iters */
+} wedge_status;
+
+typedef struct wedge_graph* wedge_graph_t; /* opaque, library-owned */
+typedef void* wedge_stream_t;              /* cudaStream_t */
+
+typedef enum { WEDGE_BFS = 0, WEDGE_CC = 1, WEDGE_SSSP = 2, WEDGE_PR = 3 } wedge_app;
+
+/* How the next iteration is chosen after each pull (Section 3.4):
+ *  THRESHOLD: Wedge Frontier iff fullness * 10^4 < tau_bp * E, where
+ *             fullness = sum of out-degrees of the produced frontier
+ *             (Section 5.2, "Frontier Fullness Threshold").
+ *  LEARNED:   a small MLP cost model picks dense or sparse-with-k; falls back
+ *             to THRESHOLD when no model is loaded.
+ *  ALWAYS_DENSE / ALWAYS_SPARSE: never / always transform. */
+typedef enum {
+    WEDGE_SWITCH_THRESHOLD = 0,
+    WEDGE_SWITCH_LEARNED = 1,
+    WEDGE_SWITCH_ALWAYS_DENSE = 2,
+    WEDGE_SWITCH_ALWAYS_SPARSE = 3
+} wedge_switch;
+
+typedef struct {
+    uint32_t tau_bp;       /* fullness threshold in basis points of E (100 = 1%) */
+    uint32_t log2_coarsen; /* k: one Wedge bit per 32 << k edges, 0..7 */
+    uint32_t switch_mode;  /* wedge_switch */
+    uint32_t max_iters;    /* 0 = default (2^20) */
+    uint32_t trace;        /* nonzero: keep per-iteration records for wedge_get_trace */
+    uint32_t reserved[3];  /* must be zero */
+} wedge_opts;
+
+/* Defaults from the paper's tuned settings (Section 5, "Experiments"):
+ * BFS tau = 1% with 8 vectors per bit, CC/SSSP tau = 20% with 4 vectors per
+ * bit.  Chunk-size equivalents used here: BFS k = 3 (256 edges), CC/SSSP
+ * k = 2 (128 edges). */
+void wedge_default_opts(wedge_app app, wedge_opts* out);
+
+typedef struct {
+    uint32_t iters;           /* pull iterations executed */
+    uint32_t sparse_iters;    /* of which pulled over a Wedge Frontier */
+    uint64_t edges_pulled;    /* CSC positions loaded by the pulls */
+    uint64_t chunks_listed;   /* Wedge Frontier entries over the run */
+    double device_ms;         /* stream time of the run (CUDA events) */
+} wedge_stats;
+
+/* One record per iteration t of the last run (when opts.trace was set). */
+typedef struct {
+    uint64_t fullness;  /* sum of out-degrees of the frontier F_t pulled at t */
+    uint32_t nfront;    /* |F_t| */
+    uint32_t mode;      /* 0 = dense pull, 1 = pull over the Wedge Frontier */
+    uint32_t log2_coarsen;
+    uint32_t nchunks;   /* Wedge Frontier entries pulled at t (mode 1) */
+    uint32_t rowsum;    /* sum over F_t of edge-index row lengths (chunks at k=0) */
+    uint32_t npieces;   /* work pieces handed to the transformation */
+    uint64_t t_pull_ns; /* device time of the pull (globaltimer), 0 if unknown */
+    uint64_t t_xform_ns;/* device time of the transformation feeding t */
+} wedge_iter_record;
+
+/* Builds a graph object on the current CUDA device.
+ *  V >= 1 vertices, E >= 0 edges; d_offsets (V+1), d_src (E) and d_w (E, or
+ *  NULL when the graph has no weights) in CSC layout (see above).  They may
+ *  be host or device pointers; host arrays are copied into library-owned
+ *  device memory, device arrays are borrowed.
+ *  d_eidx_off / d_eidx: the edge index of Sections 3.3 and 4 (a CSR keyed by
+ *  source whose row u lists, once each, the chunks holding u's out-edges,
+ *  in any order), or both NULL to have the library build it on the device.
+ *  A caller's index is checked for non-decreasing offsets and entries
+ *  < NC; rows that list the wrong chunks give wrong results, not faults.
+ *  chunk_edges must be 32.
+ *  Synchronises `stream` before returning.  Errors: INVALID_ARG (sizes,
+ *  NULL arrays, unaligned device src/w, chunk_edges != 32), OUT_OF_MEMORY,
+ *  CUDA. */
+wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offsets,
+                                const uint32_t* d_src, const uint32_t* d_w,
+                                const uint32_t* d_eidx_off, const uint32_t* d_eidx,
+                                uint32_t chunk_edges, wedge_stream_t stream, wedge_graph_t* out);
+
+/* Frees everything the library owns for g (waits for the device first). */
+wedge_status wedge_graph_destroy(wedge_graph_t g);
+
+typedef struct {
+    uint32_t V;
+    uint32_t nz_dst;      /* vertices with in-degree > 0 */
+    uint64_t E;
+    uint64_t nchunks;     /* NC = ceil(E/32) */
+    uint64_t eidx_len;    /* edge-index entries */
+    uint64_t device_bytes;/* device memory owned by the object */
+    int device;
+} wedge_graph_info;
+
+wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out);
+
+/* Copies the edge index (eidx_off[V+1], eidx[eidx_len]) into device
+ * buffers provided by the caller. */
+wedge_status wedge_graph_copy_edge_index(wedge_graph_t g, uint32_t* d_eidx_off, uint32_t* d_eidx,
+                                         wedge_stream_t stream);
+
+/* The frontier transformation (Sections 3.3, 4): from the vertex frontier
+ * d_vertex_bitmap (ceil(V/32) words, device) to the Wedge Frontier at
+ * coarsening log2_coarsen, written as a list of entries b (each standing for
+ * chunks b*2^k .. b*2^k+2^k-1) into d_chunk_list (device, capacity
+ * ceil(NC / 2^k)) with the count in *d_chunk_count (device).  Entries are
+ * distinct; their order is unspecified.  Errors: INVALID_ARG, CUDA. */
+wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_bitmap,
+                                      uint32_t log2_coarsen, uint32_t* d_chunk_list,
+                                      uint32_t* d_chunk_count, wedge_stream_t stream);
+
+/* One pull iteration of BFS, CC or SSSP (Sections 2.1, 3.2, 5):
+ *  d_values (V, device) is updated in place: BFS levels, CC labels or SSSP
+ *  distances.  iter is the iteration number (BFS gives level iter+1 to newly
+ *  reached vertices).  d_cur_bitmap: the frontier consumed (BFS only; NULL
+ *  otherwise).  d_chunk_list / d_chunk_count: the Wedge Frontier to pull
+ *  over at coarsening log2_coarsen, or d_chunk_list = NULL for a dense pull
+ *  over all edges; entries must be distinct, entries >= ceil(NC/2^k) are
+ *  ignored and the count is clamped to ceil(NC/2^k).  Outputs: bits of the vertices whose value changed are
+ *  ORed into d_next_bitmap (device, ceil(V/32) words; the caller zeroes it),
+ *  *d_fullness (device uint64) = sum of their out-degrees, *d_nfront
+ *  (device) = their number.
+ *  CC and SSSP update values in place with atomic minima, so a value may
+ *  move more than one hop in an iteration (Section 5.2, "Frontier
+ *  Precision"); the fixed point reached is the same.  Errors: INVALID_ARG,
+ *  CUDA. */
+wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_values, uint32_t iter,
+                                const uint32_t* d_cur_bitmap, const uint32_t* d_chunk_list,
+                                const uint32_t* d_chunk_count, uint32_t log2_coarsen,
+                                uint32_t* d_next_bitmap, uint64_t* d_fullness, uint32_t* d_nfront,
+                                wedge_stream_t stream);
+
+/* Whole applications (Section 5, "Applications"), each iterating pull,
+ * fullness decision and transformation on the device until the frontier
+ * is empty.  Outputs may be device or host pointers (host: copied back
+ * before the call returns).  opts may be NULL for wedge_default_opts.
+ * stats (host, may be NULL): when given, the call synchronises the stream
+ * and fills it.  Errors: INVALID_ARG (root >= V, no weights for SSSP),
+ * MAX_ITERS, TIMEOUT, CUDA. */
+wedge_status wedge_run_bfs(wedge_graph_t g, uint32_t root, uint32_t* d_level,
+                           const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+/* CC labels: smallest vertex id of the component; the graph must be
+ * symmetric (every edge present in both directions) for HCC to give
+ * components. */
+wedge_status wedge_run_cc(wedge_graph_t g, uint32_t* d_label, const wedge_opts* opts,
+                          wedge_stats* stats, wedge_stream_t stream);
+wedge_status wedge_run_sssp(wedge_graph_t g, uint32_t root, uint32_t* d_dist,
+                            const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+/* PageRank (named in Section 1; no frontier): pr0 = 1/V and `iters` times
+ * pr'(v) = (1-d)/V + d * (sum_{u->v} pr(u)/outdeg(u) + D/V), D = rank of
+ * vertices with out-degree 0.  FP32 values; in-edge sums are accumulated
+ * exactly in 64-bit fixed point (2^-62 units), so results do not depend
+ * on the schedule. */
+wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float damping,
+                          const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+
+/* Per-iteration records of the last run of g (needs opts.trace).  Copies up
+ * to cap records into host memory, sets *n to the number available.
+ * Synchronises the stream of that run. */
+wedge_status wedge_get_trace(wedge_graph_t g, wedge_iter_record* out, uint32_t cap, uint32_t* n);
+
+/* Number of kernel launches the library has enqueued since load (for
+ * accounting of device work). */
+uint64_t wedge_kernel_launches(void);
+
+const char* wedge_last_error(void);
+const char* wedge_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WEDGE_H */

@@ -1,0 +1,175 @@
+// Internal definitions shared by the translation units of libwedge.so.
+//
+// Device layout of a graph object (all library-owned unless noted):
+//   off[V+1], src[E], w[E]   CSC in-edges (borrowed, or owned copies of host input)
+//   outdeg[V]                out-degree of every vertex
+//   vid[NZ]                  ids of the vertices with in-degree > 0, ascending
+//   cmeta[NC]                per 32-edge chunk c: .x = head mask (bit i set iff
+//                            position 32c+i is the first in-edge of its
+//                            destination), .y = index into vid of the
+//                            destination of position 32c
+//   eidx_off[V+1], eidx[]    edge index (Sections 3.3, 4): row u lists the
+//                            chunks that hold u's out-edges, once each
+//   npieces_max              sum over u of ceil(|row u| / 32)
+// The head mask plus vid let a warp find the destination of each of its
+// edges from the chunk alone, the role the paper gives to Vector-Sparse
+// (Section 2.2): no search in off[] on the hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wedge.h"
+
+#define WEDGE_VERSION_STRING "wedge-gb300 0.1"
+
+namespace wedge {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kSat = 0xFFFFFFFEu;
+constexpr uint32_t kChunk = 32;
+constexpr uint32_t kMaxCoarsen = 7;
+constexpr uint32_t kDefaultMaxIters = 1u << 20;
+constexpr int kPullThreads = 256;
+constexpr int kXformThreads = 256;
+constexpr int kFixedShift = 62;  // PageRank fixed point: 1.0 == 2^62
+
+// Per-iteration record (device).  Slot t describes frontier F_t and pull t.
+struct IterRec {
+    unsigned long long fullness;  // sum outdeg over F_t (written by pull t-1)
+    unsigned int nfront;          // |F_t|
+    unsigned int npieces;         // transformation work pieces for F_t
+    unsigned int nchunks;         // Wedge Frontier entries for pull t
+    unsigned int mode;            // 0 dense, 1 sparse (decided after pull t-1)
+    unsigned int k;               // coarsening used by pull t
+    unsigned int rowsum;          // sum |eidx row| over F_t
+    unsigned long long t_pull0, t_pull1;    // globaltimer stamps of pull t
+    unsigned long long t_xf0, t_xf1;        // and of the transformation for t
+};
+static_assert(sizeof(IterRec) == 64, "IterRec layout");
+
+// Run control block (device).
+struct RunCtl {
+    unsigned int it;          // iteration about to be pulled
+    unsigned int done;        // 1 once the frontier is empty or max_iters hit
+    unsigned int ticket;      // last-block election in the pull
+    unsigned int status;      // kStatus* bits
+    unsigned int max_iters;
+    unsigned int switch_mode; // wedge_switch
+    unsigned int tau_bp;
+    unsigned int k;           // coarsening for sparse iterations
+    unsigned long long E;
+    unsigned long long dangling[2];  // PageRank: fixed-point dangling mass
+};
+constexpr unsigned int kStatusMaxIters = 1u;
+
+}  // namespace wedge
+
+struct wedge_graph {
+    int device = 0;
+    uint32_t V = 0;
+    uint64_t E = 0;
+    uint64_t NC = 0;
+    uint32_t NZ = 0;
+    uint64_t eidx_len = 0;
+    uint64_t npieces_max = 0;
+    const uint32_t* off = nullptr;
+    const uint32_t* src = nullptr;
+    const uint32_t* w = nullptr;
+    // owned
+    uint32_t* off_own = nullptr;
+    uint32_t* src_own = nullptr;
+    uint32_t* w_own = nullptr;
+    uint32_t* outdeg = nullptr;
+    uint32_t* vid = nullptr;
+    uint2* cmeta = nullptr;
+    uint32_t* eidx_off = nullptr;
+    uint32_t* eidx = nullptr;
+    bool eidx_owned = false;
+    bool eidx_off_owned = false;
+    // scratch for runs
+    uint32_t* vals = nullptr;      // V values of the current run
+    uint32_t* bm[2] = {nullptr, nullptr};  // vertex frontier bitmaps
+    uint32_t* wb = nullptr;        // Wedge Frontier bitmap, ceil(NC/32) words
+    uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries
+    uint2* pieces = nullptr;       // transformation work pieces
+    wedge::IterRec* rec = nullptr; // per-iteration records
+    uint32_t rec_cap = 0;
+    wedge::RunCtl* ctl = nullptr;
+    wedge::RunCtl* h_ctl = nullptr;  // pinned mirror
+    // PageRank scratch
+    float* contrib = nullptr;
+    unsigned long long* acc = nullptr;
+    uint32_t* split_bm = nullptr;  // destinations whose in-edges cross a 128-edge tile
+    uint64_t device_bytes = 0;
+    int num_sms = 0;
+    int pull_blocks = 0;
+    int xform_blocks = 0;
+    uint32_t last_iters = 0;
+    bool last_trace = false;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace wedge {
+
+// ---- error handling (api.cu) ----
+wedge_status set_error(wedge_status s, const std::string& msg);
+wedge_status cuda_error(cudaError_t e, const char* what);
+void count_launch(uint64_t n = 1);
+
+#define WEDGE_TRY_CUDA(expr)                                      \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return ::wedge::cuda_error(e_, #expr); \
+    } while (0)
+
+#define WEDGE_TRY(expr)                      \
+    do {                                     \
+        wedge_status s_ = (expr);            \
+        if (s_ != WEDGE_OK) return s_;       \
+    } while (0)
+
+// Allocation helper that records the bytes owned by g.
+wedge_status dev_alloc(wedge_graph* g, void** p, size_t bytes);
+void dev_free(void* p);
+
+// Exclusive scan of n uint32 values into out[0..n] (out[n] = total), on the
+// device, using tmp scratch of scan_tmp_words(n) words.  Totals must fit in
+// 32 bits.
+size_t scan_tmp_words(uint64_t n);
+wedge_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp,
+                                cudaStream_t s);
+
+// Engine (engine.cu)
+wedge_status ensure_run_scratch(wedge_graph* g);
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Kind of memory a pointer refers to, as seen from the graph's device.
+enum class PtrKind { Device, Host, Invalid };
+PtrKind classify(const void* p);
+
+__device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned long long global_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace wedge

@@ -1,0 +1,267 @@
+"""Thin ctypes binding over libwedge.so (include/wedge.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Functions carry the C names; tensors are passed by data
+pointer and the stream is torch's current stream unless one is given.  The
+binding raises if the library cannot be loaded: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwedge.so")
+
+BFS, CC, SSSP, PR = 0, 1, 2, 3
+APP_IDS = {"bfs": BFS, "cc": CC, "sssp": SSSP, "pr": PR}
+SWITCH_THRESHOLD, SWITCH_LEARNED, SWITCH_ALWAYS_DENSE, SWITCH_ALWAYS_SPARSE = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_SUPPORTED",
+          6: "MAX_ITERS"}
+INF = 0xFFFFFFFF
+
+
+class WedgeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wedge {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class wedge_opts(ctypes.Structure):
+    _fields_ = [("tau_bp", ctypes.c_uint32), ("log2_coarsen", ctypes.c_uint32),
+                ("switch_mode", ctypes.c_uint32), ("max_iters", ctypes.c_uint32),
+                ("trace", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class wedge_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_uint32), ("sparse_iters", ctypes.c_uint32),
+                ("edges_pulled", ctypes.c_uint64), ("chunks_listed", ctypes.c_uint64),
+                ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class wedge_iter_record(ctypes.Structure):
+    _fields_ = [("fullness", ctypes.c_uint64), ("nfront", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("log2_coarsen", ctypes.c_uint32), ("nchunks", ctypes.c_uint32), ("rowsum", ctypes.c_uint32),
+                ("npieces", ctypes.c_uint32), ("t_pull_ns", ctypes.c_uint64), ("t_xform_ns", ctypes.c_uint64)]
+
+
+class wedge_graph_info(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_uint32), ("nz_dst", ctypes.c_uint32), ("E", ctypes.c_uint64),
+                ("nchunks", ctypes.c_uint64), ("eidx_len", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("device", ctypes.c_int)]
+
+
+EXPORTS = [
+    "wedge_default_opts", "wedge_graph_create", "wedge_graph_destroy", "wedge_graph_get_info",
+    "wedge_graph_copy_edge_index", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
+    "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr", "wedge_get_trace", "wedge_kernel_launches",
+    "wedge_last_error", "wedge_version",
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libwedge.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "wedge_default_opts": (None, [i32, ctypes.POINTER(wedge_opts)]),
+        "wedge_graph_create": (st, [u32, u64, P, P, P, P, P, u32, P, ctypes.POINTER(P)]),
+        "wedge_graph_destroy": (st, [P]),
+        "wedge_graph_get_info": (st, [P, ctypes.POINTER(wedge_graph_info)]),
+        "wedge_graph_copy_edge_index": (st, [P, P, P, P]),
+        "wedge_frontier_transform": (st, [P, P, u32, P, P, P]),
+        "wedge_pull_iterate": (st, [P, i32, P, u32, P, P, P, u32, P, P, P, P]),
+        "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
+        "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
+        "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
+        "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
+                              ctypes.POINTER(wedge_stats), P]),
+        "wedge_get_trace": (st, [P, ctypes.POINTER(wedge_iter_record), u32, ctypes.POINTER(u32)]),
+        "wedge_kernel_launches": (u64, []),
+        "wedge_last_error": (ctypes.c_char_p, []),
+        "wedge_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise WedgeError(status, load().wedge_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int | None:
+    """Data pointer of a torch tensor or numpy array (None passes NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def wedge_default_opts(app) -> wedge_opts:
+    o = wedge_opts()
+    load().wedge_default_opts(APP_IDS[app] if isinstance(app, str) else int(app), ctypes.byref(o))
+    return o
+
+
+def wedge_graph_create(V, E, offsets, src, w=None, eidx_off=None, eidx=None, chunk_edges=32, stream=None):
+    """Returns the opaque graph handle (int).  Arrays may live on the host
+    (numpy) or the device (torch CUDA tensors, borrowed: keep them alive)."""
+    h = ctypes.c_void_p()
+    _check(load().wedge_graph_create(int(V), int(E), _ptr(offsets), _ptr(src), _ptr(w), _ptr(eidx_off),
+                                     _ptr(eidx), int(chunk_edges), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def wedge_graph_destroy(handle):
+    _check(load().wedge_graph_destroy(handle))
+
+
+def wedge_graph_get_info(handle) -> dict:
+    info = wedge_graph_info()
+    _check(load().wedge_graph_get_info(handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def wedge_graph_copy_edge_index(handle, eidx_off, eidx, stream=None):
+    _check(load().wedge_graph_copy_edge_index(handle, _ptr(eidx_off), _ptr(eidx), _stream(stream)))
+
+
+def wedge_frontier_transform(handle, vertex_bitmap, log2_coarsen, chunk_list, chunk_count, stream=None):
+    _check(load().wedge_frontier_transform(handle, _ptr(vertex_bitmap), int(log2_coarsen), _ptr(chunk_list),
+                                           _ptr(chunk_count), _stream(stream)))
+
+
+def wedge_pull_iterate(handle, app, values, it, cur_bitmap, chunk_list, chunk_count, log2_coarsen, next_bitmap,
+                       fullness, nfront, stream=None):
+    a = APP_IDS[app] if isinstance(app, str) else int(app)
+    _check(load().wedge_pull_iterate(handle, a, _ptr(values), int(it), _ptr(cur_bitmap), _ptr(chunk_list),
+                                     _ptr(chunk_count), int(log2_coarsen), _ptr(next_bitmap), _ptr(fullness),
+                                     _ptr(nfront), _stream(stream)))
+
+
+def _opts(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def wedge_run_bfs(handle, root, level, opts=None, want_stats=True, stream=None):
+    st = wedge_stats()
+    _check(load().wedge_run_bfs(handle, int(root), _ptr(level), _opts(opts),
+                                ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_run_cc(handle, label, opts=None, want_stats=True, stream=None):
+    st = wedge_stats()
+    _check(load().wedge_run_cc(handle, _ptr(label), _opts(opts), ctypes.byref(st) if want_stats else None,
+                               _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_run_sssp(handle, root, dist, opts=None, want_stats=True, stream=None):
+    st = wedge_stats()
+    _check(load().wedge_run_sssp(handle, int(root), _ptr(dist), _opts(opts),
+                                 ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_run_pr(handle, rank, iters=20, damping=0.85, opts=None, want_stats=True, stream=None):
+    st = wedge_stats()
+    _check(load().wedge_run_pr(handle, _ptr(rank), int(iters), float(damping), _opts(opts),
+                               ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_get_trace(handle, cap=1 << 16):
+    buf = (wedge_iter_record * cap)()
+    n = ctypes.c_uint32()
+    _check(load().wedge_get_trace(handle, buf, cap, ctypes.byref(n)))
+    return [{f: getattr(buf[i], f) for f, _ in wedge_iter_record._fields_} for i in range(min(n.value, cap))]
+
+
+def wedge_kernel_launches() -> int:
+    return int(load().wedge_kernel_launches())
+
+
+def wedge_last_error() -> str:
+    return load().wedge_last_error().decode(errors="replace")
+
+
+def wedge_version() -> str:
+    return load().wedge_version().decode()
+
+
+class Graph:
+    """Owns a graph handle plus the device tensors it borrows.
+
+    ``Graph.from_csc(g)`` uploads any object with V, offsets, src and
+    optional w (numpy, CSC order) as torch CUDA tensors."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = handle
+        self._keep = list(keep)
+        self.info = wedge_graph_get_info(handle)
+
+    @classmethod
+    def from_csc(cls, g, device="cuda", with_weights=True, stream=None):
+        import torch
+        off = torch.from_numpy(np.ascontiguousarray(g.offsets, dtype=np.uint32).view(np.int32)).to(device)
+        src = torch.from_numpy(np.ascontiguousarray(g.src, dtype=np.uint32).view(np.int32)).to(device)
+        w = None
+        if with_weights and getattr(g, "w", None) is not None:
+            w = torch.from_numpy(np.ascontiguousarray(g.w, dtype=np.uint32).view(np.int32)).to(device)
+        h = wedge_graph_create(g.V, src.numel(), off, src, w, stream=stream)
+        return cls(h, keep=(off, src, w))
+
+    @property
+    def V(self):
+        return self.info["V"]
+
+    @property
+    def E(self):
+        return self.info["E"]
+
+    def close(self):
+        if self.handle:
+            wedge_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

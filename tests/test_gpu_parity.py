@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle.
+
+Integer results (levels, labels, distances, chunk lists, edge index,
+fullness, frontier sizes) must match bit for bit; PageRank (FP32) must be
+within an L1 distance of 1e-6 of the FP64 oracle.  Graphs span many 128-edge
+tiles and have ragged tails (E not a multiple of 4 or 32)."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from _gpu import INF, bitmap, dev_u32, empty_u32, graph, opts, u32, unpack, zeros_u32
+from paper_1903_07754_gb300 import wedge
+
+pytestmark = pytest.mark.gpu
+
+PR_L1_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def rmat():
+    """R-MAT scale 16, edge factor 16 (a=0.57, b=c=0.19) with weights in [1,255]."""
+    return gg.rmat(16, 16).with_weights(255)
+
+
+@pytest.fixture(scope="module")
+def rmat_dev(rmat):
+    G = graph(rmat)
+    yield G
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def sym():
+    return gg.symmetrize(gg.rmat(15, 8))
+
+
+@pytest.fixture(scope="module")
+def sym_dev(sym):
+    G = graph(sym, with_weights=False)
+    yield G
+    G.close()
+
+
+def _run(G, app, root=0, o=None):
+    out = empty_u32(G.V)
+    if app == "bfs":
+        st = wedge.wedge_run_bfs(G.handle, root, out, o)
+    elif app == "cc":
+        st = wedge.wedge_run_cc(G.handle, out, o)
+    else:
+        st = wedge.wedge_run_sssp(G.handle, root, out, o)
+    return u32(out)[: G.V], st
+
+
+def test_edge_index_matches_oracle(rmat, rmat_dev):
+    G = rmat_dev
+    info = G.info
+    eo = empty_u32(G.V + 1)
+    ei = empty_u32(info["eidx_len"])
+    wedge.wedge_graph_copy_edge_index(G.handle, eo, ei)
+    eo_g, ei_g = u32(eo)[: G.V + 1].astype(np.uint64), u32(ei)[: info["eidx_len"]].astype(np.uint64)
+    eo_o, ei_o = oracle.edge_index(rmat, 32)
+    np.testing.assert_array_equal(eo_g, eo_o)
+    rows = np.repeat(np.arange(G.V, dtype=np.uint64), np.diff(eo_g).astype(np.int64))
+    order = np.lexsort((ei_g, rows))  # rows keep any order on the GPU: compare as sets
+    np.testing.assert_array_equal(ei_g[order], ei_o)
+    assert info["nchunks"] == (rmat.E + 31) // 32
+    assert info["nz_dst"] == int((rmat.indeg() > 0).sum())
+
+
+@pytest.mark.parametrize("frac", [0.0001, 0.003, 0.05, 0.6])
+def test_transform_matches_definition(rmat, rmat_dev, frac):
+    G = rmat_dev
+    r = np.array([gg.rand(77, i) for i in range(G.V)], dtype=np.uint64)
+    front = (r % np.uint64(100000)) < np.uint64(int(frac * 100000))
+    front[0] = True
+    bm = dev_u32(bitmap(G.V, front))
+    nc = G.info["nchunks"]
+    for k in (0, 1, 2, 3, 4, 7):
+        cap = (nc + (1 << k) - 1) >> k
+        lst = empty_u32(cap)
+        cnt = zeros_u32(1)
+        wedge.wedge_frontier_transform(G.handle, bm, k, lst, cnt)
+        n = int(u32(cnt)[0])
+        got = u32(lst)[:n].astype(np.uint64)
+        assert np.unique(got).size == n, "entries must be distinct"
+        want = oracle.wedge_groups_scan(rmat, front, 32 << k)
+        np.testing.assert_array_equal(np.sort(got), want)
+
+
+@pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse2", "sparse5", "tau20k1"])
+def test_bfs_matches_oracle(rmat, rmat_dev, mode):
+    want = oracle.bfs_push(rmat, 0)
+    o = {"default": opts("bfs"), "dense": opts("bfs", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0),
+         "sparse2": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=2),
+         "sparse5": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=5),
+         "tau20k1": opts("bfs", tau=2000, k=1)}[mode]
+    got, st = _run(rmat_dev, "bfs", 0, o)
+    np.testing.assert_array_equal(got, want)
+    assert st.iters == int(want[want != INF].max()) + 1
+
+
+@pytest.mark.parametrize("tau,k", [(100, 3), (2000, 0), (500, 2)])
+def test_bfs_trace_matches_oracle(rmat, rmat_dev, tau, k):
+    """BFS is level-synchronous on both sides, so every iteration's frontier
+    size, fullness, decision and Wedge Frontier size must agree."""
+    o = opts("bfs", tau=tau, k=k, trace=1)
+    got, st = _run(rmat_dev, "bfs", 0, o)
+    tr = wedge.wedge_get_trace(rmat_dev.handle)
+    _, ot = oracle.wedge_run("bfs", rmat, 0, oracle.POLICY_THRESHOLD, tau, 32 << k)
+    assert len(tr) == ot.shape[0] == st.iters
+    for t, rec in enumerate(tr):
+        assert rec["nfront"] == ot[t, 0], t
+        assert rec["fullness"] == ot[t, 1], t
+        assert rec["mode"] == ot[t, 2], t
+        if rec["mode"]:
+            assert rec["nchunks"] == ot[t, 3], t
+
+
+@pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse3", "tau50k1"])
+def test_cc_matches_union_find(sym, sym_dev, mode):
+    want = oracle.cc_union_find(sym)
+    o = {"default": opts("cc"), "dense": opts("cc", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("cc", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0),
+         "sparse3": opts("cc", switch=wedge.SWITCH_ALWAYS_SPARSE, k=3),
+         "tau50k1": opts("cc", tau=5000, k=1)}[mode]
+    got, _ = _run(sym_dev, "cc", 0, o)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse4"])
+def test_sssp_matches_dijkstra(rmat, rmat_dev, mode):
+    want = oracle.sssp_dijkstra(rmat, 0)
+    o = {"default": opts("sssp"), "dense": opts("sssp", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("sssp", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0),
+         "sparse4": opts("sssp", switch=wedge.SWITCH_ALWAYS_SPARSE, k=4)}[mode]
+    got, _ = _run(rmat_dev, "sssp", 0, o)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_pagerank_l1(rmat, rmat_dev):
+    want = oracle.pr_pull(rmat, 0.85, 20)
+    rank = torch.empty(rmat.V, dtype=torch.float32, device="cuda")
+    wedge.wedge_run_pr(rmat_dev.handle, rank, 20, 0.85)
+    got = rank.cpu().numpy().astype(np.float64)
+    l1 = np.abs(got - want).sum()
+    assert l1 <= PR_L1_TOL, l1
+    # the exact fixed-point sums make the result independent of the schedule
+    rank2 = torch.empty_like(rank)
+    wedge.wedge_run_pr(rmat_dev.handle, rank2, 20, 0.85)
+    assert torch.equal(rank, rank2)
+
+
+def test_pull_iterate_bfs_step(rmat, rmat_dev):
+    """One BFS iteration from the oracle's level-t state, dense and over the
+    Wedge Frontier, yields exactly the level-(t+1) set."""
+    G = rmat_dev
+    lvl = oracle.bfs_push(rmat, 0)
+    od = oracle.outdeg(rmat)
+    depth = int(lvl[lvl != INF].max())
+    for t in range(depth):
+        state = np.where(lvl <= t, lvl, INF).astype(np.uint32)
+        cur = dev_u32(bitmap(G.V, lvl == t))
+        for sparse in (False, True):
+            vals = dev_u32(state)
+            nxt = zeros_u32((G.V + 31) // 32)
+            full = torch.zeros(1, dtype=torch.int64, device="cuda")
+            nf = zeros_u32(1)
+            lst = cnt = None
+            k = 2
+            if sparse:
+                lst = empty_u32(G.info["nchunks"])
+                cnt = zeros_u32(1)
+                wedge.wedge_frontier_transform(G.handle, cur, k, lst, cnt)
+            wedge.wedge_pull_iterate(G.handle, "bfs", vals, t, cur, lst, cnt, k, nxt, full, nf)
+            want = np.where(lvl <= t + 1, lvl, INF).astype(np.uint32)
+            np.testing.assert_array_equal(u32(vals)[: G.V], want)
+            np.testing.assert_array_equal(unpack(u32(nxt), G.V), lvl == t + 1)
+            assert int(full.item()) == int(od[lvl == t + 1].sum())
+            assert int(u32(nf)[0]) == int((lvl == t + 1).sum())
+
+
+@pytest.mark.parametrize("app", ["cc", "sssp"])
+def test_pull_iterate_min_step_bounds(rmat, sym, rmat_dev, sym_dev, app):
+    """CC/SSSP update in place, so one GPU iteration may move values further
+    than one synchronous step; it can never overshoot the fixed point, and the
+    reported frontier is exactly the set of vertices whose value dropped."""
+    g, G = (sym, sym_dev) if app == "cc" else (rmat, rmat_dev)
+    fixed = oracle.cc_union_find(g) if app == "cc" else oracle.sssp_dijkstra(g, 0)
+    # state after two synchronous iterations from the start
+    state, _ = oracle.wedge_run(app, g, 0, oracle.POLICY_ALWAYS_DENSE, 0, 32, max_iters=2)
+    one, _ = oracle.wedge_run(app, g, 0, oracle.POLICY_ALWAYS_DENSE, 0, 32, max_iters=3)
+    vals = dev_u32(state)
+    nxt = zeros_u32((G.V + 31) // 32)
+    full = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nf = zeros_u32(1)
+    wedge.wedge_pull_iterate(G.handle, app, vals, 2, None, None, None, 0, nxt, full, nf)
+    got = u32(vals)[: G.V]
+    assert np.all(got <= one) and np.all(got >= fixed)
+    changed = got < state
+    np.testing.assert_array_equal(unpack(u32(nxt), G.V), changed)
+    assert int(u32(nf)[0]) == int(changed.sum())
+    assert int(full.item()) == int(oracle.outdeg(g)[changed].sum())
+
+
+def _small_cases():
+    cases = []
+    for i, (V, m) in enumerate([(1, 0), (7, 0), (5, 3), (40, 37), (64, 130), (300, 1201), (1000, 3333),
+                                (4096, 70001)]):
+        cases.append(gg.random_graph(V, m, seed=900 + i))
+    cases.append(gg.grid(64, 0.0))
+    cases.append(gg.grid(48, 0.02))
+    return cases
+
+
+@pytest.mark.parametrize("idx", range(10))
+def test_small_and_degenerate_graphs(idx):
+    g = _small_cases()[idx].with_weights(1000)
+    G = graph(g)
+    try:
+        roots = sorted({0, g.V - 1, g.V // 2})
+        for root in roots:
+            got, _ = _run(G, "bfs", root, opts("bfs"))
+            np.testing.assert_array_equal(got, oracle.bfs_push(g, root))
+            got, _ = _run(G, "sssp", root, opts("sssp", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0))
+            np.testing.assert_array_equal(got, oracle.sssp_dijkstra(g, root))
+        s = gg.symmetrize(g)
+        Gs = graph(s, with_weights=False)
+        got, _ = _run(Gs, "cc", 0, opts("cc"))
+        np.testing.assert_array_equal(got, oracle.cc_union_find(s))
+        Gs.close()
+        rank = torch.empty(g.V, dtype=torch.float32, device="cuda")
+        wedge.wedge_run_pr(G.handle, rank, 20, 0.85)
+        assert np.abs(rank.cpu().numpy() - oracle.pr_pull(g, 0.85, 20)).sum() <= PR_L1_TOL
+    finally:
+        G.close()
+
+
+def test_host_buffers_and_caller_edge_index():
+    """Host (numpy) CSC and outputs go through the same entry points; a
+    caller-supplied edge index gives the same results as the built one."""
+    g = gg.rmat(12, 16).with_weights(255)
+    h = wedge.wedge_graph_create(g.V, g.E, g.offsets, g.src, g.w)
+    try:
+        out = np.empty(g.V, dtype=np.uint32)
+        wedge.wedge_run_bfs(h, 0, out)
+        np.testing.assert_array_equal(out, oracle.bfs_push(g, 0))
+        wedge.wedge_run_sssp(h, 0, out)
+        np.testing.assert_array_equal(out, oracle.sssp_dijkstra(g, 0))
+    finally:
+        wedge.wedge_graph_destroy(h)
+    eo, ei = oracle.edge_index(g, 32)
+    h = wedge.wedge_graph_create(g.V, g.E, g.offsets, g.src, g.w, eo.astype(np.uint32), ei.astype(np.uint32))
+    try:
+        out = np.empty(g.V, dtype=np.uint32)
+        wedge.wedge_run_bfs(h, 0, out, opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=1))
+        np.testing.assert_array_equal(out, oracle.bfs_push(g, 0))
+    finally:
+        wedge.wedge_graph_destroy(h)
+
+
+def test_invalid_arguments_are_rejected():
+    g = gg.rmat(8, 4)
+    bad = g.src.copy()
+    bad[5] = g.V  # out-of-range source id: caught by the device-side check
+    with pytest.raises(wedge.WedgeError) as e:
+        wedge.wedge_graph_create(g.V, g.E, g.offsets, bad)
+    assert e.value.status == 1
+    off = g.offsets.copy()
+    i = int(np.flatnonzero(off[: g.V - 1] > 0)[0])
+    off[i + 1] = off[i] - 1  # decreasing offsets, still 0 .. E at the ends
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_graph_create(g.V, g.E, off, g.src)
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_graph_create(g.V, g.E, g.offsets, g.src, chunk_edges=64)
+    G = graph(g, with_weights=False)
+    try:
+        out = empty_u32(g.V)
+        with pytest.raises(wedge.WedgeError):
+            wedge.wedge_run_bfs(G.handle, g.V, out)
+        with pytest.raises(wedge.WedgeError):
+            wedge.wedge_run_sssp(G.handle, 0, out)  # no weights
+        o = opts("bfs")
+        o.log2_coarsen = 9
+        with pytest.raises(wedge.WedgeError):
+            wedge.wedge_run_bfs(G.handle, 0, out, o)
+        o = opts("bfs", max_iters=1)
+        with pytest.raises(wedge.WedgeError) as e:
+            wedge.wedge_run_bfs(G.handle, 0, out, o)
+        assert e.value.status == 6
+    finally:
+        G.close()
