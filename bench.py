@@ -170,6 +170,8 @@ def main():
     ap.add_argument("--ref-pr-iters", type=int, default=PR_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr"],
+                    help="run only one small case for a profiler (no JSON line)")
     args = ap.parse_args()
 
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -197,6 +199,17 @@ def main():
     od = oracle.outdeg(g)
     G = wedge.Graph.from_csc(g)
     S = wedge.Graph.from_csc(s, with_weights=False)
+    if args.profile_case:
+        if args.profile_case == "cc-dense":
+            print(json.dumps(roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)))
+        else:
+            r = torch.empty(g.V, dtype=torch.float32, device=dev)
+            for _ in range(2):
+                wedge.wedge_run_pr(G.handle, r, 3, DAMPING, None, False)
+            torch.cuda.synchronize()
+        G.close()
+        S.close()
+        return
     V = g.V
     lvl = torch.empty(V, dtype=torch.int32, device=dev)
     lab = torch.empty(V, dtype=torch.int32, device=dev)

@@ -789,7 +789,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     WEDGE_TRY(check_opts(&o));
     if (!out) return set_error(WEDGE_ERR_INVALID_ARG, "output is NULL");
     if (app != kCC && root >= g->V) return set_error(WEDGE_ERR_INVALID_ARG, "root out of range");
-    if (app == kSSSP && !g->w) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
+    if (app == kSSSP && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
     DeviceGuard dg(g->device);
     const uint32_t max_iters = o.max_iters ? (o.max_iters < kDefaultMaxIters ? o.max_iters : kDefaultMaxIters)
                                            : kDefaultMaxIters;
@@ -945,7 +945,7 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     if (app != WEDGE_BFS && app != WEDGE_CC && app != WEDGE_SSSP)
         return set_error(WEDGE_ERR_INVALID_ARG, "app must be BFS, CC or SSSP");
     if (app == WEDGE_BFS && !d_cur_bitmap) return set_error(WEDGE_ERR_INVALID_ARG, "BFS needs the current frontier");
-    if (app == WEDGE_SSSP && !g->w) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
+    if (app == WEDGE_SSSP && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
     if (d_chunk_list && !d_chunk_count) return set_error(WEDGE_ERR_INVALID_ARG, "chunk list without count");
     if (log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
     if (iter + 2 >= g->rec_cap) return set_error(WEDGE_ERR_INVALID_ARG, "iter too large");
