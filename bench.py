@@ -163,14 +163,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--ref-pr-iters", type=int, default=PR_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr"],
+    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced"],
                     help="run only one small case for a profiler (no JSON line)")
     args = ap.parse_args()
 
@@ -202,10 +202,32 @@ def main():
     if args.profile_case:
         if args.profile_case == "cc-dense":
             print(json.dumps(roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)))
-        else:
+        elif args.profile_case == "step":
+            o = [wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")]
+            out = torch.empty(g.V, dtype=torch.int32, device=dev)
+            r = torch.empty(g.V, dtype=torch.float32, device=dev)
+            for _ in range(args.steps):
+                wedge.wedge_run_bfs(G.handle, 0, out, o[0], False)
+                wedge.wedge_run_cc(S.handle, out, o[1], False)
+                wedge.wedge_run_sssp(G.handle, 0, out, o[2], False)
+                wedge.wedge_run_pr(G.handle, r, PR_ITERS, DAMPING, None, False)
+            torch.cuda.synchronize()
+        elif args.profile_case == "pr":
             r = torch.empty(g.V, dtype=torch.float32, device=dev)
             for _ in range(2):
                 wedge.wedge_run_pr(G.handle, r, 3, DAMPING, None, False)
+            torch.cuda.synchronize()
+        else:
+            # the step's frontier runs through the host-polled loop (traced
+            # runs), so that a profiler sees every kernel launch
+            out = torch.empty(g.V, dtype=torch.int32, device=dev)
+            for a, h in (("bfs", G), ("cc", S), ("sssp", G)):
+                o = wedge.wedge_default_opts(a)
+                o.trace = 1
+                fn = {"bfs": lambda: wedge.wedge_run_bfs(h.handle, 0, out, o, False),
+                      "cc": lambda: wedge.wedge_run_cc(h.handle, out, o, False),
+                      "sssp": lambda: wedge.wedge_run_sssp(h.handle, 0, out, o, False)}[a]
+                fn()
             torch.cuda.synchronize()
         G.close()
         S.close()

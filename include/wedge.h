@@ -134,6 +134,25 @@ wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offset
                                 const uint32_t* d_eidx_off, const uint32_t* d_eidx,
                                 uint32_t chunk_edges, wedge_stream_t stream, wedge_graph_t* out);
 
+/* Kernel schedule of a graph's pulls (chosen by an autotuner; results do
+ * not depend on it).
+ *  dense_loader: 0 = each warp streams its 256-edge slice with 16-byte
+ *                loads that bypass L1 (default: L1 stays free for the
+ *                gathered vertex values);
+ *                1 = a producer warp per block stages 2048-edge tiles in
+ *                shared memory with 1D bulk copies (TMA) through a 4-stage
+ *                mbarrier pipeline.
+ *  blocks_per_sm: pull blocks per SM, 0 = as many as fit.
+ * Changing it drops the graph's cached device-loop graphs. */
+typedef struct {
+    uint32_t dense_loader;
+    uint32_t blocks_per_sm;
+    uint32_t reserved[6]; /* must be zero */
+} wedge_tuning;
+
+wedge_status wedge_graph_set_tuning(wedge_graph_t g, const wedge_tuning* t);
+wedge_status wedge_graph_get_tuning(wedge_graph_t g, wedge_tuning* out);
+
 /* Frees everything the library owns for g (waits for the device first). */
 wedge_status wedge_graph_destroy(wedge_graph_t g);
 

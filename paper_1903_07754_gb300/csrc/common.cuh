@@ -32,9 +32,23 @@ constexpr uint32_t kSat = 0xFFFFFFFEu;
 constexpr uint32_t kChunk = 32;
 constexpr uint32_t kMaxCoarsen = 7;
 constexpr uint32_t kDefaultMaxIters = 1u << 20;
-constexpr int kPullThreads = 256;
 constexpr int kXformThreads = 256;
 constexpr int kFixedShift = 62;  // PageRank fixed point: 1.0 == 2^62
+
+// Pull geometry.  A warp processes a slice of kSliceC chunks (kEPL edges per
+// lane); a block has kCW such consumer warps plus one producer warp that
+// streams tiles of kTileC chunks into kStages shared-memory stages with 1D
+// bulk copies (dense pulls).
+constexpr int kEPL = 8;
+constexpr int kSliceE = 32 * kEPL;          // 256 edges
+constexpr int kSliceC = kSliceE / 32;       // 8 chunks
+constexpr int kCW = 8;
+constexpr int kPullThreads = (kCW + 1) * 32;
+constexpr int kTileC = kCW * kSliceC;       // 64 chunks per stage
+constexpr int kTileE = kTileC * 32;         // 2048 edges per stage
+constexpr int kStages = 4;
+constexpr int kMetaPad = 2;                 // chunk metadata entries copied past a tile
+constexpr int kSliceShift = 8;              // log2(kSliceE)
 
 // Per-iteration record (device).  Slot t describes frontier F_t and pull t.
 struct IterRec {
@@ -62,6 +76,8 @@ struct RunCtl {
     unsigned int k;           // coarsening for sparse iterations
     unsigned long long E;
     unsigned long long dangling[2];  // PageRank: fixed-point dangling mass
+    unsigned int loops;              // loop-body executions (bounds the device loop)
+    unsigned int pad_;
 };
 constexpr unsigned int kStatusMaxIters = 1u;
 
@@ -100,12 +116,26 @@ struct wedge_graph {
     wedge::RunCtl* ctl = nullptr;
     wedge::RunCtl* h_ctl = nullptr;  // pinned mirror
     // PageRank scratch
-    float* contrib = nullptr;
+    float* contrib = nullptr;               // pr(u)/outdeg(u)
     unsigned long long* acc = nullptr;
-    uint32_t* split_bm = nullptr;  // destinations whose in-edges cross a 128-edge tile
+    float* rank = nullptr;
+    uint32_t* split_bm = nullptr;  // destinations whose in-edges cross a pull slice boundary
+    uint64_t meta_len = 0;         // cmeta entries allocated (NC rounded up plus padding)
+    // device loop graphs (one per frontier application) and the PageRank graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
+    bool loop_failed = false;
+    cudaGraphExec_t pr_exec = nullptr;
+    uint32_t pr_exec_iters = 0;
+    float pr_exec_damping = -1.f;
+    int pull_smem = 0;
     uint64_t device_bytes = 0;
     int num_sms = 0;
+    size_t smem_per_sm = 0;
     int pull_blocks = 0;
+    int pull_blocks_app[4] = {0, 0, 0, 0};     // direct-load pulls
+    int pull_blocks_tma[4] = {0, 0, 0, 0};     // bulk-copy staged dense pulls
+    wedge_tuning tuning{};
     int xform_blocks = 0;
     uint32_t last_iters = 0;
     bool last_trace = false;

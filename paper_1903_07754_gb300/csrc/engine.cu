@@ -1,17 +1,26 @@
 // The Wedge hot path on the device:
-//   pull (dense over all chunks, or over the listed Wedge Frontier chunks) with
-//   the frontier-fullness epilogue and the fullness decision,
-//   frontier transformation (Sections 3.3, 3.4, 4),
-//   run drivers for BFS, CC, SSSP and PageRank (Section 5).
+//   pull (dense over all chunks, or over the listed Wedge Frontier chunks)
+//   with the frontier-fullness epilogue and the fullness decision
+//   (Sections 3.2, 3.4, Fig. 5), the frontier transformation (Sections 3.3,
+//   4), PageRank, and the run drivers for BFS, CC, SSSP and PageRank
+//   (Section 5).  The iteration loop runs on the device inside a CUDA graph
+//   with a conditional while node.
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace wedge {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+// Direct-load pulls are bound by the latency of their gathers: ask for enough
+// resident blocks per SM to keep 40 warps in flight.
+#ifndef WEDGE_DIRECT_MIN_BLOCKS
+#define WEDGE_DIRECT_MIN_BLOCKS 5
+#endif
+constexpr int kDirectMinBlocks = WEDGE_DIRECT_MIN_BLOCKS;
 enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3 };
 
 // ------------------------------------------------------------------------
@@ -20,74 +29,80 @@ enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3 };
 struct PullParams {
     const uint32_t* src;
     const uint32_t* w;
-    const uint2* cmeta;
+    const uint2* cmeta;          // padded: entries up to a full tile past NC
     const uint32_t* vid;
     const uint32_t* outdeg;
     const uint32_t* eidx_off;
     unsigned long long E;
     unsigned long long NC;
-    uint32_t* vals;             // BFS levels / CC labels / SSSP distances
-    uint32_t* bm[2];            // vertex frontier bitmaps indexed by iteration parity
-    const uint32_t* clist;      // Wedge Frontier list (sparse pulls)
-    uint32_t* wb;               // Wedge Frontier bitmap, consumed words are zeroed
-    uint2* pieces;              // transformation work produced for the next frontier
+    uint32_t* vals;              // BFS levels / CC labels / SSSP distances
+    uint32_t* bm[2];             // vertex frontier bitmaps indexed by iteration parity
+    const uint32_t* clist;       // Wedge Frontier list (sparse pulls)
+    uint32_t* wb;                // Wedge Frontier bitmap: consumed words are zeroed
     IterRec* rec;
     RunCtl* ctl;
-    const float* contrib;       // PageRank
-    unsigned long long* acc;    // PageRank fixed-point in-edge sums
-    unsigned int pr_iter;       // PageRank iteration (dangling slot bookkeeping)
-    int decide;                 // elect a last block that takes the fullness decision
+    const float* contrib;        // PageRank: pr(u)/outdeg(u)
+    unsigned long long* acc;     // PageRank: fixed-point in-edge sums
+    unsigned int pr_iter;
+    int decide;                  // elect a last block that takes the fullness decision
     int trace;
+    int dense_tma;               // dense pulls stage tiles with bulk copies
 };
 
 struct XformParams {
     const uint32_t* eidx;
-    const uint2* pieces;
+    const uint32_t* eidx_off;
+    uint2* pieces;
     uint32_t* wb;
     uint32_t* clist;
     IterRec* rec;
     RunCtl* ctl;
-    uint32_t* bm_clear[2];      // run mode: bitmap cleared per parity (nullptr = none)
+    uint32_t* bm[2];             // run mode: frontier bitmaps by parity
+    const uint32_t* bm_in;       // standalone mode: the caller's frontier bitmap
+    uint32_t V;
     unsigned long long bm_words;
-    unsigned int* count_out;    // standalone mode: count destination (else rec[it].nchunks)
-    int standalone_k;           // >= 0: standalone transformation at this coarsening
+    unsigned int* count_out;     // standalone mode: list count (else rec[it].nchunks)
+    int standalone_k;            // >= 0: standalone transformation at this coarsening
     int trace;
 };
 
 // ------------------------------------------------------------------------
-// Application traits: the per-edge candidate and the combine operator
+// Application traits: per-edge candidate and combine operator
 // ------------------------------------------------------------------------
 template <int APP>
 struct Traits;
-
 template <>
 struct Traits<kBFS> {  // found-a-parent flag, OR
     using T = uint32_t;
     static __device__ __forceinline__ T neutral() { return 0u; }
     static __device__ __forceinline__ T op(T a, T b) { return a | b; }
+    static __device__ __forceinline__ bool keep(T a) { return a != 0u; }
 };
 template <>
 struct Traits<kCC> {  // label, min
     using T = uint32_t;
     static __device__ __forceinline__ T neutral() { return kInf; }
     static __device__ __forceinline__ T op(T a, T b) { return a < b ? a : b; }
+    static __device__ __forceinline__ bool keep(T a) { return a != kInf; }
 };
 template <>
 struct Traits<kSSSP> {  // distance, min
     using T = uint32_t;
     static __device__ __forceinline__ T neutral() { return kInf; }
     static __device__ __forceinline__ T op(T a, T b) { return a < b ? a : b; }
+    static __device__ __forceinline__ bool keep(T a) { return a != kInf; }
 };
 template <>
-struct Traits<kPR> {  // fixed-point contribution, sum
+struct Traits<kPR> {  // fixed-point contribution, sum (every segment is stored)
     using T = unsigned long long;
     static __device__ __forceinline__ T neutral() { return 0ull; }
     static __device__ __forceinline__ T op(T a, T b) { return a + b; }
+    static __device__ __forceinline__ bool keep(T) { return true; }
 };
 
 template <int APP>
-__device__ __forceinline__ typename Traits<APP>::T candidate(const PullParams& P, const uint32_t* cur,
-                                                             uint32_t u, uint32_t w) {
+__device__ __forceinline__ typename Traits<APP>::T candidate(const PullParams& P, const uint32_t* cur, uint32_t u,
+                                                             uint32_t w) {
     if constexpr (APP == kBFS) {
         return (__ldg(cur + (u >> 5)) >> (u & 31)) & 1u;
     } else if constexpr (APP == kCC) {
@@ -98,6 +113,7 @@ __device__ __forceinline__ typename Traits<APP>::T candidate(const PullParams& P
         const unsigned long long s = (unsigned long long)d + w;
         return s > kSat ? kSat : (uint32_t)s;
     } else {
+        // exact 64-bit fixed point of the FP32 contribution (2^-62 units)
         return __float2ull_rn(__ldg(P.contrib + u) * 0x1p62f);
     }
 }
@@ -107,8 +123,8 @@ __device__ __forceinline__ bool set_bit(uint32_t* bm, uint32_t v) {
     return (atomicOr(bm + (v >> 5), bit) & bit) == 0;
 }
 
-// Decision after pull it_next-1 for pull it_next (Section 3.4, Fig. 5):
-// run by one thread once all blocks of the pull have published their sums.
+// The fullness decision (Section 3.4, "Frontier Fullness Threshold"; Fig. 5):
+// run by one thread once every block has published its frontier sums.
 __device__ void decide_next(IterRec* rec, RunCtl* C, unsigned it_next) {
     IterRec* r = rec + it_next;
     const unsigned long long F = __ldcg(&r->fullness);
@@ -128,218 +144,227 @@ __device__ void decide_next(IterRec* rec, RunCtl* C, unsigned it_next) {
     C->it = it_next;
 }
 
-// ------------------------------------------------------------------------
-// Pull kernel (K1 dense / K4 sparse, with the K5 fullness epilogue)
-//
-// Work unit: a 32-edge chunk.  A warp processes a tile of four units; lane L
-// holds edges 4*(L&7) .. 4*(L&7)+3 of unit L>>3 (one 16-byte load each of
-// src, and of w for SSSP).  Dense pulls take units 0..NC-1 in order; sparse
-// pulls expand list entry b into units b*2^k .. b*2^k+2^k-1.
-// Destinations come from the chunk's head mask and first-destination index.
-// A segmented scan over the 128 edges of the tile combines the candidates of
-// each destination.  A segment that starts at its destination's first edge
-// and ends right before the next destination's first edge holds all in-edges
-// of that destination, so its lane is the only writer (plain store);
-// other segments combine with atomics (min, or 64-bit add for PageRank).
-// ------------------------------------------------------------------------
 struct Stats {
     unsigned long long F;
     unsigned int n;
     unsigned int row;
 };
 
+// ------------------------------------------------------------------------
+// One warp slice of the pull (K1/K4 + K5): kSliceC chunks, kEPL = 8 edges
+// per lane (lane L holds edges 8*(L&3) .. +7 of slice chunk L>>2).
+//
+// Destinations come from the chunk's head mask (bit i: position 32c+i is
+// the first in-edge of its destination) and the index of the destination of
+// position 32c.  Each lane combines its edges per destination; a segmented
+// scan across lanes carries partial segments.  Every segment end becomes a
+// record (destination index, combined value) in the warp's shared buffer;
+// the warp then applies the records with all 32 lanes.  A segment that starts
+// at its destination's first edge and ends just before the next
+// destination's first edge holds all in-edges of that destination: its
+// record is applied with a plain read-modify-write, others with atomics.
+// ------------------------------------------------------------------------
 template <int APP>
-__device__ __forceinline__ void pull_tile(const PullParams& P, unsigned it, bool sparse, unsigned k,
-                                          unsigned long long nunits, unsigned long long tile,
-                                          const uint32_t* cur, uint32_t* next, Stats& st) {
+__device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, const uint32_t* cur, uint32_t* next,
+                                              const uint32_t (&sv)[kEPL], const uint32_t (&wv)[kEPL], int nvalid,
+                                              unsigned long long c, uint2 meta, unsigned next_head, bool contig,
+                                              uint32_t* s_kid, typename Traits<APP>::T* s_val, Stats& st) {
     using Tr = Traits<APP>;
     using T = typename Tr::T;
-    const unsigned lane = threadIdx.x & 31, g = lane >> 3, s = lane & 7;
-    const unsigned long long j = tile * 4 + g;
-    bool uvalid = j < nunits;
-    unsigned long long c = 0;
-    if (uvalid) {
-        if (sparse) {
-            const unsigned long long kmask = (1ull << k) - 1;
-            const uint32_t b = P.clist[j >> k];
-            c = ((unsigned long long)b << k) | (j & kmask);
-            uvalid = c < P.NC;
-            // the pull consumes the Wedge Frontier bitmap: zero its word
-            if (uvalid && P.wb && s == 0 && (j & kmask) == 0) P.wb[b >> 5] = 0u;
-        } else {
-            c = j;
-            uvalid = c < P.NC;
-        }
-    }
-    const unsigned long long cprev = __shfl_up_sync(kFull, c, 8);
-    const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 8);
-    const bool contig = g > 0 && pvalid && uvalid && c == cprev + 1;
-
-    const unsigned long long p0 = c * 32 + 4 * s;
-    uint2 meta = make_uint2(0u, 0u);
-    unsigned next_head = 1u;  // head bit of position 32c+32 (1 past the end)
-    int nvalid = 0;
-    if (uvalid) {
-        meta = __ldg(P.cmeta + c);
-        if (s == 7 && c + 1 < P.NC) next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
-        const long long rem = (long long)P.E - (long long)p0;
-        nvalid = rem >= 4 ? 4 : (rem > 0 ? (int)rem : 0);
-    }
-    uint32_t sv[4] = {0, 0, 0, 0}, wv[4] = {0, 0, 0, 0};
-    if (nvalid == 4) {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(P.src + p0));
-        sv[0] = q.x; sv[1] = q.y; sv[2] = q.z; sv[3] = q.w;
-        if constexpr (APP == kSSSP) {
-            const uint4 r = __ldcs(reinterpret_cast<const uint4*>(P.w + p0));
-            wv[0] = r.x; wv[1] = r.y; wv[2] = r.z; wv[3] = r.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (i < nvalid) {
-                sv[i] = P.src[p0 + i];
-                if constexpr (APP == kSSSP) wv[i] = P.w[p0 + i];
-            }
-    }
+    const unsigned lane = threadIdx.x & 31, sub = lane & 3, o = 8 * sub;
     const uint32_t heads = meta.x;
-    T cand[4];
-    bool hd[4], brk[4];
-    uint32_t kid[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const unsigned idx = 4 * s + i;
-        cand[i] = (i < nvalid) ? candidate<APP>(P, cur, sv[i], wv[i]) : Tr::neutral();
-        hd[i] = (heads >> idx) & 1u;
-        brk[i] = hd[i] || (idx == 0 && !contig);
-        kid[i] = meta.y + __popc(heads & ((2u << idx) - 1u) & ~1u);
-    }
-    // in-lane segmented inclusive scan
-    T inc[4];
-    bool ish[4];
+    const uint32_t vmask = (nvalid >= 8) ? 0xFFu : ((1u << nvalid) - 1u);
+    const uint32_t hb = (heads >> o) & vmask;
+    const uint32_t brk = (hb | ((sub == 0 && !contig) ? 1u : 0u)) & vmask;
+
+    T inc[kEPL];
     T run = Tr::neutral();
-    bool rsh = false;
-    int first_brk = 4;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (brk[i]) {
-            run = cand[i];
-            rsh = hd[i];
-            if (first_brk == 4) first_brk = i;
-        } else {
-            run = Tr::op(run, cand[i]);
-        }
+    for (int i = 0; i < kEPL; ++i) {
+        const T cv = (i < nvalid) ? candidate<APP>(P, cur, sv[i], wv[i]) : Tr::neutral();
+        run = ((brk >> i) & 1u) ? cv : Tr::op(run, cv);
         inc[i] = run;
-        ish[i] = rsh;
     }
-    // cross-lane segmented scan of (has break, value, start-is-head)
-    bool f = first_brk < 4;
+    // segmented scan across lanes: (lane has a break, tail value, tail starts at a head)
+    const int last_brk = brk ? 31 - __clz(brk) : -1;
+    bool f = brk != 0 || nvalid == 0;
     T v = run;
-    bool sh = rsh;
+    unsigned sr = brk ? ((hb >> last_brk) & 1u) : 0u;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned f2 = __shfl_up_sync(kFull, (unsigned)f, o);
-        const T v2 = __shfl_up_sync(kFull, v, o);
-        const unsigned sh2 = __shfl_up_sync(kFull, (unsigned)sh, o);
-        if (lane >= (unsigned)o && !f) {
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned f2 = __shfl_up_sync(kFull, (unsigned)f, d);
+        const T v2 = __shfl_up_sync(kFull, v, d);
+        const unsigned sr2 = __shfl_up_sync(kFull, sr, d);
+        if (lane >= (unsigned)d && !f) {
             v = Tr::op(v2, v);
-            sh = sh2;
+            sr = sr2;
             f = f2;
         }
     }
-    const T cv = __shfl_up_sync(kFull, v, 1);
-    const bool csh = __shfl_up_sync(kFull, (unsigned)sh, 1);
-    // what follows the lane's last edge
-    const unsigned mypack = (unsigned)brk[0] | ((unsigned)hd[0] << 1) | ((nvalid > 0) << 2);
-    const unsigned nx = __shfl_down_sync(kFull, mypack, 1);
-    const bool nx_valid = lane < 31 && (nx & 4u);
-    const bool nx_brk = nx & 1u, nx_hd = (nx >> 1) & 1u;
-
-    uint32_t act_v[4];
-    int nact = 0;
+    T carry = __shfl_up_sync(kFull, v, 1);
+    unsigned carry_sr = __shfl_up_sync(kFull, sr, 1);
+    if (lane == 0) {
+        carry = Tr::neutral();
+        carry_sr = 0;
+    }
+    // does this lane's last segment end at its last edge?
+    const unsigned mine = (brk & 1u) | ((nvalid > 0) << 1);
+    const unsigned nx = __shfl_down_sync(kFull, mine, 1);
+    const bool nx_valid = lane < 31 && (nx & 2u);
+    const bool tail_close = nvalid > 0 && (nvalid < kEPL || !nx_valid || (nx & 1u));
+    const bool next_past_end = c * 32 + o + kEPL >= P.E;
+    const bool tail_real = nvalid < kEPL || next_past_end ||
+                           ((sub == 3) ? (next_head != 0) : (((heads >> (o + kEPL)) & 1u) != 0));
+    // record positions: every break b >= 1 closes a segment at b-1; plus the tail
+    uint32_t R = brk >> 1;
+    if (tail_close) R |= 1u << (nvalid - 1);
+    const int first = brk ? __ffs(brk) - 1 : kEPL;
+    T rv[kEPL];
+    uint32_t K = 0, X = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (i >= nvalid) break;
-        bool end, end_head;
-        if (i < 3) {
-            if (i + 1 < nvalid) {
-                end = brk[i + 1];
-                end_head = hd[i + 1];
-            } else {
-                end = true;  // next position is past E
-                end_head = true;
+    for (int e = 0; e < kEPL; ++e) {
+        rv[e] = Tr::neutral();
+        if ((R >> e) & 1u) {
+            const T val = (e < first) ? Tr::op(carry, inc[e]) : inc[e];
+            rv[e] = val;
+            if (Tr::keep(val)) {
+                K |= 1u << e;
+                const uint32_t below = brk & ((2u << e) - 1u);
+                const int lb = below ? 31 - __clz(below) : 0;
+                const unsigned sreal = (e < first) ? carry_sr : ((hb >> lb) & 1u);
+                const unsigned ereal = (e == nvalid - 1 && tail_close) ? (unsigned)tail_real : 1u;
+                X |= (sreal & ereal) << e;
             }
-        } else {
-            end = !nx_valid || nx_brk;
-            end_head = (s == 7) ? (next_head != 0) : (nx_valid ? nx_hd : true);
         }
-        if (!end) continue;
-        const T m = (i < first_brk) ? Tr::op(cv, inc[i]) : inc[i];
-        const bool start_head = (i < first_brk) ? csh : ish[i];
-        const bool excl = start_head && end_head;
-        const uint32_t dv = __ldg(P.vid + kid[i]);
+    }
+    // compact the records of the warp into its shared buffer
+    const unsigned cnt = __popc(K);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (unsigned)d) incl += y;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned slot = incl - cnt;
+#pragma unroll
+    for (int e = 0; e < kEPL; ++e) {
+        if ((K >> e) & 1u) {
+            const uint32_t kid = meta.y + __popc(heads & ((2u << (o + e)) - 1u) & ~1u);
+            s_kid[slot] = kid | (((X >> e) & 1u) << 31);
+            s_val[slot] = rv[e];
+            ++slot;
+        }
+    }
+    __syncwarp();
+    for (unsigned r = lane; r < total; r += 32) {
+        const uint32_t kx = s_kid[r];
+        const T m = s_val[r];
+        const bool excl = kx >> 31;
+        const uint32_t dv = __ldg(P.vid + (kx & 0x7FFFFFFFu));
+        bool act = false;
         if constexpr (APP == kBFS) {
-            if (m && P.vals[dv] == kInf) {
+            if (P.vals[dv] == kInf) {
                 P.vals[dv] = it + 1;
-                if (set_bit(next, dv)) act_v[nact++] = dv;
+                act = set_bit(next, dv);
             }
         } else if constexpr (APP == kPR) {
             if (excl) P.acc[dv] = m;
             else if (m) atomicAdd(P.acc + dv, m);
         } else {
-            if (m != kInf) {
-                bool changed;
-                if (excl) {
-                    const uint32_t old = P.vals[dv];
-                    changed = m < old;
-                    if (changed) P.vals[dv] = m;
-                } else {
-                    changed = m < atomicMin(P.vals + dv, m);
-                }
-                if (changed && set_bit(next, dv)) act_v[nact++] = dv;
+            bool changed;
+            if (excl) {
+                const uint32_t old = P.vals[dv];
+                changed = m < old;
+                if (changed) P.vals[dv] = m;
+            } else {
+                changed = m < atomicMin(P.vals + dv, m);
             }
+            act = changed && set_bit(next, dv);
+        }
+        if (act) {
+            st.F += __ldg(P.outdeg + dv);
+            st.n += 1;
+            st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
         }
     }
-    if constexpr (APP != kPR) {
-        // frontier bookkeeping: fullness, size, edge-index work pieces
-        uint32_t rb[4], rl[4];
-        unsigned np = 0;
-        for (int a = 0; a < nact; ++a) {
-            const uint32_t u = act_v[a];
-            rb[a] = __ldg(P.eidx_off + u);
-            rl[a] = __ldg(P.eidx_off + u + 1) - rb[a];
-            st.F += __ldg(P.outdeg + u);
-            st.n += 1;
-            st.row += rl[a];
-            np += (rl[a] + 31u) >> 5;
-        }
-        unsigned incl = np;
+    __syncwarp();
+}
+
+template <int APP>
+constexpr int pull_records_bytes() {
+    using T = typename Traits<APP>::T;
+    return kCW * kSliceE * (4 + (int)sizeof(T));
+}
+
+template <int APP>
+constexpr int pull_stage_bytes() {
+    return 2 * kStages * 8                                        // mbarriers
+           + kStages * kTileE * 4 * (APP == kSSSP ? 2 : 1)        // src (+ w)
+           + kStages * (kTileC + kMetaPad) * 8;                   // chunk metadata
+}
+
+// Shared memory of a pull: the record buffers, plus the stages when dense
+// pulls use bulk copies.
+template <int APP>
+constexpr int pull_smem_bytes(bool tma) {
+    return pull_records_bytes<APP>() + (tma ? pull_stage_bytes<APP>() : 0);
+}
+
+// A lane's 8 consecutive edges (and weights) straight from global memory.
+template <int APP>
+__device__ __forceinline__ void load_lane_edges(const PullParams& P, unsigned long long e_lane, int nvalid,
+                                                uint32_t (&sv)[kEPL], uint32_t (&wv)[kEPL]) {
+    if (nvalid == kEPL) {
+        const uint4 a = ld_stream(P.src + e_lane);
+        const uint4 b = ld_stream(P.src + e_lane + 4);
+        sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
+        sv[4] = b.x; sv[5] = b.y; sv[6] = b.z; sv[7] = b.w;
+        if constexpr (APP == kSSSP) {
+            const uint4 x = ld_stream(P.w + e_lane);
+            const uint4 y = ld_stream(P.w + e_lane + 4);
+            wv[0] = x.x; wv[1] = x.y; wv[2] = x.z; wv[3] = x.w;
+            wv[4] = y.x; wv[5] = y.y; wv[6] = y.z; wv[7] = y.w;
+        } else {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= (unsigned)o) incl += y;
+            for (int i = 0; i < kEPL; ++i) wv[i] = 0;
         }
-        const unsigned total = __shfl_sync(kFull, incl, 31);
-        if (total) {
-            unsigned base = 0;
-            if (lane == 31) base = atomicAdd(&P.rec[it + 1].npieces, total);
-            base = __shfl_sync(kFull, base, 31) + incl - np;
-            for (int a = 0; a < nact; ++a)
-                for (uint32_t q = 0; q < rl[a]; q += 32) {
-                    const uint32_t len = rl[a] - q < 32u ? rl[a] - q : 32u;
-                    P.pieces[base++] = make_uint2(rb[a] + q, len);
-                }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kEPL; ++i) {
+            sv[i] = i < nvalid ? P.src[e_lane + i] : 0u;
+            wv[i] = 0;
+            if constexpr (APP == kSSSP) wv[i] = i < nvalid ? P.w[e_lane + i] : 0u;
         }
     }
 }
 
-template <int APP>
-__global__ void __launch_bounds__(kPullThreads) k_pull(const PullParams P) {
+template <int APP, bool TMA>
+__global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDirectMinBlocks) k_pull(const PullParams P) {
+    using T = typename Traits<APP>::T;
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_F;
     __shared__ unsigned s_n, s_row, s_last;
     RunCtl* C = P.ctl;
     if (C->done) return;
     const unsigned it = C->it;
-    const IterRec rin = P.rec[it];
+    const unsigned mode = P.rec[it].mode;
+    const unsigned k = P.rec[it].k;
+    const unsigned nchunks = P.rec[it].nchunks;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // layout: [records: values, ids][stages: barriers, src, w, metadata]
+    T* s_val = reinterpret_cast<T*>(smem);
+    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
+    unsigned char* stage = smem + pull_records_bytes<APP>();
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage);
+    uint64_t* empty = full + kStages;
+    uint32_t* s_src = reinterpret_cast<uint32_t*>(stage + 2 * kStages * 8);
+    uint32_t* s_w = s_src + kStages * kTileE;
+    uint2* s_meta = reinterpret_cast<uint2*>(s_w + (APP == kSSSP ? kStages * kTileE : 0));
+    const unsigned wsel = warp < kCW ? warp : 0;
+    uint32_t* my_kid = s_kid + wsel * kSliceE;
+    T* my_val = s_val + wsel * kSliceE;
+    constexpr bool tma = TMA;
     if (threadIdx.x == 0) {
         s_F = 0;
         s_n = 0;
@@ -348,27 +373,188 @@ __global__ void __launch_bounds__(kPullThreads) k_pull(const PullParams P) {
         if constexpr (APP == kPR) {
             if (blockIdx.x == 0) C->dangling[(P.pr_iter + 1) & 1] = 0ull;
         }
+        if (mode == 0 && tma) {
+            for (int s = 0; s < kStages; ++s) {
+                mbar_init(full + s, 1);
+                mbar_init(empty + s, kCW);
+            }
+            fence_mbar_init();
+        }
     }
     __syncthreads();
-    const bool sparse = rin.mode != 0;
-    const unsigned k = rin.k;
-    const unsigned long long nunits = sparse ? ((unsigned long long)rin.nchunks << k) : P.NC;
-    const unsigned long long ntiles = (nunits + 3) / 4;
-    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t* cur = P.bm[it & 1];
     uint32_t* next = P.bm[(it + 1) & 1];
     Stats st{0ull, 0u, 0u};
-    for (unsigned long long t = gw; t < ntiles; t += nw) pull_tile<APP>(P, it, sparse, k, nunits, t, cur, next, st);
+    const unsigned q = lane >> 2, sub = lane & 3;
+
+    if constexpr (!TMA) {
+    if (mode == 0) {
+        // ---- dense, direct: every warp streams 256-edge slices ----
+        // The next slice's edges and chunk metadata are loaded before the
+        // current slice is processed, so the stream overlaps the gathers.
+        const unsigned long long nslices = (P.NC + kSliceC - 1) / kSliceC;
+        const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
+        const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
+        uint32_t sv[kEPL], wv[kEPL];
+        uint2 meta = make_uint2(0u, 0u);
+        unsigned next_head = 1u;
+        int nvalid = 0;
+        unsigned long long c = 0;
+        auto fetch = [&](unsigned long long sl) {
+            c = sl * kSliceC + q;
+            const unsigned long long e_lane = c * 32 + 8 * sub;
+            nvalid = 0;
+            meta = make_uint2(0u, 0u);
+            next_head = 1u;
+            if (sl < nslices && c < P.NC) {
+                const long long left = (long long)P.E - (long long)e_lane;
+                nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
+                meta = __ldg(P.cmeta + c);
+                next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
+            }
+            load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
+        };
+        if (gw < nslices) fetch(gw);
+        for (unsigned long long sl = gw; sl < nslices; sl += nw) {
+            uint32_t cs[kEPL], cw[kEPL];
+#pragma unroll
+            for (int i = 0; i < kEPL; ++i) {
+                cs[i] = sv[i];
+                cw[i] = wv[i];
+            }
+            const uint2 cmeta = meta;
+            const unsigned cnh = next_head;
+            const int cnv = nvalid;
+            const unsigned long long cc = c;
+            fetch(sl + nw);
+            process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st);
+        }
+    }
+    }
+    if (TMA && mode == 0) {
+        // ---- dense, staged: tiles of kTileC chunks streamed by bulk copies ----
+        const unsigned long long ntile = (P.NC + kTileC - 1) / kTileC;
+        if (warp == kCW) {
+            if (lane == 0) {
+                unsigned kk = 0;
+                for (unsigned long long t = blockIdx.x; t < ntile; t += gridDim.x, ++kk) {
+                    const unsigned s = kk % kStages;
+                    if (kk >= kStages && !mbar_wait(empty + s, ((kk / kStages) - 1) & 1u, &C->status)) break;
+                    fence_proxy_async();
+                    const unsigned long long c0 = t * kTileC, e0 = c0 * 32;
+                    const unsigned long long rem = P.E - e0;
+                    const uint32_t ne = rem < (unsigned long long)kTileE ? (uint32_t)rem : (uint32_t)kTileE;
+                    const uint32_t nb = (ne * 4u) & ~15u;
+                    const uint32_t mb = (kTileC + kMetaPad) * 8;
+                    const uint32_t bytes = mb + nb * (APP == kSSSP ? 2u : 1u);
+                    mbar_arrive_expect_tx(full + s, bytes);
+                    bulk_load(s_meta + s * (kTileC + kMetaPad), P.cmeta + c0, mb, full + s);
+                    if (nb) {
+                        bulk_load(s_src + s * kTileE, P.src + e0, nb, full + s);
+                        if constexpr (APP == kSSSP) bulk_load(s_w + s * kTileE, P.w + e0, nb, full + s);
+                    }
+                }
+            }
+            __syncwarp();
+        } else {
+            unsigned kk = 0;
+            for (unsigned long long t = blockIdx.x; t < ntile; t += gridDim.x, ++kk) {
+                const unsigned s = kk % kStages;
+                if (!mbar_wait(full + s, (kk / kStages) & 1u, &C->status)) break;
+                const unsigned long long c0 = t * kTileC, e0 = c0 * 32;
+                const unsigned long long rem = P.E - e0;
+                const uint32_t ne = rem < (unsigned long long)kTileE ? (uint32_t)rem : (uint32_t)kTileE;
+                const uint32_t staged = ne & ~3u;  // edges delivered by the bulk copy
+                const unsigned long long c = c0 + warp * kSliceC + q;
+                const uint32_t local = warp * kSliceE + lane * kEPL;
+                const long long left = (long long)ne - (long long)local;
+                const int nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
+                uint32_t sv[kEPL], wv[kEPL];
+                const uint32_t* ss = s_src + s * kTileE + local;
+                const uint32_t* sw = s_w + s * kTileE + local;
+                if (local + kEPL <= staged) {
+                    const uint4 a = *reinterpret_cast<const uint4*>(ss);
+                    const uint4 b = *reinterpret_cast<const uint4*>(ss + 4);
+                    sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
+                    sv[4] = b.x; sv[5] = b.y; sv[6] = b.z; sv[7] = b.w;
+                    if constexpr (APP == kSSSP) {
+                        const uint4 x = *reinterpret_cast<const uint4*>(sw);
+                        const uint4 y = *reinterpret_cast<const uint4*>(sw + 4);
+                        wv[0] = x.x; wv[1] = x.y; wv[2] = x.z; wv[3] = x.w;
+                        wv[4] = y.x; wv[5] = y.y; wv[6] = y.z; wv[7] = y.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kEPL; ++i) wv[i] = 0;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kEPL; ++i) {
+                        sv[i] = 0;
+                        wv[i] = 0;
+                        if (i < nvalid) {
+                            const uint32_t li = local + i;
+                            sv[i] = li < staged ? ss[i] : P.src[e0 + li];
+                            if constexpr (APP == kSSSP) wv[i] = li < staged ? sw[i] : P.w[e0 + li];
+                        }
+                    }
+                }
+                const uint2* sm = s_meta + s * (kTileC + kMetaPad) + warp * kSliceC + q;
+                const uint2 meta = sm[0];
+                const unsigned next_head = sm[1].x & 1u;
+                // the stage is no longer read past this point
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + s);
+                process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, q > 0, my_kid, my_val,
+                                   st);
+            }
+        }
+    }
+    if (mode != 0 && warp < kCW) {
+        // ---- sparse: slices of 8 listed chunks, loaded directly ----
+        const unsigned long long nunits = (unsigned long long)nchunks << k;
+        const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
+        const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
+        const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
+        const unsigned long long kmask = (1ull << k) - 1;
+        for (unsigned long long sl = gw; sl < nslices; sl += nw) {
+            const unsigned long long j = sl * kSliceC + q;
+            bool uvalid = j < nunits;
+            unsigned long long c = 0;
+            if (uvalid) {
+                const uint32_t b = __ldg(P.clist + (j >> k));
+                c = ((unsigned long long)b << k) | (j & kmask);
+                uvalid = c < P.NC;
+                if (uvalid && P.wb && sub == 0 && (j & kmask) == 0) P.wb[b >> 5] = 0u;  // consume the bit's word
+            }
+            const unsigned long long cprev = __shfl_up_sync(kFull, c, 4);
+            const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 4);
+            const bool contig = q > 0 && pvalid && uvalid && c == cprev + 1;
+            const unsigned long long e_lane = c * 32 + 8 * sub;
+            int nvalid = 0;
+            if (uvalid) {
+                const long long left = (long long)P.E - (long long)e_lane;
+                nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
+            }
+            uint32_t sv[kEPL], wv[kEPL];
+            load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
+            uint2 meta = make_uint2(0u, 0u);
+            unsigned next_head = 1u;
+            if (uvalid) {
+                meta = __ldg(P.cmeta + c);
+                next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
+            }
+            process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st);
+        }
+    }
 
     if constexpr (APP != kPR) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            st.F += __shfl_down_sync(kFull, st.F, o);
-            st.n += __shfl_down_sync(kFull, st.n, o);
-            st.row += __shfl_down_sync(kFull, st.row, o);
+        for (int d = 16; d > 0; d >>= 1) {
+            st.F += __shfl_down_sync(kFull, st.F, d);
+            st.n += __shfl_down_sync(kFull, st.n, d);
+            st.row += __shfl_down_sync(kFull, st.row, d);
         }
-        if ((threadIdx.x & 31) == 0 && st.n) {
+        if (lane == 0 && st.n) {
             atomicAdd(&s_F, st.F);
             atomicAdd(&s_n, st.n);
             atomicAdd(&s_row, st.row);
@@ -384,8 +570,7 @@ __global__ void __launch_bounds__(kPullThreads) k_pull(const PullParams P) {
         s_last = 0;
         if (P.decide) {
             __threadfence();
-            const unsigned ticket = atomicAdd(&C->ticket, 1u);
-            s_last = ticket == gridDim.x - 1;
+            s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
         }
     }
     __syncthreads();
@@ -398,12 +583,86 @@ __global__ void __launch_bounds__(kPullThreads) k_pull(const PullParams P) {
 }
 
 // ------------------------------------------------------------------------
-// Transformation (K2): expand the work pieces of the frontier's edge-index
-// rows, set the Wedge Frontier bits (bit b = list entry b at coarsening k)
-// and append every newly set bit to the Wedge Frontier list.  The bitmap
-// removes duplicates (Section 4); only the first setter of a bit appends it.
+// Transformation (K2), two kernels.
+//   A (k_xform_scan): walk the vertex frontier bitmap; every active vertex's
+//     edge-index row is cut into pieces of at most 32 entries; one
+//     reservation per warp.  In run mode it also clears the bitmap the next
+//     pull fills and the record that pull accumulates into.
+//   B (k_xform_expand): expand the pieces with the warp's lanes balanced over
+//     up to 32 pieces at a time, set the Wedge Frontier bits (bit b = list
+//     entry b at coarsening k) and append every newly set bit to the list:
+//     the bitmap removes duplicates (Section 4).
 // ------------------------------------------------------------------------
-__device__ __forceinline__ void expand_pieces(const XformParams& X, unsigned n, unsigned k, unsigned* count) {
+__global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
+    RunCtl* C = X.ctl;
+    const uint32_t* bm;
+    IterRec* r;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    if (X.standalone_k >= 0) {
+        bm = X.bm_in;
+        r = X.rec;
+    } else {
+        if (C->done) return;
+        const unsigned it = C->it;
+        if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
+        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
+        for (unsigned long long i = tid; i < X.bm_words; i += nth) clr[i] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
+            reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
+        r = X.rec + it;
+        if (r->mode == 0) return;
+        bm = (it & 1) ? X.bm[1] : X.bm[0];
+    }
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long gw = tid >> 5, nw = nth >> 5;
+    const uint32_t V = X.V;
+    for (unsigned long long base = gw * 32; base < X.bm_words; base += nw * 32) {
+        const unsigned long long wi = base + lane;
+        uint32_t word = wi < X.bm_words ? bm[wi] : 0u;
+        if (wi == X.bm_words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
+        unsigned np = 0;
+        for (uint32_t w = word; w; w &= w - 1) {
+            const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
+            np += (__ldg(X.eidx_off + u + 1) - __ldg(X.eidx_off + u) + 31u) >> 5;
+        }
+        unsigned incl = np;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (!total) continue;
+        unsigned slot = 0;
+        if (lane == 31) slot = atomicAdd(&r->npieces, total);
+        slot = __shfl_sync(kFull, slot, 31) + incl - np;
+        for (uint32_t w = word; w; w &= w - 1) {
+            const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
+            const uint32_t rb = __ldg(X.eidx_off + u), rl = __ldg(X.eidx_off + u + 1) - rb;
+            for (uint32_t qq = 0; qq < rl; qq += 32) X.pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
+    RunCtl* C = X.ctl;
+    unsigned n, k;
+    unsigned* count;
+    unsigned it = 0;
+    if (X.standalone_k >= 0) {
+        n = __ldcg(&X.rec[0].npieces);
+        k = (unsigned)X.standalone_k;
+        count = X.count_out;
+    } else {
+        if (C->done) return;
+        it = C->it;
+        const IterRec* r = X.rec + it;
+        if (r->mode == 0) return;
+        n = r->npieces;
+        k = r->k;
+        count = &X.rec[it].nchunks;
+    }
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -413,9 +672,9 @@ __device__ __forceinline__ void expand_pieces(const XformParams& X, unsigned n, 
         const uint2 pc = idx < n ? X.pieces[idx] : make_uint2(0u, 0u);
         unsigned incl = pc.y;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= (unsigned)o) incl += y;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
         const unsigned excl = incl - pc.y;
@@ -434,8 +693,7 @@ __device__ __forceinline__ void expand_pieces(const XformParams& X, unsigned n, 
             bool fresh = false;
             uint32_t b = 0;
             if (act) {
-                const uint32_t chunk = __ldg(X.eidx + st + (e - ex));
-                b = chunk >> k;
+                b = __ldg(X.eidx + st + (e - ex)) >> k;
                 const uint32_t bit = 1u << (b & 31);
                 fresh = (atomicOr(X.wb + (b >> 5), bit) & bit) == 0;
             }
@@ -449,39 +707,16 @@ __device__ __forceinline__ void expand_pieces(const XformParams& X, unsigned n, 
             }
         }
     }
-}
-
-__global__ void __launch_bounds__(kXformThreads) k_transform(const XformParams X) {
-    RunCtl* C = X.ctl;
-    if (X.standalone_k >= 0) {
-        expand_pieces(X, __ldcg(&X.rec[0].npieces), (unsigned)X.standalone_k, X.count_out);
-        return;
-    }
-    if (C->done) return;
-    const unsigned it = C->it;
-    if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
-    // run bookkeeping: the bitmap that pull `it` fills must be clear, and so
-    // must the record that pull `it` accumulates into
-    uint32_t* clr = X.bm_clear[(it + 1) & 1];
-    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
-    if (clr)
-        for (unsigned long long i = tid; i < X.bm_words; i += nth) clr[i] = 0u;
-    if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
-        reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
-    const IterRec r = X.rec[it];
-    if (r.mode != 0) expand_pieces(X, r.npieces, r.k, &X.rec[it].nchunks);
-    if (X.trace) {
+    if (X.trace && X.standalone_k < 0) {
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
     }
 }
 
-// Vertex bitmap -> frontier size, fullness and work pieces (used for the
-// initial frontier and by the standalone transformation entry point).
-__global__ void k_frontier_scan(const uint32_t* __restrict__ bm, uint32_t V, const uint32_t* __restrict__ outdeg,
-                                const uint32_t* __restrict__ eidx_off, uint2* __restrict__ pieces, IterRec* rec,
-                                RunCtl* C, int decide) {
+// Initial frontier: size, fullness and edge-index work (the transformation
+// derives its pieces from the bitmap), then the decision for pull 0.
+__global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, const uint32_t* __restrict__ outdeg,
+                                 const uint32_t* __restrict__ eidx_off, IterRec* rec, RunCtl* C) {
     __shared__ unsigned long long s_F;
     __shared__ unsigned s_n, s_row, s_last;
     if (threadIdx.x == 0) {
@@ -497,25 +732,17 @@ __global__ void k_frontier_scan(const uint32_t* __restrict__ bm, uint32_t V, con
          wi += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t word = bm[wi];
         if (wi == words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const uint32_t u = (uint32_t)(wi * 32 + b);
-            const uint32_t rb = eidx_off[u], rl = eidx_off[u + 1] - rb;
+        for (; word; word &= word - 1) {
+            const uint32_t u = (uint32_t)(wi * 32 + __ffs(word) - 1);
             F += outdeg[u];
             n += 1;
-            row += rl;
-            const unsigned np = (rl + 31u) >> 5;
-            if (np) {
-                unsigned slot = atomicAdd(&rec->npieces, np);
-                for (uint32_t q = 0; q < rl; q += 32) pieces[slot++] = make_uint2(rb + q, rl - q < 32u ? rl - q : 32u);
-            }
+            row += eidx_off[u + 1] - eidx_off[u];
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        F += __shfl_down_sync(kFull, F, o);
-        n += __shfl_down_sync(kFull, n, o);
-        row += __shfl_down_sync(kFull, row, o);
+    for (int d = 16; d > 0; d >>= 1) {
+        F += __shfl_down_sync(kFull, F, d);
+        n += __shfl_down_sync(kFull, n, d);
+        row += __shfl_down_sync(kFull, row, d);
     }
     if ((threadIdx.x & 31) == 0 && n) {
         atomicAdd(&s_F, F);
@@ -529,16 +756,13 @@ __global__ void k_frontier_scan(const uint32_t* __restrict__ bm, uint32_t V, con
             atomicAdd(&rec->nfront, s_n);
             atomicAdd(&rec->rowsum, s_row);
         }
-        s_last = 0;
-        if (decide) {
-            __threadfence();
-            s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
-        }
+        __threadfence();
+        s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         __threadfence();
-        decide_next(rec, C, 0);  // rec points at slot 0 for the initial frontier
+        decide_next(rec, C, 0);
         C->ticket = 0;
     }
 }
@@ -569,10 +793,37 @@ __global__ void k_run_init(int app, uint32_t V, uint32_t root, uint32_t* vals, u
     }
 }
 
+// Loop control of the device loop: count the body execution and keep
+// looping while the frontier is non-empty, never more than max_iters + 2
+// times.
+__global__ void k_loop_ctl(RunCtl* C, cudaGraphConditionalHandle h) {
+    if (threadIdx.x == 0) {
+        const unsigned n = ++C->loops;
+        const bool more = !C->done && n < C->max_iters + 2;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
 // ------------------------------------------------------------------------
 // PageRank vertex step (K6): pr = (1-d)/V + d*(acc + D/V); then either the
-// next iteration's contributions and dangling mass, or the final ranks.
+// next iteration's fixed-point contributions and dangling mass, or the
+// final FP32 ranks.
 // ------------------------------------------------------------------------
+// Block-wide sum of x, added to *dst with one atomic per block (blockDim
+// a multiple of 32, at most 1024).
+__device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long* dst) {
+    __shared__ unsigned long long part[32];
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(kFull, x, d);
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        x = lane < (blockDim.x >> 5) ? part[lane] : 0ull;
+        for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(kFull, x, d);
+        if (lane == 0 && x) atomicAdd(dst, x);
+    }
+}
+
 __global__ void k_pr_init(uint32_t V, const uint32_t* __restrict__ outdeg, float* __restrict__ contrib,
                           unsigned long long* __restrict__ acc, RunCtl* C) {
     const float pr0 = 1.0f / (float)V;
@@ -584,8 +835,7 @@ __global__ void k_pr_init(uint32_t V, const uint32_t* __restrict__ outdeg, float
         acc[v] = 0ull;
         if (!od) dang += __float2ull_rn(pr0 * 0x1p62f);
     }
-    for (int o = 16; o > 0; o >>= 1) dang += __shfl_down_sync(kFull, dang, o);
-    if ((threadIdx.x & 31) == 0 && dang) atomicAdd(&C->dangling[0], dang);
+    block_add_u64(dang, &C->dangling[0]);
 }
 
 __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, const uint32_t* __restrict__ split_bm,
@@ -607,10 +857,11 @@ __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, cons
             if (!od) dang += __float2ull_rn(pr * 0x1p62f);
         }
     }
-    if (!last) {
-        for (int o = 16; o > 0; o >>= 1) dang += __shfl_down_sync(kFull, dang, o);
-        if ((threadIdx.x & 31) == 0 && dang) atomicAdd(&C->dangling[(t + 1) & 1], dang);
-    }
+    if (!last) block_add_u64(dang, &C->dangling[(t + 1) & 1]);
+}
+
+__global__ void k_ctl_init(RunCtl* C, RunCtl init) {
+    if (threadIdx.x == 0) *C = init;
 }
 
 __global__ void k_clear_listed(const uint32_t* __restrict__ list, const uint32_t* __restrict__ count,
@@ -619,10 +870,6 @@ __global__ void k_clear_listed(const uint32_t* __restrict__ list, const uint32_t
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
         wb[list[i] >> 5] = 0u;
-}
-
-__global__ void k_ctl_init(RunCtl* C, RunCtl init) {
-    if (threadIdx.x == 0) *C = init;
 }
 
 __global__ void k_standalone_prep(IterRec* rec, RunCtl* C, unsigned iter, unsigned sparse, unsigned k,
@@ -652,21 +899,63 @@ __global__ void k_standalone_out(const IterRec* rec, unsigned iter, unsigned lon
 // ------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------
-static int pull_grid(const wedge_graph* g) { return g->pull_blocks; }
-
 template <int APP>
-static void launch_pull(const PullParams& P, int blocks, cudaStream_t s) {
-    k_pull<APP><<<blocks, kPullThreads, 0, s>>>(P);
+static void launch_pull(const wedge_graph* g, const PullParams& P, cudaStream_t s) {
+    if (P.dense_tma)
+        k_pull<APP, true><<<g->pull_blocks_tma[APP], kPullThreads, pull_smem_bytes<APP>(true), s>>>(P);
+    else
+        k_pull<APP, false><<<g->pull_blocks_app[APP], kCW * 32, pull_smem_bytes<APP>(false), s>>>(P);
+}
+
+static void launch_pull_app(const wedge_graph* g, int app, const PullParams& P, cudaStream_t s) {
+    switch (app) {
+        case kBFS: launch_pull<kBFS>(g, P, s); break;
+        case kCC: launch_pull<kCC>(g, P, s); break;
+        case kSSSP: launch_pull<kSSSP>(g, P, s); break;
+        default: launch_pull<kPR>(g, P, s); break;
+    }
     count_launch();
 }
 
-static void launch_pull_app(int app, const PullParams& P, int blocks, cudaStream_t s) {
-    switch (app) {
-        case kBFS: launch_pull<kBFS>(P, blocks, s); break;
-        case kCC: launch_pull<kCC>(P, blocks, s); break;
-        case kSSSP: launch_pull<kSSSP>(P, blocks, s); break;
-        default: launch_pull<kPR>(P, blocks, s); break;
-    }
+// Blocks per SM for one pull variant, and a shared-memory carveout just
+// large enough for them: the rest of the unified L1 caches the gathered
+// vertex values.
+template <int APP, bool TMA>
+static wedge_status set_pull_variant(wedge_graph* g, int* blocks) {
+    const int threads = TMA ? kPullThreads : kCW * 32;
+    const int bytes = pull_smem_bytes<APP>(TMA);
+    WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_pull<APP, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_pull<APP, TMA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+    int n = 0;
+    WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pull<APP, TMA>, threads, bytes));
+    const int cap = g->tuning.blocks_per_sm;
+    if (cap > 0 && n > cap) n = cap;
+    if (n < 1) n = 1;
+    cudaFuncAttributes fa;
+    WEDGE_TRY_CUDA(cudaFuncGetAttributes(&fa, k_pull<APP, TMA>));
+    const size_t need = (size_t)n * (bytes + fa.sharedSizeBytes + 1024);
+    int pct = (int)((need * 100 + g->smem_per_sm - 1) / g->smem_per_sm);
+    if (pct > 100) pct = 100;
+    WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_pull<APP, TMA>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    *blocks = g->num_sms * n;
+    return WEDGE_OK;
+}
+
+template <int APP>
+static wedge_status set_pull_attrs(wedge_graph* g) {
+    WEDGE_TRY((set_pull_variant<APP, false>(g, &g->pull_blocks_app[APP])));
+    WEDGE_TRY((set_pull_variant<APP, true>(g, &g->pull_blocks_tma[APP])));
+    return WEDGE_OK;
+}
+
+static wedge_status configure_pulls(wedge_graph* g) {
+    WEDGE_TRY(set_pull_attrs<kBFS>(g));
+    WEDGE_TRY(set_pull_attrs<kCC>(g));
+    WEDGE_TRY(set_pull_attrs<kSSSP>(g));
+    WEDGE_TRY(set_pull_attrs<kPR>(g));
+    g->pull_blocks = g->pull_blocks_app[kCC];
+    return WEDGE_OK;
 }
 
 wedge_status ensure_run_scratch(wedge_graph* g) {
@@ -685,14 +974,14 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->ctl, sizeof(RunCtl)));
     WEDGE_TRY_CUDA(cudaMemset(g->ctl, 0, sizeof(RunCtl)));
     WEDGE_TRY_CUDA(cudaMallocHost((void**)&g->h_ctl, sizeof(RunCtl)));
+    memset(g->h_ctl, 0, sizeof(RunCtl));
     WEDGE_TRY(dev_alloc(g, (void**)&g->contrib, V * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->acc, V * 8));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->rank, V * 4));
     WEDGE_TRY_CUDA(cudaEventCreate(&g->ev0));
     WEDGE_TRY_CUDA(cudaEventCreate(&g->ev1));
-    int per_sm = 0;
-    WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pull<kSSSP>, kPullThreads, 0));
-    if (per_sm < 1) per_sm = 1;
-    g->pull_blocks = g->num_sms * per_sm;
+    WEDGE_TRY_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    WEDGE_TRY(configure_pulls(g));
     g->xform_blocks = g->num_sms * 4;
     return WEDGE_OK;
 }
@@ -712,31 +1001,80 @@ static PullParams pull_params(wedge_graph* g, int trace) {
     P.bm[1] = g->bm[1];
     P.clist = g->clist;
     P.wb = g->wb;
-    P.pieces = g->pieces;
     P.rec = g->rec;
     P.ctl = g->ctl;
     P.contrib = g->contrib;
     P.acc = g->acc;
     P.decide = 1;
     P.trace = trace;
+    P.dense_tma = g->tuning.dense_loader == 1 ? 1 : 0;
     return P;
 }
 
 static XformParams xform_params(wedge_graph* g, int trace) {
     XformParams X{};
     X.eidx = g->eidx;
+    X.eidx_off = g->eidx_off;
     X.pieces = g->pieces;
     X.wb = g->wb;
     X.clist = g->clist;
     X.rec = g->rec;
     X.ctl = g->ctl;
-    X.bm_clear[0] = g->bm[0];
-    X.bm_clear[1] = g->bm[1];
+    X.bm[0] = g->bm[0];
+    X.bm[1] = g->bm[1];
+    X.bm_in = nullptr;
+    X.V = g->V;
     X.bm_words = ((uint64_t)g->V + 31) / 32;
     X.count_out = nullptr;
     X.standalone_k = -1;
     X.trace = trace;
     return X;
+}
+
+static void launch_xform(const wedge_graph* g, const XformParams& X, cudaStream_t s) {
+    k_xform_scan<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+    k_xform_expand<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+    count_launch(2);
+}
+
+// Captures the loop body (pull, transformation, loop control) under a
+// conditional while node.  The body reads everything from the library-owned
+// buffers, so one instance serves every run of `app` on g.
+static wedge_status build_loop_graph(wedge_graph* g, int app) {
+    cudaGraph_t graph = nullptr;
+    WEDGE_TRY_CUDA(cudaGraphCreate(&graph, 0));
+    struct Destroy {
+        cudaGraph_t g;
+        ~Destroy() {
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{graph};
+    cudaGraphConditionalHandle handle;
+    WEDGE_TRY_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    WEDGE_TRY_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = g->cap_stream;
+    WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    PullParams P = pull_params(g, 0);
+    XformParams X = xform_params(g, 0);
+    launch_pull_app(g, app, P, cs);
+    launch_xform(g, X, cs);
+    k_loop_ctl<<<1, 32, 0, cs>>>(g->ctl, handle);
+    cudaError_t le = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) return cuda_error(le, "loop body launch");
+    if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    WEDGE_TRY_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    g->loop_exec[app] = exec;
+    return WEDGE_OK;
 }
 
 static wedge_status check_opts(const wedge_opts* o) {
@@ -748,39 +1086,53 @@ static wedge_status check_opts(const wedge_opts* o) {
 }
 
 static wedge_status fill_stats(wedge_graph* g, cudaStream_t s, wedge_stats* stats) {
+    if (!stats) return WEDGE_OK;
     WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
-    WEDGE_TRY_CUDA(cudaMemcpy(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost));
     const uint32_t iters = g->h_ctl->it;
     g->last_iters = iters;
-    if (stats) {
-        std::vector<IterRec> r(iters + 1);
-        if (iters) WEDGE_TRY_CUDA(cudaMemcpy(r.data(), g->rec, (size_t)iters * sizeof(IterRec), cudaMemcpyDeviceToHost));
-        stats->iters = iters;
-        stats->sparse_iters = 0;
-        stats->edges_pulled = 0;
-        stats->chunks_listed = 0;
-        for (uint32_t t = 0; t < iters; ++t) {
-            if (r[t].mode) {
-                stats->sparse_iters++;
-                stats->chunks_listed += r[t].nchunks;
-                uint64_t e = (uint64_t)r[t].nchunks << (5 + r[t].k);
-                stats->edges_pulled += e < g->E ? e : g->E;
-            } else {
-                stats->edges_pulled += g->E;
-            }
+    std::vector<IterRec> r(iters + 1);
+    if (iters) WEDGE_TRY_CUDA(cudaMemcpy(r.data(), g->rec, (size_t)iters * sizeof(IterRec), cudaMemcpyDeviceToHost));
+    stats->iters = iters;
+    stats->sparse_iters = 0;
+    stats->edges_pulled = 0;
+    stats->chunks_listed = 0;
+    for (uint32_t t = 0; t < iters; ++t) {
+        if (r[t].mode) {
+            stats->sparse_iters++;
+            stats->chunks_listed += r[t].nchunks;
+            const uint64_t e = (uint64_t)r[t].nchunks << (5 + r[t].k);
+            stats->edges_pulled += e < g->E ? e : g->E;
+        } else {
+            stats->edges_pulled += g->E;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
-        stats->device_ms = ms;
     }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    stats->device_ms = ms;
+    if (g->h_ctl->status & kStatusTimeout) return set_error(WEDGE_ERR_TIMEOUT, "a bounded device wait timed out");
     if (g->h_ctl->status & kStatusMaxIters)
         return set_error(WEDGE_ERR_MAX_ITERS, "frontier still non-empty at max_iters");
     return WEDGE_OK;
 }
 
-// The loop: pull and transform alternate on the device; the host only polls
-// the done flag after each batch of iterations (kernels after the last
-// iteration return at once).
+// Host-polled loop: traced runs, and graphs whose device loop could not be built.
+static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, const XformParams& X, uint32_t max_iters,
+                              cudaStream_t s) {
+    const int batch = 8;
+    uint32_t launched = 0;
+    for (;;) {
+        for (int b = 0; b < batch; ++b) {
+            launch_pull_app(g, app, P, s);
+            launch_xform(g, X, s);
+        }
+        launched += batch;
+        WEDGE_TRY_CUDA(cudaGetLastError());
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+        if (g->h_ctl->done || launched > max_iters + 2) return WEDGE_OK;
+    }
+}
+
 static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uint32_t* out,
                                      const wedge_opts* opts_in, wedge_stats* stats, cudaStream_t s) {
     wedge_opts o;
@@ -791,8 +1143,8 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     if (app != kCC && root >= g->V) return set_error(WEDGE_ERR_INVALID_ARG, "root out of range");
     if (app == kSSSP && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
     DeviceGuard dg(g->device);
-    const uint32_t max_iters = o.max_iters ? (o.max_iters < kDefaultMaxIters ? o.max_iters : kDefaultMaxIters)
-                                           : kDefaultMaxIters;
+    const uint32_t max_iters =
+        o.max_iters ? (o.max_iters < kDefaultMaxIters ? o.max_iters : kDefaultMaxIters) : kDefaultMaxIters;
     const int trace = o.trace ? 1 : 0;
     RunCtl init{};
     init.max_iters = max_iters;
@@ -801,35 +1153,50 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     init.k = o.log2_coarsen;
     init.E = g->E;
     const uint64_t wb_words = (g->NC + 31) / 32 + 1;
+    if (!trace && !g->loop_exec[app] && !g->loop_failed) {
+        if (build_loop_graph(g, app) != WEDGE_OK) {
+            g->loop_failed = true;  // this graph keeps the host-polled loop
+            std::fprintf(stderr, "wedge: device loop graph unavailable (%s); using the host-polled loop\n",
+                         wedge_last_error());
+            cudaGetLastError();
+        }
+    }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
-    k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words,
-                                              g->rec, g->ctl, init);
-    k_frontier_scan<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->pieces, g->rec,
-                                                   g->ctl, 1);
+    k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words, g->rec,
+                                              g->ctl, init);
+    k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl);
+    count_launch(2);
     PullParams P = pull_params(g, trace);
     XformParams X = xform_params(g, trace);
-    k_transform<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
-    count_launch(3);
+    launch_xform(g, X, s);
     WEDGE_TRY_CUDA(cudaGetLastError());
-    const int batch = 8;
-    uint32_t launched = 0;
-    for (;;) {
-        for (int b = 0; b < batch; ++b) {
-            launch_pull_app(app, P, pull_grid(g), s);
-            k_transform<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
-            count_launch();
-        }
-        launched += batch;
-        WEDGE_TRY_CUDA(cudaGetLastError());
-        WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
-        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
-        if (g->h_ctl->done || launched > max_iters + 2) break;
+    if (!trace && g->loop_exec[app]) {
+        WEDGE_TRY_CUDA(cudaGraphLaunch(g->loop_exec[app], s));
+    } else {
+        WEDGE_TRY(host_loop(g, app, P, X, max_iters, s));
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(out, g->vals, (uint64_t)g->V * 4, cudaMemcpyDefault, s));
     g->last_trace = trace;
     g->last_stream = s;
     return fill_stats(g, s, stats);
+}
+
+// PageRank: iters x (dense pull, vertex step).
+static void pr_enqueue(wedge_graph* g, uint32_t iters, float damping, cudaStream_t s) {
+    const int vb = g->num_sms * 8;
+    PullParams P = pull_params(g, 0);
+    P.decide = 0;
+    const float base = (1.0f - damping) / (float)g->V;
+    for (uint32_t t = 0; t < iters; ++t) {
+        P.pr_iter = t;
+        launch_pull_app(g, kPR, P, s);
+        const int last = (t + 1 == iters);
+        k_pr_apply<<<vb, 256, 0, s>>>(g->V, g->outdeg, g->split_bm, g->acc, g->contrib, g->rank, g->ctl, t, last, base,
+                                      damping);
+        count_launch();
+    }
 }
 
 }  // namespace wedge
@@ -861,39 +1228,49 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
     if (!g) return set_error(WEDGE_ERR_INVALID_ARG, "graph is NULL");
     if (!d_rank) return set_error(WEDGE_ERR_INVALID_ARG, "rank output is NULL");
     if (!(damping >= 0.0f && damping <= 1.0f)) return set_error(WEDGE_ERR_INVALID_ARG, "damping must be in [0,1]");
-    (void)opts;
+    if (opts) WEDGE_TRY(check_opts(opts));
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t V = g->V;
-    const int vb = g->num_sms * 8;
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     RunCtl init{};
     init.max_iters = 0xFFFFFFFFu;
-    k_ctl_init<<<1, 32, 0, s>>>(g->ctl, init);
-    count_launch();
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, 2 * sizeof(IterRec), s));
-    k_pr_init<<<vb, 256, 0, s>>>(V, g->outdeg, g->contrib, g->acc, g->ctl);
-    count_launch();
-    PullParams P = pull_params(g, 0);
-    P.decide = 0;
-    const float base = (1.0f - damping) / (float)V;
+    k_ctl_init<<<1, 32, 0, s>>>(g->ctl, init);
+    k_pr_init<<<g->num_sms * 8, 256, 0, s>>>(V, g->outdeg, g->contrib, g->acc, g->ctl);
+    count_launch(2);
     if (iters == 0) {
-        // pr0 = 1/V everywhere
         std::vector<float> h(V, 1.0f / (float)V);
         WEDGE_TRY_CUDA(cudaMemcpyAsync(d_rank, h.data(), (uint64_t)V * 4, cudaMemcpyHostToDevice, s));
         WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
-    }
-    for (uint32_t t = 0; t < iters; ++t) {
-        P.pr_iter = t;
-        launch_pull<kPR>(P, pull_grid(g), s);
-        const int last = (t + 1 == iters);
-        k_pr_apply<<<vb, 256, 0, s>>>(V, g->outdeg, g->split_bm, g->acc, g->contrib, g->contrib, g->ctl, t, last,
-                                      base, damping);
-        count_launch();
+    } else {
+        if (!g->pr_exec || g->pr_exec_iters != iters || g->pr_exec_damping != damping) {
+            if (g->pr_exec) {
+                cudaGraphExecDestroy(g->pr_exec);
+                g->pr_exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            WEDGE_TRY_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+            pr_enqueue(g, iters, damping, g->cap_stream);
+            cudaError_t le = cudaGetLastError();
+            cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
+            if (le != cudaSuccess || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_error(le != cudaSuccess ? le : ce, "PageRank capture");
+            }
+            cudaError_t ie = cudaGraphInstantiate(&g->pr_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return cuda_error(ie, "cudaGraphInstantiate");
+            g->pr_exec_iters = iters;
+            g->pr_exec_damping = damping;
+        } else {
+            count_launch(2ull * iters);
+        }
+        WEDGE_TRY_CUDA(cudaGraphLaunch(g->pr_exec, s));
     }
     WEDGE_TRY_CUDA(cudaGetLastError());
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
-    if (iters) WEDGE_TRY_CUDA(cudaMemcpyAsync(d_rank, g->contrib, (uint64_t)V * 4, cudaMemcpyDefault, s));
+    if (iters) WEDGE_TRY_CUDA(cudaMemcpyAsync(d_rank, g->rank, (uint64_t)V * 4, cudaMemcpyDefault, s));
     if (stats) {
         WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
         stats->iters = iters;
@@ -906,6 +1283,7 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
     }
     g->last_iters = iters;
     g->last_trace = false;
+    g->last_stream = s;
     return WEDGE_OK;
 }
 
@@ -918,20 +1296,14 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
     cudaStream_t s = (cudaStream_t)stream;
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, sizeof(IterRec), s));
     WEDGE_TRY_CUDA(cudaMemsetAsync(d_chunk_count, 0, 4, s));
-    k_frontier_scan<<<g->num_sms * 4, 256, 0, s>>>(d_vertex_bitmap, g->V, g->outdeg, g->eidx_off, g->pieces, g->rec,
-                                                   g->ctl, 0);
-    XformParams X{};
-    X.eidx = g->eidx;
-    X.pieces = g->pieces;
-    X.wb = g->wb;
+    XformParams X = xform_params(g, 0);
+    X.bm_in = d_vertex_bitmap;
     X.clist = d_chunk_list;
-    X.rec = g->rec;
-    X.ctl = g->ctl;
     X.count_out = d_chunk_count;
     X.standalone_k = (int)log2_coarsen;
-    k_transform<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+    launch_xform(g, X, s);
     k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
-    count_launch(3);
+    count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
 }
@@ -961,10 +1333,37 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     P.clist = d_chunk_list ? d_chunk_list : g->clist;
     P.wb = nullptr;  // a caller's list has no library bitmap behind it
     P.decide = 0;
-    launch_pull_app(app, P, pull_grid(g), s);
+    launch_pull_app(g, app, P, s);
     k_standalone_out<<<1, 32, 0, s>>>(g->rec, iter, reinterpret_cast<unsigned long long*>(d_fullness), d_nfront);
     count_launch(2);
     WEDGE_TRY_CUDA(cudaGetLastError());
+    return WEDGE_OK;
+}
+
+wedge_status wedge_graph_set_tuning(wedge_graph_t g, const wedge_tuning* t) {
+    if (!g || !t) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (t->dense_loader > 1) return set_error(WEDGE_ERR_INVALID_ARG, "dense_loader must be 0 or 1");
+    for (uint32_t r : t->reserved)
+        if (r) return set_error(WEDGE_ERR_INVALID_ARG, "reserved tuning fields must be zero");
+    DeviceGuard dg(g->device);
+    WEDGE_TRY_CUDA(cudaDeviceSynchronize());
+    g->tuning = *t;
+    for (auto& e : g->loop_exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    if (g->pr_exec) {
+        cudaGraphExecDestroy(g->pr_exec);
+        g->pr_exec = nullptr;
+    }
+    g->loop_failed = false;
+    return configure_pulls(g);
+}
+
+wedge_status wedge_graph_get_tuning(wedge_graph_t g, wedge_tuning* out) {
+    if (!g || !out) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    *out = g->tuning;
     return WEDGE_OK;
 }
 
@@ -972,7 +1371,7 @@ wedge_status wedge_get_trace(wedge_graph_t g, wedge_iter_record* out, uint32_t c
     if (!g || !n || (!out && cap)) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard dg(g->device);
     WEDGE_TRY_CUDA(cudaStreamSynchronize(g->last_stream));
-    const uint32_t iters = g->last_iters;
+    const uint32_t iters = g->h_ctl->it;
     *n = iters;
     const uint32_t m = iters < cap ? iters : cap;
     if (!m) return WEDGE_OK;

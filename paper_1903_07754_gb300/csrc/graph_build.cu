@@ -138,7 +138,7 @@ __global__ void k_chunk_meta(const uint32_t* __restrict__ off, uint32_t V, const
         vid[k] = (uint32_t)v;
         atomicOr(&cmeta[b >> 5].x, 1u << (b & 31));
         for (uint32_t c = (b + 31) >> 5; c <= (e - 1) >> 5; ++c) cmeta[c].y = k;
-        if ((b >> 7) != ((e - 1) >> 7)) atomicOr(&split_bm[v >> 5], 1u << (v & 31));
+        if ((b >> kSliceShift) != ((e - 1) >> kSliceShift)) atomicOr(&split_bm[v >> 5], 1u << (v & 31));
     }
 }
 
@@ -165,6 +165,13 @@ __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64
             atomicAdd(&counter[s], 1u);
         }
     }
+}
+
+// Metadata past the last chunk reads as "a new destination starts here".
+__global__ void k_meta_pad(uint2* __restrict__ cmeta, uint64_t NC, uint64_t len) {
+    for (uint64_t c = NC + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < len;
+         c += (uint64_t)gridDim.x * blockDim.x)
+        cmeta[c] = make_uint2(1u, 0u);
 }
 
 __global__ void k_pieces_total(const uint32_t* __restrict__ rowlen, uint32_t V,
@@ -255,7 +262,12 @@ static void free_graph(wedge_graph* g) {
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     dev_free(g->contrib);
     dev_free(g->acc);
+    dev_free(g->rank);
     dev_free(g->split_bm);
+    for (auto& e : g->loop_exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
@@ -317,8 +329,11 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     WEDGE_TRY_CUDA(cudaMemcpy(&g->NZ, knz + V, 4, cudaMemcpyDeviceToHost));
 
     WEDGE_TRY(dev_alloc(g, (void**)&g->vid, (uint64_t)(g->NZ ? g->NZ : 1) * 4));
-    WEDGE_TRY(dev_alloc(g, (void**)&g->cmeta, (NC ? NC : 1) * sizeof(uint2)));
-    WEDGE_TRY_CUDA(cudaMemsetAsync(g->cmeta, 0, (NC ? NC : 1) * sizeof(uint2), s));
+    g->meta_len = (NC + kTileC - 1) / kTileC * kTileC + kTileC + kMetaPad;
+    WEDGE_TRY(dev_alloc(g, (void**)&g->cmeta, g->meta_len * sizeof(uint2)));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->cmeta, 0, g->meta_len * sizeof(uint2), s));
+    k_meta_pad<<<grid_for(g->meta_len - NC, 256, sms), 256, 0, s>>>(g->cmeta, NC, g->meta_len);
+    count_launch();
     const uint64_t bm_words = ((uint64_t)V + 31) / 32;
     WEDGE_TRY(dev_alloc(g, (void**)&g->split_bm, bm_words * 4));
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->split_bm, 0, bm_words * 4, s));
@@ -426,6 +441,7 @@ wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offset
         return cuda_error(e, "cudaGetDeviceProperties");
     }
     g->num_sms = prop.multiProcessorCount;
+    g->smem_per_sm = prop.sharedMemPerMultiprocessor;
     g->V = V;
     g->E = E;
     g->NC = (E + kChunk - 1) / kChunk;

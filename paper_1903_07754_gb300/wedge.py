@@ -50,6 +50,11 @@ class wedge_iter_record(ctypes.Structure):
                 ("npieces", ctypes.c_uint32), ("t_pull_ns", ctypes.c_uint64), ("t_xform_ns", ctypes.c_uint64)]
 
 
+class wedge_tuning(ctypes.Structure):
+    _fields_ = [("dense_loader", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
 class wedge_graph_info(ctypes.Structure):
     _fields_ = [("V", ctypes.c_uint32), ("nz_dst", ctypes.c_uint32), ("E", ctypes.c_uint64),
                 ("nchunks", ctypes.c_uint64), ("eidx_len", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
@@ -60,7 +65,7 @@ EXPORTS = [
     "wedge_default_opts", "wedge_graph_create", "wedge_graph_destroy", "wedge_graph_get_info",
     "wedge_graph_copy_edge_index", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
     "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr", "wedge_get_trace", "wedge_kernel_launches",
-    "wedge_last_error", "wedge_version",
+    "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
 ]
 
 _lib = None
@@ -91,6 +96,8 @@ def load(path: str = LIB_PATH):
         "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
                               ctypes.POINTER(wedge_stats), P]),
         "wedge_get_trace": (st, [P, ctypes.POINTER(wedge_iter_record), u32, ctypes.POINTER(u32)]),
+        "wedge_graph_set_tuning": (st, [P, ctypes.POINTER(wedge_tuning)]),
+        "wedge_graph_get_tuning": (st, [P, ctypes.POINTER(wedge_tuning)]),
         "wedge_kernel_launches": (u64, []),
         "wedge_last_error": (ctypes.c_char_p, []),
         "wedge_version": (ctypes.c_char_p, []),
@@ -211,6 +218,19 @@ def wedge_get_trace(handle, cap=1 << 16):
     n = ctypes.c_uint32()
     _check(load().wedge_get_trace(handle, buf, cap, ctypes.byref(n)))
     return [{f: getattr(buf[i], f) for f, _ in wedge_iter_record._fields_} for i in range(min(n.value, cap))]
+
+
+def wedge_graph_set_tuning(handle, dense_loader=0, blocks_per_sm=0):
+    t = wedge_tuning()
+    t.dense_loader = int(dense_loader)
+    t.blocks_per_sm = int(blocks_per_sm)
+    _check(load().wedge_graph_set_tuning(handle, ctypes.byref(t)))
+
+
+def wedge_graph_get_tuning(handle) -> dict:
+    t = wedge_tuning()
+    _check(load().wedge_graph_get_tuning(handle, ctypes.byref(t)))
+    return {"dense_loader": t.dense_loader, "blocks_per_sm": t.blocks_per_sm}
 
 
 def wedge_kernel_launches() -> int:
