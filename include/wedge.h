@@ -183,6 +183,27 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
                                       uint32_t log2_coarsen, uint32_t* d_chunk_list,
                                       uint32_t* d_chunk_count, wedge_stream_t stream);
 
+/* The frontier transformation without any memory allocation.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a framework that owns all device memory through its own pool,
+ * latency-critical loops, deployments whose device footprint is fixed at
+ * load time).  It needs no graph object: the caller passes the edge index
+ * (d_eidx_off[V+1], d_eidx: chunk ids of each source's out-edges, as built
+ * by wedge_graph_create or given to it), the vertex bitmap, and the output
+ * list (capacity ceil(ceil(E/32) / 2^k)) and count, all device memory.
+ * Output: as wedge_frontier_transform (distinct entries, unspecified order).
+ * The duplicate-removing bitmap lives in a fixed 4 MiB device array that
+ * every GPU loading the library holds until the process exits; graphs with
+ * ceil(ceil(E/32) / 2^k) > 2^25 are rejected with INVALID_ARG.  The first call
+ * on a device looks up that array's address; make that first call before
+ * any stream capture.  All calls on a device share the array (each clears
+ * the part it uses), so calls that overlap on the GPU race.
+ * Errors: INVALID_ARG, NOT_SUPPORTED (device index >= 64), CUDA. */
+wedge_status wedge_frontier_transform_noalloc(uint32_t V, uint64_t E, const uint32_t* d_eidx_off,
+                                              const uint32_t* d_eidx, const uint32_t* d_vertex_bitmap,
+                                              uint32_t log2_coarsen, uint32_t* d_chunk_list,
+                                              uint32_t* d_chunk_count, wedge_stream_t stream);
+
 /* One pull iteration of BFS, CC or SSSP (Sections 2.1, 3.2, 5):
  *  d_values (V, device) is updated in place: BFS levels, CC labels or SSSP
  *  distances.  iter is the iteration number (BFS gives level iter+1 to newly

@@ -66,6 +66,7 @@ EXPORTS = [
     "wedge_graph_copy_edge_index", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
     "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr", "wedge_get_trace", "wedge_kernel_launches",
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
+    "wedge_frontier_transform_noalloc",
 ]
 
 _lib = None
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
         "wedge_graph_get_info": (st, [P, ctypes.POINTER(wedge_graph_info)]),
         "wedge_graph_copy_edge_index": (st, [P, P, P, P]),
         "wedge_frontier_transform": (st, [P, P, u32, P, P, P]),
+        "wedge_frontier_transform_noalloc": (st, [u32, u64, P, P, P, u32, P, P, P]),
         "wedge_pull_iterate": (st, [P, i32, P, u32, P, P, P, u32, P, P, P, P]),
         "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
@@ -171,6 +173,15 @@ def wedge_graph_copy_edge_index(handle, eidx_off, eidx, stream=None):
 def wedge_frontier_transform(handle, vertex_bitmap, log2_coarsen, chunk_list, chunk_count, stream=None):
     _check(load().wedge_frontier_transform(handle, _ptr(vertex_bitmap), int(log2_coarsen), _ptr(chunk_list),
                                            _ptr(chunk_count), _stream(stream)))
+
+
+def wedge_frontier_transform_noalloc(V, E, eidx_off, eidx, vertex_bitmap, log2_coarsen, chunk_list, chunk_count,
+                                     stream=None):
+    """Allocation-free transformation for callers that cannot call cudaMalloc:
+    its scratch is a fixed device array inside the library (see wedge.h)."""
+    _check(load().wedge_frontier_transform_noalloc(int(V), int(E), _ptr(eidx_off), _ptr(eidx), _ptr(vertex_bitmap),
+                                                   int(log2_coarsen), _ptr(chunk_list), _ptr(chunk_count),
+                                                   _stream(stream)))
 
 
 def wedge_pull_iterate(handle, app, values, it, cur_bitmap, chunk_list, chunk_count, log2_coarsen, next_bitmap,
