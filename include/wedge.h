@@ -249,6 +249,49 @@ wedge_status wedge_run_sssp(wedge_graph_t g, uint32_t root, uint32_t* d_dist,
 wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float damping,
                           const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
 
+/* ---- Learned switch (not in the paper) --------------------------------
+ * A cost model replaces the fixed fullness threshold and the fixed
+ * precision of Section 3.4: before each pull it predicts ln(milliseconds)
+ * of the iteration under each candidate (dense pull; Wedge Frontier at
+ * k = 0..4) and the lowest prediction wins (WEDGE_SWITCH_LEARNED).  Model:
+ * 12 features -> 64 ReLU -> 64 ReLU -> 1; parameters as one FP32 array of
+ * WEDGE_MLP_PARAMS floats laid out W1[64][12] | b1[64] | W2[64][64] | b2[64]
+ * | w3[64] | b3.  Features (per candidate): log2(|F|+1)/32,
+ * log2(fullness+1)/32, fullness/E, log2(edge-index row sum+1)/32, log2(V)/32,
+ * log2(E)/32, (E/V)/64, log2(1+max/mean out-degree)/16, t/(t+8), app (BFS 0,
+ * CC 0.5, SSSP 1), is_sparse, k/4. */
+#define WEDGE_MLP_FEATURES 12
+#define WEDGE_MLP_PARAMS 5057
+#define WEDGE_MLP_CANDIDATES 6
+
+/* FP32 forward on n rows (d_x row-major n x 12) into d_y (n); device memory. */
+wedge_status wedge_mlp_forward(const float* d_params, const float* d_x, uint32_t n, float* d_y,
+                               wedge_stream_t stream);
+/* The same model as the decision evaluates it: BF16 copy of the weights,
+ * BF16 activations, FP32 accumulation.  Synchronises the stream. */
+wedge_status wedge_mlp_forward_bf16(const float* d_params, const float* d_x, uint32_t n, float* d_y,
+                                    wedge_stream_t stream);
+/* *d_loss = mean_i (f(x_i) - t_i)^2 and d_grad (5057) = its gradient with
+ * respect to the parameters (FP32, device memory). */
+wedge_status wedge_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_t, uint32_t n,
+                                 float* d_grad, float* d_loss, wedge_stream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step t >= 1) on d_params
+ * with moment buffers d_m, d_v (5057 floats each, start at zero). */
+wedge_status wedge_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, uint32_t t, float lr,
+                            wedge_stream_t stream);
+/* Installs (params != NULL, host or device FP32) or removes the cost model
+ * used by WEDGE_SWITCH_LEARNED on g; without one the threshold decides. */
+wedge_status wedge_set_cost_model(wedge_graph_t g, const float* params);
+/* Training traces: runs app (BFS, CC, SSSP) from root with the threshold
+ * policy of opts (log2_coarsen <= 4), and before every pull t (t < cap and
+ * t < max_iters, 0 = no limit) times each candidate c (transformation +
+ * pull, from the same saved state) into h_ms[t*6+c], with its features in
+ * h_features[(t*6+c)*12 ..], and the threshold's choice in h_chosen[t]
+ * (0 dense, 1+k sparse).  Host outputs; synchronous.  *n_iters = rows. */
+wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t root, const wedge_opts* opts,
+                                    uint32_t max_iters, float* h_features, float* h_ms, uint32_t* h_chosen,
+                                    uint32_t cap, uint32_t* n_iters, wedge_stream_t stream);
+
 /* Per-iteration records of the last run of g (needs opts.trace).  Copies up
  * to cap records into host memory, sets *n to the number available.
  * Synchronises the stream of that run. */

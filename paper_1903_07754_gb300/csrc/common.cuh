@@ -129,6 +129,11 @@ struct wedge_graph {
     uint32_t pr_exec_iters = 0;
     float pr_exec_damping = -1.f;
     int pull_smem = 0;
+    // learned switch
+    void* mlp_bf16 = nullptr;        // cost model weights (BF16)
+    bool has_model = false;
+    uint32_t max_outdeg = 0;
+    uint32_t* snap_vals = nullptr;   // candidate-timing trace: value snapshot
     uint64_t device_bytes = 0;
     int num_sms = 0;
     size_t smem_per_sm = 0;

@@ -5,11 +5,15 @@
 //   4), PageRank, and the run drivers for BFS, CC, SSSP and PageRank
 //   (Section 5).  The iteration loop runs on the device inside a CUDA graph
 //   with a conditional while node.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "mlp.cuh"
 #include "tma.cuh"
 
 namespace wedge {
@@ -47,6 +51,8 @@ struct PullParams {
     int decide;                  // elect a last block that takes the fullness decision
     int trace;
     int dense_tma;               // dense pulls stage tiles with bulk copies
+    const __nv_bfloat16* mlp;    // learned switch weights (nullptr: threshold)
+    GraphFeat gf;                // graph statistics of the learned switch's features
 };
 
 struct XformParams {
@@ -123,18 +129,74 @@ __device__ __forceinline__ bool set_bit(uint32_t* bm, uint32_t v) {
     return (atomicOr(bm + (v >> 5), bit) & bit) == 0;
 }
 
-// The fullness decision (Section 3.4, "Frontier Fullness Threshold"; Fig. 5):
-// run by one thread once every block has published its frontier sums.
-__device__ void decide_next(IterRec* rec, RunCtl* C, unsigned it_next) {
+// The fullness decision (Section 3.4, "Frontier Fullness Threshold"; Fig. 5)
+// for pull it_next, taken by one block once every block has published its
+// frontier sums.  With the learned switch, the block first evaluates the
+// cost model on the six candidates (dense; Wedge Frontier with k = 0..4):
+// BF16 weights and activations, FP32 accumulation; the lowest predicted
+// time wins.  Without a model, or if no prediction is finite, the threshold
+// decides.  `sm` needs 2*6*64 + 8 floats of shared memory.
+__device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __nv_bfloat16* mlp,
+                             const GraphFeat& gf, float* sm) {
     IterRec* r = rec + it_next;
     const unsigned long long F = __ldcg(&r->fullness);
     const unsigned nf = __ldcg(&r->nfront);
-    unsigned sparse;
-    if (C->switch_mode == WEDGE_SWITCH_ALWAYS_DENSE) sparse = 0;
-    else if (C->switch_mode == WEDGE_SWITCH_ALWAYS_SPARSE) sparse = 1;
-    else sparse = (F * 10000ull < (unsigned long long)C->tau_bp * C->E) ? 1u : 0u;
+    const unsigned rows = __ldcg(&r->rowsum);
+    const bool learned = C->switch_mode == WEDGE_SWITCH_LEARNED && mlp != nullptr && nf > 0;
+    float* h1 = sm;
+    float* h2 = sm + kCandidates * kMlpHidden;
+    float* out = sm + 2 * kCandidates * kMlpHidden;
+    if (learned) {
+        const double E = (double)C->E;
+        for (int o = threadIdx.x; o < kCandidates * kMlpHidden; o += blockDim.x) {
+            const int c = o / kMlpHidden, j = o % kMlpHidden;
+            float x[kMlpIn];
+            mlp_features(gf, E, nf, (double)F, rows, it_next, c, x);
+            float a = __bfloat162float(mlp[kMlpB1 + j]);
+            for (int f = 0; f < kMlpIn; ++f)
+                a = fmaf(__bfloat162float(mlp[kMlpW1 + j * kMlpIn + f]), __bfloat162float(__float2bfloat16_rn(x[f])), a);
+            h1[o] = __bfloat162float(__float2bfloat16_rn(fmaxf(a, 0.f)));
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < kCandidates * kMlpHidden; o += blockDim.x) {
+            const int c = o / kMlpHidden, j = o % kMlpHidden;
+            float a = __bfloat162float(mlp[kMlpB2 + j]);
+            for (int k = 0; k < kMlpHidden; ++k)
+                a = fmaf(__bfloat162float(mlp[kMlpW2 + j * kMlpHidden + k]), h1[c * kMlpHidden + k], a);
+            h2[o] = __bfloat162float(__float2bfloat16_rn(fmaxf(a, 0.f)));
+        }
+        __syncthreads();
+        if (threadIdx.x < kCandidates) {
+            float y = __bfloat162float(mlp[kMlpB3]);
+            for (int j = 0; j < kMlpHidden; ++j)
+                y = fmaf(__bfloat162float(mlp[kMlpW3 + j]), h2[threadIdx.x * kMlpHidden + j], y);
+            out[threadIdx.x] = y;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    int choice = -1;
+    if (learned) {
+        float best = 0.f;
+        for (int c = 0; c < kCandidates; ++c)
+            if (isfinite(out[c]) && (choice < 0 || out[c] < best)) {
+                best = out[c];
+                choice = c;
+            }
+    }
+    unsigned sparse, k = C->k;
+    if (choice >= 0) {
+        sparse = choice > 0;
+        if (sparse) k = (unsigned)(choice - 1);
+    } else if (C->switch_mode == WEDGE_SWITCH_ALWAYS_DENSE) {
+        sparse = 0;
+    } else if (C->switch_mode == WEDGE_SWITCH_ALWAYS_SPARSE) {
+        sparse = 1;
+    } else {
+        sparse = (F * 10000ull < (unsigned long long)C->tau_bp * C->E) ? 1u : 0u;
+    }
     r->mode = sparse;
-    r->k = C->k;
+    r->k = k;
     if (nf == 0) {
         C->done = 1;
     } else if (it_next >= C->max_iters) {
@@ -574,11 +636,13 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
         }
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {  // uniform across the block
         __threadfence();
-        decide_next(P.rec, C, it + 1);
-        C->ticket = 0;
-        if (P.trace) P.rec[it].t_pull1 = global_timer();
+        decide_block(P.rec, C, it + 1, P.mlp, P.gf, reinterpret_cast<float*>(smem));
+        if (threadIdx.x == 0) {
+            C->ticket = 0;
+            if (P.trace) P.rec[it].t_pull1 = global_timer();
+        }
     }
 }
 
@@ -716,7 +780,9 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
 // Initial frontier: size, fullness and edge-index work (the transformation
 // derives its pieces from the bitmap), then the decision for pull 0.
 __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, const uint32_t* __restrict__ outdeg,
-                                 const uint32_t* __restrict__ eidx_off, IterRec* rec, RunCtl* C) {
+                                 const uint32_t* __restrict__ eidx_off, IterRec* rec, RunCtl* C,
+                                 const __nv_bfloat16* mlp, GraphFeat gf) {
+    __shared__ float dsm[2 * kCandidates * kMlpHidden + 8];
     __shared__ unsigned long long s_F;
     __shared__ unsigned s_n, s_row, s_last;
     if (threadIdx.x == 0) {
@@ -760,10 +826,10 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
         s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {
         __threadfence();
-        decide_next(rec, C, 0);
-        C->ticket = 0;
+        decide_block(rec, C, 0, mlp, gf, dsm);
+        if (threadIdx.x == 0) C->ticket = 0;
     }
 }
 
@@ -889,6 +955,10 @@ __global__ void k_standalone_prep(IterRec* rec, RunCtl* C, unsigned iter, unsign
     }
 }
 
+__global__ void k_rec_set(IterRec* rec, unsigned t, IterRec v) {
+    if (threadIdx.x == 0) rec[t] = v;
+}
+
 __global__ void k_standalone_out(const IterRec* rec, unsigned iter, unsigned long long* fullness, uint32_t* nfront) {
     if (threadIdx.x == 0) {
         *fullness = rec[iter + 1].fullness;
@@ -986,8 +1056,21 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     return WEDGE_OK;
 }
 
-static PullParams pull_params(wedge_graph* g, int trace) {
+static GraphFeat graph_feat(const wedge_graph* g, int app) {
+    GraphFeat f;
+    f.log2V = (float)std::log2((double)g->V);
+    f.log2E = (float)std::log2((double)(g->E ? g->E : 1));
+    f.avg_deg = (float)((double)g->E / (double)g->V);
+    const double mean = (double)g->E / (double)g->V;
+    f.skew = (float)(std::log2(1.0 + (mean > 0 ? g->max_outdeg / mean : 0.0)) / 16.0);
+    f.app = app == kBFS ? 0.f : (app == kCC ? 0.5f : 1.f);
+    return f;
+}
+
+static PullParams pull_params(wedge_graph* g, int trace, int app = kCC) {
     PullParams P{};
+    P.gf = graph_feat(g, app);
+    P.mlp = g->has_model ? reinterpret_cast<const __nv_bfloat16*>(g->mlp_bf16) : nullptr;
     P.src = g->src;
     P.w = g->w;
     P.cmeta = g->cmeta;
@@ -1061,7 +1144,7 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaStream_t cs = g->cap_stream;
     WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    PullParams P = pull_params(g, 0);
+    PullParams P = pull_params(g, 0, app);
     XformParams X = xform_params(g, 0);
     launch_pull_app(g, app, P, cs);
     launch_xform(g, X, cs);
@@ -1148,7 +1231,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     const int trace = o.trace ? 1 : 0;
     RunCtl init{};
     init.max_iters = max_iters;
-    init.switch_mode = o.switch_mode == WEDGE_SWITCH_LEARNED ? WEDGE_SWITCH_THRESHOLD : o.switch_mode;
+    init.switch_mode = o.switch_mode;
     init.tau_bp = o.tau_bp;
     init.k = o.log2_coarsen;
     init.E = g->E;
@@ -1164,9 +1247,10 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words, g->rec,
                                               g->ctl, init);
-    k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl);
+    PullParams P = pull_params(g, trace, app);
+    k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, P.mlp,
+                                                    P.gf);
     count_launch(2);
-    PullParams P = pull_params(g, trace);
     XformParams X = xform_params(g, trace);
     launch_xform(g, X, s);
     WEDGE_TRY_CUDA(cudaGetLastError());
@@ -1364,6 +1448,90 @@ wedge_status wedge_graph_set_tuning(wedge_graph_t g, const wedge_tuning* t) {
 wedge_status wedge_graph_get_tuning(wedge_graph_t g, wedge_tuning* out) {
     if (!g || !out) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
     *out = g->tuning;
+    return WEDGE_OK;
+}
+
+// Candidate-timing trace (training data of the learned switch; not in the
+// paper).  Runs `app` with the threshold policy; before each pull it times
+// every candidate (transformation + pull, CUDA events) from the same
+// snapshotted state, then restores the state and advances with the
+// threshold's choice.
+wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t root, const wedge_opts* opts_in,
+                                    uint32_t max_iters, float* h_features, float* h_ms, uint32_t* h_chosen,
+                                    uint32_t cap, uint32_t* n_iters, wedge_stream_t stream) {
+    if (!g || !h_features || !h_ms || !h_chosen || !n_iters) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (app != WEDGE_BFS && app != WEDGE_CC && app != WEDGE_SSSP)
+        return set_error(WEDGE_ERR_INVALID_ARG, "app must be BFS, CC or SSSP");
+    if (app != WEDGE_CC && root >= g->V) return set_error(WEDGE_ERR_INVALID_ARG, "root out of range");
+    if (app == WEDGE_SSSP && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
+    wedge_opts o;
+    if (opts_in) o = *opts_in;
+    else wedge_default_opts(app, &o);
+    WEDGE_TRY(check_opts(&o));
+    if (o.log2_coarsen >= kCandidates - 1) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 4");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->snap_vals) WEDGE_TRY(dev_alloc(g, (void**)&g->snap_vals, (uint64_t)g->V * 4));
+    const uint32_t limit = max_iters ? (max_iters < kDefaultMaxIters ? max_iters : kDefaultMaxIters)
+                                     : kDefaultMaxIters;
+    RunCtl init{};
+    init.max_iters = limit;
+    init.switch_mode = o.switch_mode == WEDGE_SWITCH_LEARNED ? WEDGE_SWITCH_THRESHOLD : o.switch_mode;
+    init.tau_bp = o.tau_bp;
+    init.k = o.log2_coarsen;
+    init.E = g->E;
+    PullParams P = pull_params(g, 0, app);
+    P.mlp = nullptr;
+    XformParams X = xform_params(g, 0);
+    k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb,
+                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init);
+    k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
+                                                    P.gf);
+    count_launch(2);
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    const uint64_t vbytes = (uint64_t)g->V * 4;
+    uint32_t t = 0;
+    for (; t < cap; ++t) {
+        RunCtl hc;
+        IterRec hr;
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(&hc, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(&hr, g->rec + t, sizeof(IterRec), cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+        if (hc.done || hc.it != t) break;
+        for (int c = 0; c < kCandidates; ++c)
+            mlp_features(P.gf, (double)g->E, hr.nfront, (double)hr.fullness, hr.rowsum, t, c,
+                         h_features + ((size_t)t * kCandidates + c) * kMlpIn);
+        h_chosen[t] = hr.mode ? hr.k + 1 : 0;
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(g->snap_vals, g->vals, vbytes, cudaMemcpyDeviceToDevice, s));
+        for (int c = 0; c <= kCandidates; ++c) {
+            // c < kCandidates: time candidate c; c == kCandidates: advance
+            IterRec cr = hr;
+            if (c < kCandidates) {
+                cr.mode = c > 0;
+                cr.k = c > 0 ? (unsigned)(c - 1) : hr.k;
+            }
+            WEDGE_TRY_CUDA(cudaMemcpyAsync(g->vals, g->snap_vals, vbytes, cudaMemcpyDeviceToDevice, s));
+            k_ctl_init<<<1, 32, 0, s>>>(g->ctl, hc);
+            k_rec_set<<<1, 32, 0, s>>>(g->rec, t, cr);
+            count_launch(2);
+            P.decide = c == kCandidates ? 1 : 0;
+            WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
+            launch_xform(g, X, s);
+            launch_pull_app(g, app, P, s);
+            WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
+            WEDGE_TRY_CUDA(cudaGetLastError());
+            if (c < kCandidates) {
+                WEDGE_TRY_CUDA(cudaEventSynchronize(g->ev1));
+                float ms = 0.f;
+                WEDGE_TRY_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+                h_ms[(size_t)t * kCandidates + c] = ms;
+            }
+        }
+    }
+    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+    *n_iters = t;
+    g->last_stream = s;
+    WEDGE_TRY_CUDA(cudaMemcpy(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost));
     return WEDGE_OK;
 }
 

@@ -184,6 +184,14 @@ __global__ void k_pieces_total(const uint32_t* __restrict__ rowlen, uint32_t V,
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
 }
 
+__global__ void k_max_u32(const uint32_t* __restrict__ a, uint32_t n, unsigned* __restrict__ out) {
+    unsigned m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, a[i]);
+    for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, d));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_rowlen_from_off(const uint32_t* __restrict__ eoff, uint32_t V, uint32_t* __restrict__ rowlen) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V;
          v += (uint64_t)gridDim.x * blockDim.x)
@@ -264,6 +272,8 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->acc);
     dev_free(g->rank);
     dev_free(g->split_bm);
+    dev_free(g->mlp_bf16);
+    dev_free(g->snap_vals);
     for (auto& e : g->loop_exec)
         if (e) cudaGraphExecDestroy(e);
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
@@ -398,6 +408,20 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
             k_eidx_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, knz, g->eidx);
             count_launch();
         }
+    }
+    // largest out-degree (a statistic of the learned switch's features)
+    {
+        unsigned* d_max = nullptr;
+        WEDGE_TRY(dev_alloc(nullptr, (void**)&d_max, 4));
+        cudaError_t e = cudaMemsetAsync(d_max, 0, 4, s);
+        if (e == cudaSuccess) {
+            k_max_u32<<<grid_for(V, 256, sms), 256, 0, s>>>(g->outdeg, V, d_max);
+            count_launch();
+            e = cudaMemcpyAsync(&g->max_outdeg, d_max, 4, cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        dev_free(d_max);
+        if (e != cudaSuccess) return cuda_error(e, "max out-degree");
     }
     // work pieces bound: sum ceil(|row| / 32)
     unsigned long long* d_total = nullptr;

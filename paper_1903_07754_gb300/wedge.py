@@ -66,8 +66,10 @@ EXPORTS = [
     "wedge_graph_copy_edge_index", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
     "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr", "wedge_get_trace", "wedge_kernel_launches",
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
-    "wedge_frontier_transform_noalloc",
+    "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
+    "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates",
 ]
+MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
 _lib = None
 
@@ -99,6 +101,13 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(wedge_stats), P]),
         "wedge_get_trace": (st, [P, ctypes.POINTER(wedge_iter_record), u32, ctypes.POINTER(u32)]),
         "wedge_graph_set_tuning": (st, [P, ctypes.POINTER(wedge_tuning)]),
+        "wedge_mlp_forward": (st, [P, P, u32, P, P]),
+        "wedge_mlp_forward_bf16": (st, [P, P, u32, P, P]),
+        "wedge_mlp_loss_grad": (st, [P, P, P, u32, P, P, P]),
+        "wedge_mlp_adam": (st, [P, P, P, P, u32, ctypes.c_float, P]),
+        "wedge_set_cost_model": (st, [P, P]),
+        "wedge_trace_candidates": (st, [P, i32, u32, ctypes.POINTER(wedge_opts), u32, P, P, P, u32,
+                                        ctypes.POINTER(u32), P]),
         "wedge_graph_get_tuning": (st, [P, ctypes.POINTER(wedge_tuning)]),
         "wedge_kernel_launches": (u64, []),
         "wedge_last_error": (ctypes.c_char_p, []),
@@ -242,6 +251,44 @@ def wedge_graph_get_tuning(handle) -> dict:
     t = wedge_tuning()
     _check(load().wedge_graph_get_tuning(handle, ctypes.byref(t)))
     return {"dense_loader": t.dense_loader, "blocks_per_sm": t.blocks_per_sm}
+
+
+def wedge_mlp_forward(params, x, n, y, stream=None):
+    _check(load().wedge_mlp_forward(_ptr(params), _ptr(x), int(n), _ptr(y), _stream(stream)))
+
+
+def wedge_mlp_forward_bf16(params, x, n, y, stream=None):
+    _check(load().wedge_mlp_forward_bf16(_ptr(params), _ptr(x), int(n), _ptr(y), _stream(stream)))
+
+
+def wedge_mlp_loss_grad(params, x, t, n, grad, loss, stream=None):
+    _check(load().wedge_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), int(n), _ptr(grad), _ptr(loss),
+                                      _stream(stream)))
+
+
+def wedge_mlp_adam(params, grad, m, v, step, lr, stream=None):
+    _check(load().wedge_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)))
+
+
+def wedge_set_cost_model(handle, params):
+    """params: FP32 array of MLP_PARAMS (host numpy or device tensor), or None."""
+    if params is not None and isinstance(params, np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().wedge_set_cost_model(handle, _ptr(params)))
+
+
+def wedge_trace_candidates(handle, app, root=0, opts=None, max_iters=0, cap=4096, stream=None):
+    """Returns (features [n, 6, 12], ms [n, 6], chosen [n]) as numpy arrays."""
+    a = APP_IDS[app] if isinstance(app, str) else int(app)
+    feat = np.zeros((cap, MLP_CANDIDATES, MLP_FEATURES), dtype=np.float32)
+    ms = np.zeros((cap, MLP_CANDIDATES), dtype=np.float32)
+    chosen = np.zeros(cap, dtype=np.uint32)
+    n = ctypes.c_uint32()
+    _check(load().wedge_trace_candidates(handle, a, int(root), _opts(opts), int(max_iters), feat.ctypes.data,
+                                         ms.ctypes.data, chosen.ctypes.data, int(cap), ctypes.byref(n),
+                                         _stream(stream)))
+    k = n.value
+    return feat[:k].copy(), ms[:k].copy(), chosen[:k].copy()
 
 
 def wedge_kernel_launches() -> int:
