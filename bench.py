@@ -309,6 +309,21 @@ def main():
         t_d = time_fn(lambda: fn(odn))
         per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "dense_pull_ms": t_d,
                          "speedup_vs_dense_pull": t_d / t_w}
+    # learned switch (cost model trained by paper_1903_07754_gb300.train_cost_model)
+    from paper_1903_07754_gb300 import costmodel
+    if os.path.exists(costmodel.DEFAULT_MODEL):
+        params = costmodel.load_params()
+        wedge.wedge_set_cost_model(G.handle, params)
+        wedge.wedge_set_cost_model(S.handle, params)
+        for name, (fn, ow, _) in runs.items():
+            ol = wedge.wedge_default_opts(name)
+            ol.switch_mode = wedge.SWITCH_LEARNED
+            t_l = time_fn(lambda: fn(ol))
+            per_app[name]["learned_ms"] = t_l
+            per_app[name]["speedup_learned_vs_threshold"] = per_app[name]["ms"] / t_l
+            per_app[name]["speedup_learned_vs_dense_pull"] = per_app[name]["dense_pull_ms"] / t_l
+        wedge.wedge_set_cost_model(G.handle, None)
+        wedge.wedge_set_cost_model(S.handle, None)
     t_pr = time_fn(lambda: wedge.wedge_run_pr(G.handle, rank_t, PR_ITERS, DAMPING, None, False))
     per_app["pr"] = {"ms": t_pr, "gteps": edges["pr"] / (t_pr / 1e3) / 1e9}
     st = step(want_stats=True)
