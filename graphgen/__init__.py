@@ -206,6 +206,30 @@ def random_graph(V: int, m: int, seed: int, undirected: bool = False) -> Graph:
     return from_edges(V, s, d, undirected=undirected, name=f"random-{V}-{m}-{seed}")
 
 
+def block_diagonal(graphs) -> tuple[Graph, np.ndarray]:
+    """Concatenates graphs into one CSC with disjoint vertex ranges (graph i's
+    vertex v becomes base[i] + v).  Returns (graph, base offsets)."""
+    base = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        base[i + 1] = base[i] + g.V
+    V = int(base[-1])
+    E = sum(g.E for g in graphs)
+    if E >= 2**32 - 1 or V >= 2**32:
+        raise ValueError("batch too large for 32-bit ids")
+    offsets = np.empty(V + 1, dtype=np.uint32)
+    src = np.empty(E, dtype=np.uint32)
+    w = np.empty(E, dtype=np.uint32) if all(g.w is not None for g in graphs) else None
+    e0 = 0
+    for i, g in enumerate(graphs):
+        offsets[base[i]:base[i + 1]] = g.offsets[:-1].astype(np.int64) + e0
+        src[e0:e0 + g.E] = g.src.astype(np.int64) + base[i]
+        if w is not None:
+            w[e0:e0 + g.E] = g.w
+        e0 += g.E
+    offsets[V] = E
+    return Graph(V, offsets, src, w, f"batch-{len(graphs)}", False, dict(kind="block-diagonal")), base[:-1]
+
+
 def roots(g: Graph, count: int, seed: int = SEED_ROOTS) -> np.ndarray:
     """`count` roots uniform (with replacement) over vertices with outdeg > 0."""
     od = g.outdeg()

@@ -292,6 +292,27 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                                     uint32_t max_iters, float* h_features, float* h_ms, uint32_t* h_chosen,
                                     uint32_t cap, uint32_t* n_iters, wedge_stream_t stream);
 
+/* ---- Batched BFS (not in the paper) ------------------------------------
+ * Up to 64 BFS queries in one run (multi-source BFS): each vertex carries a
+ * 64-bit mask of the queries that reached it and of those for which it is in
+ * the current frontier.  The union of the queries' frontiers drives the
+ * fullness decision and the Wedge Frontier (Sections 3.3, 3.4), so every
+ * pull serves all queries.  The loop runs in one persistent cooperative
+ * launch (bounded grid barriers), captured in a CUDA graph per
+ * (queries, roots, output, options).
+ *  roots[nroots] (host or device) with root_query[nroots] giving the query
+ *  of each root (NULL: root i is query i); several roots may share a query
+ *  (a query's level is then the distance to the nearest of its roots, as
+ *  for graphs concatenated block-diagonally, one root per graph).
+ *  d_levels (device, V * nqueries uint32): vertex-major,
+ *  d_levels[v * nqueries + q] = hop distance of v from query q's roots
+ *  (0xFFFFFFFF if unreached).  opts as for wedge_run_bfs (learned switch
+ *  not used).  Errors: INVALID_ARG (ids, sizes, host output), TIMEOUT,
+ *  MAX_ITERS (when stats != NULL), CUDA. */
+wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
+                                 uint32_t nroots, uint32_t nqueries, uint32_t* d_levels,
+                                 const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+
 /* Per-iteration records of the last run of g (needs opts.trace).  Copies up
  * to cap records into host memory, sets *n to the number available.
  * Synchronises the stream of that run. */

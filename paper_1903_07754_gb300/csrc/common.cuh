@@ -134,6 +134,18 @@ struct wedge_graph {
     bool has_model = false;
     uint32_t max_outdeg = 0;
     uint32_t* snap_vals = nullptr;   // candidate-timing trace: value snapshot
+    // batched BFS
+    unsigned long long* ms_fb[2] = {nullptr, nullptr};
+    unsigned long long* ms_seen = nullptr;
+    uint32_t* ms_roots = nullptr;    // roots then their query ids
+    uint32_t ms_cap = 0;
+    unsigned* ms_bar = nullptr;
+    int ms_blocks = 0;
+    cudaGraphExec_t ms_exec = nullptr;
+    uint32_t ms_exec_q = 0, ms_exec_n = 0;
+    uint32_t* ms_exec_levels = nullptr;
+    uint32_t ms_exec_key[4] = {0, 0, 0, 0};
+    bool ms_graph_failed = false;
     uint64_t device_bytes = 0;
     int num_sms = 0;
     size_t smem_per_sm = 0;

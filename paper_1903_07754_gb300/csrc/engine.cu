@@ -25,7 +25,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 #define WEDGE_DIRECT_MIN_BLOCKS 5
 #endif
 constexpr int kDirectMinBlocks = WEDGE_DIRECT_MIN_BLOCKS;
-enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3 };
+enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3, kMSBFS = 4 };
 
 // ------------------------------------------------------------------------
 // Kernel parameter blocks
@@ -53,6 +53,11 @@ struct PullParams {
     int dense_tma;               // dense pulls stage tiles with bulk copies
     const __nv_bfloat16* mlp;    // learned switch weights (nullptr: threshold)
     GraphFeat gf;                // graph statistics of the learned switch's features
+    // batched BFS: per-vertex 64-bit query masks and the vertex-major levels
+    unsigned long long* fb[2];   // frontier masks by iteration parity
+    unsigned long long* seen;    // queries that have reached each vertex
+    uint32_t* levels;            // levels[v * Q + q]
+    uint32_t Q;
 };
 
 struct XformParams {
@@ -99,6 +104,13 @@ struct Traits<kSSSP> {  // distance, min
     static __device__ __forceinline__ bool keep(T a) { return a != kInf; }
 };
 template <>
+struct Traits<kMSBFS> {  // union of the sources' frontier query masks, OR
+    using T = unsigned long long;
+    static __device__ __forceinline__ T neutral() { return 0ull; }
+    static __device__ __forceinline__ T op(T a, T b) { return a | b; }
+    static __device__ __forceinline__ bool keep(T a) { return a != 0ull; }
+};
+template <>
 struct Traits<kPR> {  // fixed-point contribution, sum (every segment is stored)
     using T = unsigned long long;
     static __device__ __forceinline__ T neutral() { return 0ull; }
@@ -108,11 +120,14 @@ struct Traits<kPR> {  // fixed-point contribution, sum (every segment is stored)
 
 template <int APP>
 __device__ __forceinline__ typename Traits<APP>::T candidate(const PullParams& P, const uint32_t* cur, uint32_t u,
-                                                             uint32_t w) {
+                                                             uint32_t w, unsigned it) {
     if constexpr (APP == kBFS) {
         return (__ldg(cur + (u >> 5)) >> (u & 31)) & 1u;
     } else if constexpr (APP == kCC) {
         return P.vals[u];
+    } else if constexpr (APP == kMSBFS) {
+        // written earlier in the same persistent launch: read through L2
+        return __ldcg(((it & 1) ? P.fb[1] : P.fb[0]) + u);
     } else if constexpr (APP == kSSSP) {
         const uint32_t d = P.vals[u];
         if (d == kInf) return kInf;
@@ -243,7 +258,7 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
     T run = Tr::neutral();
 #pragma unroll
     for (int i = 0; i < kEPL; ++i) {
-        const T cv = (i < nvalid) ? candidate<APP>(P, cur, sv[i], wv[i]) : Tr::neutral();
+        const T cv = (i < nvalid) ? candidate<APP>(P, cur, sv[i], wv[i], it) : Tr::neutral();
         run = ((brk >> i) & 1u) ? cv : Tr::op(run, cv);
         inc[i] = run;
     }
@@ -330,6 +345,28 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
                 P.vals[dv] = it + 1;
                 act = set_bit(next, dv);
             }
+        } else if constexpr (APP == kMSBFS) {
+            // queries reaching dv for the first time take level it+1
+            unsigned long long* nxt = (it & 1) ? P.fb[0] : P.fb[1];
+            unsigned long long fresh, prev;
+            if (excl) {
+                const unsigned long long old = __ldcg(P.seen + dv);
+                fresh = m & ~old;
+                if (fresh) P.seen[dv] = old | fresh;
+            } else {
+                fresh = m & ~atomicOr(P.seen + dv, m);
+            }
+            if (fresh) {
+                for (unsigned long long b = fresh; b; b &= b - 1)
+                    P.levels[(size_t)dv * P.Q + (__ffsll((long long)b) - 1)] = it + 1;
+                if (excl) {
+                    prev = __ldcg(nxt + dv);
+                    nxt[dv] = prev | fresh;
+                } else {
+                    prev = atomicOr(nxt + dv, fresh);
+                }
+                act = prev == 0ull && set_bit(next, dv);
+            }
         } else if constexpr (APP == kPR) {
             if (excl) P.acc[dv] = m;
             else if (m) atomicAdd(P.acc + dv, m);
@@ -401,6 +438,94 @@ __device__ __forceinline__ void load_lane_edges(const PullParams& P, unsigned lo
     }
 }
 
+// Dense pull over all chunks with direct loads: warp gw of nw takes slices
+// gw, gw + nw, ...  The next slice's edges and chunk metadata are loaded
+// before the current slice is processed, so the stream overlaps the gathers.
+template <int APP>
+__device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned it, const uint32_t* cur,
+                                                  uint32_t* next, uint32_t* my_kid, typename Traits<APP>::T* my_val,
+                                                  Stats& st, unsigned long long gw, unsigned long long nw) {
+    const unsigned lane = threadIdx.x & 31, q = lane >> 2, sub = lane & 3;
+    const unsigned long long nslices = (P.NC + kSliceC - 1) / kSliceC;
+    uint32_t sv[kEPL], wv[kEPL];
+    uint2 meta = make_uint2(0u, 0u);
+    unsigned next_head = 1u;
+    int nvalid = 0;
+    unsigned long long c = 0;
+    auto fetch = [&](unsigned long long sl) {
+        c = sl * kSliceC + q;
+        const unsigned long long e_lane = c * 32 + 8 * sub;
+        nvalid = 0;
+        meta = make_uint2(0u, 0u);
+        next_head = 1u;
+        if (sl < nslices && c < P.NC) {
+            const long long left = (long long)P.E - (long long)e_lane;
+            nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
+            meta = __ldg(P.cmeta + c);
+            next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
+        }
+        load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
+    };
+    if (gw < nslices) fetch(gw);
+    for (unsigned long long sl = gw; sl < nslices; sl += nw) {
+        uint32_t cs[kEPL], cw[kEPL];
+#pragma unroll
+        for (int i = 0; i < kEPL; ++i) {
+            cs[i] = sv[i];
+            cw[i] = wv[i];
+        }
+        const uint2 cmeta = meta;
+        const unsigned cnh = next_head;
+        const int cnv = nvalid;
+        const unsigned long long cc = c;
+        fetch(sl + nw);
+        process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st);
+    }
+}
+
+// Pull over the Wedge Frontier list: slices of 8 listed chunks (list entry
+// b at coarsening k stands for chunks b*2^k .. b*2^k + 2^k - 1), loaded
+// directly; the Wedge bitmap words of the entries are zeroed as consumed.
+template <int APP>
+__device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, unsigned k, unsigned nchunks,
+                                            const uint32_t* cur, uint32_t* next, uint32_t* my_kid,
+                                            typename Traits<APP>::T* my_val, Stats& st, unsigned long long gw,
+                                            unsigned long long nw) {
+    const unsigned lane = threadIdx.x & 31, q = lane >> 2, sub = lane & 3;
+    const unsigned long long nunits = (unsigned long long)nchunks << k;
+    const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
+    const unsigned long long kmask = (1ull << k) - 1;
+    for (unsigned long long sl = gw; sl < nslices; sl += nw) {
+        const unsigned long long j = sl * kSliceC + q;
+        bool uvalid = j < nunits;
+        unsigned long long c = 0;
+        if (uvalid) {
+            const uint32_t b = __ldcg(P.clist + (j >> k));
+            c = ((unsigned long long)b << k) | (j & kmask);
+            uvalid = c < P.NC;
+            if (uvalid && P.wb && sub == 0 && (j & kmask) == 0) P.wb[b >> 5] = 0u;
+        }
+        const unsigned long long cprev = __shfl_up_sync(kFull, c, 4);
+        const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 4);
+        const bool contig = q > 0 && pvalid && uvalid && c == cprev + 1;
+        const unsigned long long e_lane = c * 32 + 8 * sub;
+        int nvalid = 0;
+        if (uvalid) {
+            const long long left = (long long)P.E - (long long)e_lane;
+            nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
+        }
+        uint32_t sv[kEPL], wv[kEPL];
+        load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
+        uint2 meta = make_uint2(0u, 0u);
+        unsigned next_head = 1u;
+        if (uvalid) {
+            meta = __ldg(P.cmeta + c);
+            next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
+        }
+        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st);
+    }
+}
+
 template <int APP, bool TMA>
 __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDirectMinBlocks) k_pull(const PullParams P) {
     using T = typename Traits<APP>::T;
@@ -447,51 +572,12 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
     const uint32_t* cur = P.bm[it & 1];
     uint32_t* next = P.bm[(it + 1) & 1];
     Stats st{0ull, 0u, 0u};
-    const unsigned q = lane >> 2, sub = lane & 3;
+    const unsigned q = lane >> 2;
 
     if constexpr (!TMA) {
-    if (mode == 0) {
-        // ---- dense, direct: every warp streams 256-edge slices ----
-        // The next slice's edges and chunk metadata are loaded before the
-        // current slice is processed, so the stream overlaps the gathers.
-        const unsigned long long nslices = (P.NC + kSliceC - 1) / kSliceC;
-        const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
-        const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
-        uint32_t sv[kEPL], wv[kEPL];
-        uint2 meta = make_uint2(0u, 0u);
-        unsigned next_head = 1u;
-        int nvalid = 0;
-        unsigned long long c = 0;
-        auto fetch = [&](unsigned long long sl) {
-            c = sl * kSliceC + q;
-            const unsigned long long e_lane = c * 32 + 8 * sub;
-            nvalid = 0;
-            meta = make_uint2(0u, 0u);
-            next_head = 1u;
-            if (sl < nslices && c < P.NC) {
-                const long long left = (long long)P.E - (long long)e_lane;
-                nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
-                meta = __ldg(P.cmeta + c);
-                next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
-            }
-            load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
-        };
-        if (gw < nslices) fetch(gw);
-        for (unsigned long long sl = gw; sl < nslices; sl += nw) {
-            uint32_t cs[kEPL], cw[kEPL];
-#pragma unroll
-            for (int i = 0; i < kEPL; ++i) {
-                cs[i] = sv[i];
-                cw[i] = wv[i];
-            }
-            const uint2 cmeta = meta;
-            const unsigned cnh = next_head;
-            const int cnv = nvalid;
-            const unsigned long long cc = c;
-            fetch(sl + nw);
-            process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st);
-        }
-    }
+        if (mode == 0)
+            pull_dense_direct<APP>(P, it, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
+                                   (unsigned long long)gridDim.x * kCW);
     }
     if (TMA && mode == 0) {
         // ---- dense, staged: tiles of kTileC chunks streamed by bulk copies ----
@@ -571,43 +657,9 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
             }
         }
     }
-    if (mode != 0 && warp < kCW) {
-        // ---- sparse: slices of 8 listed chunks, loaded directly ----
-        const unsigned long long nunits = (unsigned long long)nchunks << k;
-        const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
-        const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
-        const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
-        const unsigned long long kmask = (1ull << k) - 1;
-        for (unsigned long long sl = gw; sl < nslices; sl += nw) {
-            const unsigned long long j = sl * kSliceC + q;
-            bool uvalid = j < nunits;
-            unsigned long long c = 0;
-            if (uvalid) {
-                const uint32_t b = __ldg(P.clist + (j >> k));
-                c = ((unsigned long long)b << k) | (j & kmask);
-                uvalid = c < P.NC;
-                if (uvalid && P.wb && sub == 0 && (j & kmask) == 0) P.wb[b >> 5] = 0u;  // consume the bit's word
-            }
-            const unsigned long long cprev = __shfl_up_sync(kFull, c, 4);
-            const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 4);
-            const bool contig = q > 0 && pvalid && uvalid && c == cprev + 1;
-            const unsigned long long e_lane = c * 32 + 8 * sub;
-            int nvalid = 0;
-            if (uvalid) {
-                const long long left = (long long)P.E - (long long)e_lane;
-                nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
-            }
-            uint32_t sv[kEPL], wv[kEPL];
-            load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
-            uint2 meta = make_uint2(0u, 0u);
-            unsigned next_head = 1u;
-            if (uvalid) {
-                meta = __ldg(P.cmeta + c);
-                next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
-            }
-            process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st);
-        }
-    }
+    if (mode != 0 && warp < kCW)
+        pull_sparse<APP>(P, it, k, nchunks, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
+                         (unsigned long long)gridDim.x * kCW);
 
     if constexpr (APP != kPR) {
 #pragma unroll
@@ -657,38 +709,20 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
 //     entry b at coarsening k) and append every newly set bit to the list:
 //     the bitmap removes duplicates (Section 4).
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
-    RunCtl* C = X.ctl;
-    const uint32_t* bm;
-    IterRec* r;
-    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
-    if (X.standalone_k >= 0) {
-        bm = X.bm_in;
-        r = X.rec;
-    } else {
-        if (C->done) return;
-        const unsigned it = C->it;
-        if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
-        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
-        for (unsigned long long i = tid; i < X.bm_words; i += nth) clr[i] = 0u;
-        if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
-            reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
-        r = X.rec + it;
-        if (r->mode == 0) return;
-        bm = (it & 1) ? X.bm[1] : X.bm[0];
-    }
+// Warp-level scan of bitmap words [gw*32, ...) step nw*32: pieces of the
+// active vertices' edge-index rows, one reservation per warp on *npieces.
+__device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V, unsigned long long words,
+                                                 const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                 unsigned* npieces, unsigned long long gw, unsigned long long nw) {
     const unsigned lane = threadIdx.x & 31;
-    const unsigned long long gw = tid >> 5, nw = nth >> 5;
-    const uint32_t V = X.V;
-    for (unsigned long long base = gw * 32; base < X.bm_words; base += nw * 32) {
+    for (unsigned long long base = gw * 32; base < words; base += nw * 32) {
         const unsigned long long wi = base + lane;
-        uint32_t word = wi < X.bm_words ? bm[wi] : 0u;
-        if (wi == X.bm_words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
+        uint32_t word = wi < words ? __ldcg(bm + wi) : 0u;
+        if (wi == words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
         unsigned np = 0;
         for (uint32_t w = word; w; w &= w - 1) {
             const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
-            np += (__ldg(X.eidx_off + u + 1) - __ldg(X.eidx_off + u) + 31u) >> 5;
+            np += (__ldg(eidx_off + u + 1) - __ldg(eidx_off + u) + 31u) >> 5;
         }
         unsigned incl = np;
 #pragma unroll
@@ -699,41 +733,26 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
         const unsigned total = __shfl_sync(kFull, incl, 31);
         if (!total) continue;
         unsigned slot = 0;
-        if (lane == 31) slot = atomicAdd(&r->npieces, total);
+        if (lane == 31) slot = atomicAdd(npieces, total);
         slot = __shfl_sync(kFull, slot, 31) + incl - np;
         for (uint32_t w = word; w; w &= w - 1) {
             const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
-            const uint32_t rb = __ldg(X.eidx_off + u), rl = __ldg(X.eidx_off + u + 1) - rb;
-            for (uint32_t qq = 0; qq < rl; qq += 32) X.pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
+            const uint32_t rb = __ldg(eidx_off + u), rl = __ldg(eidx_off + u + 1) - rb;
+            for (uint32_t qq = 0; qq < rl; qq += 32) pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
         }
     }
 }
 
-__global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
-    RunCtl* C = X.ctl;
-    unsigned n, k;
-    unsigned* count;
-    unsigned it = 0;
-    if (X.standalone_k >= 0) {
-        n = __ldcg(&X.rec[0].npieces);
-        k = (unsigned)X.standalone_k;
-        count = X.count_out;
-    } else {
-        if (C->done) return;
-        it = C->it;
-        const IterRec* r = X.rec + it;
-        if (r->mode == 0) return;
-        n = r->npieces;
-        k = r->k;
-        count = &X.rec[it].nchunks;
-    }
+// Warp-level expansion of n pieces: Wedge bitmap bits (entry = chunk >> k),
+// fresh bits appended to list with a warp-aggregated reservation on *count.
+__device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigned n, unsigned k,
+                                                    const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
+                                                    unsigned* count, unsigned long long gw, unsigned long long nw) {
     const unsigned lane = threadIdx.x & 31;
-    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
         const unsigned long long idx = base + lane;
-        const uint2 pc = idx < n ? X.pieces[idx] : make_uint2(0u, 0u);
+        const uint2 pc = idx < n ? __ldcg(pieces + idx) : make_uint2(0u, 0u);
         unsigned incl = pc.y;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -757,9 +776,9 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
             bool fresh = false;
             uint32_t b = 0;
             if (act) {
-                b = __ldg(X.eidx + st + (e - ex)) >> k;
+                b = __ldg(eidx + st + (e - ex)) >> k;
                 const uint32_t bit = 1u << (b & 31);
-                fresh = (atomicOr(X.wb + (b >> 5), bit) & bit) == 0;
+                fresh = (atomicOr(wb + (b >> 5), bit) & bit) == 0;
             }
             const unsigned m = __ballot_sync(kFull, fresh);
             if (m) {
@@ -767,10 +786,57 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
                 unsigned slot = 0;
                 if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
                 slot = __shfl_sync(kFull, slot, leader);
-                if (fresh) X.clist[slot + __popc(m & lt_mask)] = b;
+                if (fresh) list[slot + __popc(m & lt_mask)] = b;
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
+    RunCtl* C = X.ctl;
+    const uint32_t* bm;
+    IterRec* r;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    if (X.standalone_k >= 0) {
+        bm = X.bm_in;
+        r = X.rec;
+    } else {
+        if (C->done) return;
+        const unsigned it = C->it;
+        if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
+        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
+        for (unsigned long long i = tid; i < X.bm_words; i += nth) clr[i] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
+            reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
+        r = X.rec + it;
+        if (r->mode == 0) return;
+        bm = (it & 1) ? X.bm[1] : X.bm[0];
+    }
+    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+}
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
+    RunCtl* C = X.ctl;
+    unsigned n, k;
+    unsigned* count;
+    unsigned it = 0;
+    if (X.standalone_k >= 0) {
+        n = __ldcg(&X.rec[0].npieces);
+        k = (unsigned)X.standalone_k;
+        count = X.count_out;
+    } else {
+        if (C->done) return;
+        it = C->it;
+        const IterRec* r = X.rec + it;
+        if (r->mode == 0) return;
+        n = r->npieces;
+        k = r->k;
+        count = &X.rec[it].nchunks;
+    }
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
@@ -867,6 +933,185 @@ __global__ void k_loop_ctl(RunCtl* C, cudaGraphConditionalHandle h) {
         const unsigned n = ++C->loops;
         const bool more = !C->done && n < C->max_iters + 2;
         cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Batched BFS (not in the paper): up to 64 traversals at once with a 64-bit
+// query mask per vertex (multi-source BFS: a source's frontier mask is the
+// set of queries that reached it in the previous iteration).  The union of
+// the queries' frontiers drives the fullness decision and the Wedge
+// Frontier, so one pull serves all queries.  The whole loop runs in one
+// persistent cooperative launch; phases are separated by a bounded grid
+// barrier.
+// ------------------------------------------------------------------------
+
+// Data that blocks of this one launch write and later read back (frontier
+// and seen masks, bitmaps, the Wedge list, work pieces) is read with
+// ld.global.cg: L1 is not coherent across SMs inside a launch.
+//
+// Grid-wide barrier on (count, generation).  Returns false (and records
+// kStatusTimeout) if the other blocks do not arrive within kWaitNs.
+__device__ bool grid_sync(unsigned* count, unsigned* gen, unsigned* status) {
+    __shared__ unsigned s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ok = 1;
+        volatile unsigned* vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            for (unsigned n = 1; *vgen == g; ++n) {
+                if ((n & 127u) == 0 && gtimer() - t0 > kWaitNs) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned*)status & kStatusTimeout) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void k_msbfs_clear(uint32_t V, unsigned long long* fb0, unsigned long long* fb1, unsigned long long* seen,
+                              uint32_t* bm0, uint32_t* bm1, uint32_t* wb, unsigned long long wb_words, IterRec* rec,
+                              RunCtl* C, RunCtl init, unsigned* bar) {
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long v = tid; v < V; v += nth) {
+        fb0[v] = 0ull;
+        fb1[v] = 0ull;
+        seen[v] = 0ull;
+    }
+    const unsigned long long words = ((unsigned long long)V + 31) / 32;
+    for (unsigned long long i = tid; i < words; i += nth) {
+        bm0[i] = 0u;
+        bm1[i] = 0u;
+    }
+    for (unsigned long long i = tid; i < wb_words; i += nth) wb[i] = 0u;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 2 * sizeof(IterRec) / 4) reinterpret_cast<unsigned*>(rec)[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            *C = init;
+            bar[0] = 0u;
+            bar[1] = 0u;
+        }
+    }
+}
+
+__global__ void k_msbfs_roots(const uint32_t* __restrict__ roots, const uint32_t* __restrict__ rq, uint32_t nroots,
+                              uint32_t Q, unsigned long long* fb0, unsigned long long* seen, uint32_t* levels,
+                              uint32_t* bm0) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += gridDim.x * blockDim.x) {
+        const uint32_t v = roots[i], q = rq[i];
+        const unsigned long long bit = 1ull << q;
+        atomicOr(fb0 + v, bit);
+        atomicOr(seen + v, bit);
+        levels[(size_t)v * Q + q] = 0u;
+        atomicOr(bm0 + (v >> 5), 1u << (v & 31));
+    }
+}
+
+__global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const XformParams X, unsigned* bar) {
+    using T = unsigned long long;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long s_F;
+    __shared__ unsigned s_n, s_row;
+    RunCtl* C = P.ctl;
+    if (C->done) return;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* s_val = reinterpret_cast<T*>(smem);
+    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
+    uint32_t* my_kid = s_kid + warp * kSliceE;
+    T* my_val = s_val + warp * kSliceE;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
+    const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long words = ((unsigned long long)X.V + 31) / 32;
+    unsigned it = C->it;
+    unsigned mode = P.rec[it].mode, k = P.rec[it].k;
+    for (;;) {
+        // ---- pull it ----
+        if (threadIdx.x == 0) {
+            s_F = 0;
+            s_n = 0;
+            s_row = 0;
+        }
+        __syncthreads();
+        Stats st{0ull, 0u, 0u};
+        const uint32_t* cur = (it & 1) ? P.bm[1] : P.bm[0];
+        uint32_t* next = (it & 1) ? P.bm[0] : P.bm[1];
+        if (mode == 0)
+            pull_dense_direct<kMSBFS>(P, it, cur, next, my_kid, my_val, st, gw, nw);
+        else
+            pull_sparse<kMSBFS>(P, it, k, __ldcg(&P.rec[it].nchunks), cur, next, my_kid, my_val, st, gw, nw);
+        for (int d = 16; d > 0; d >>= 1) {
+            st.F += __shfl_down_sync(kFull, st.F, d);
+            st.n += __shfl_down_sync(kFull, st.n, d);
+            st.row += __shfl_down_sync(kFull, st.row, d);
+        }
+        if (lane == 0 && st.n) {
+            atomicAdd(&s_F, st.F);
+            atomicAdd(&s_n, st.n);
+            atomicAdd(&s_row, st.row);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_n) {
+            atomicAdd(&P.rec[it + 1].fullness, s_F);
+            atomicAdd(&P.rec[it + 1].nfront, s_n);
+            atomicAdd(&P.rec[it + 1].rowsum, s_row);
+        }
+        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        // ---- decision: every block computes it from the same sums ----
+        const unsigned nit = it + 1;
+        const unsigned long long F = __ldcg(&P.rec[nit].fullness);
+        const unsigned nf = __ldcg(&P.rec[nit].nfront);
+        unsigned sparse;
+        if (C->switch_mode == WEDGE_SWITCH_ALWAYS_DENSE) sparse = 0;
+        else if (C->switch_mode == WEDGE_SWITCH_ALWAYS_SPARSE) sparse = 1;
+        else sparse = (F * 10000ull < (unsigned long long)C->tau_bp * C->E) ? 1u : 0u;
+        const bool done = nf == 0 || nit >= C->max_iters;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            P.rec[nit].mode = sparse;
+            P.rec[nit].k = C->k;
+            C->it = nit;
+            if (done) {
+                C->done = 1;
+                if (nf) C->status |= kStatusMaxIters;
+            }
+        }
+        if (done) break;
+        // ---- retire frontier it (masks and bitmap), prepare the next ----
+        uint32_t* cbm = (it & 1) ? P.bm[1] : P.bm[0];
+        unsigned long long* cfr = (it & 1) ? P.fb[1] : P.fb[0];
+        for (unsigned long long wi = tid; wi < words; wi += nth) {
+            uint32_t w = __ldcg(cbm + wi);
+            if (!w) continue;
+            cbm[wi] = 0u;
+            for (; w; w &= w - 1) cfr[wi * 32 + __ffs(w) - 1] = 0ull;
+        }
+        if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
+            reinterpret_cast<unsigned*>(P.rec + nit + 1)[threadIdx.x] = 0u;
+        if (sparse) xform_scan_words(next, X.V, words, X.eidx_off, X.pieces, &P.rec[nit].npieces, gw, nw);
+        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        if (sparse)
+            xform_expand_pieces(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
+                                &P.rec[nit].nchunks, gw, nw);
+        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        it = nit;
+        mode = sparse;
+        k = C->k;
     }
 }
 
@@ -1267,6 +1512,74 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     return fill_stats(g, s, stats);
 }
 
+// Batched BFS: everything after the roots' upload, enqueued on s (also the
+// body of the captured graph).
+static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, uint32_t* levels, const RunCtl& init,
+                                  cudaStream_t s) {
+    WEDGE_TRY_CUDA(cudaMemsetAsync(levels, 0xFF, (size_t)g->V * Q * 4, s));
+    k_msbfs_clear<<<g->num_sms * 4, 256, 0, s>>>(g->V, g->ms_fb[0], g->ms_fb[1], g->ms_seen, g->bm[0], g->bm[1], g->wb,
+                                                 (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->ms_bar);
+    k_msbfs_roots<<<(nroots + 255) / 256, 256, 0, s>>>(g->ms_roots, g->ms_roots + g->ms_cap, nroots, Q, g->ms_fb[0],
+                                                       g->ms_seen, levels, g->bm[0]);
+    PullParams P = pull_params(g, 0, kBFS);
+    P.mlp = nullptr;
+    P.fb[0] = g->ms_fb[0];
+    P.fb[1] = g->ms_fb[1];
+    P.seen = g->ms_seen;
+    P.levels = levels;
+    P.Q = Q;
+    P.decide = 0;
+    XformParams X = xform_params(g, 0);
+    k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
+                                                    P.gf);
+    launch_xform(g, X, s);
+    count_launch(3);
+    void* args[] = {(void*)&P, (void*)&X, (void*)&g->ms_bar};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(g->ms_blocks);
+    cfg.blockDim = dim3(kCW * 32);
+    cfg.dynamicSmemBytes = pull_records_bytes<kMSBFS>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    WEDGE_TRY_CUDA(cudaLaunchKernelExC(&cfg, (const void*)k_msbfs, args));
+    count_launch();
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    return WEDGE_OK;
+}
+
+static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
+    const uint64_t V = g->V;
+    if (!g->ms_seen) {
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_seen, V * 8));
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_fb[0], V * 8));
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_fb[1], V * 8));
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_bar, 64));
+        const int smem = pull_records_bytes<kMSBFS>();
+        WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_msbfs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int n = 0;
+        WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_msbfs, kCW * 32, smem));
+        if (n < 1) return set_error(WEDGE_ERR_NOT_SUPPORTED, "batched BFS kernel does not fit on an SM");
+        g->ms_blocks = g->num_sms * n;  // every block co-resident (cooperative launch)
+    }
+    if (nroots > g->ms_cap) {
+        if (g->ms_exec) {
+            cudaGraphExecDestroy(g->ms_exec);
+            g->ms_exec = nullptr;
+        }
+        dev_free(g->ms_roots);
+        g->ms_roots = nullptr;
+        uint32_t cap = 64;
+        while (cap < nroots) cap *= 2;
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_roots, (uint64_t)cap * 2 * 4));
+        g->ms_cap = cap;
+    }
+    return WEDGE_OK;
+}
+
 // PageRank: iters x (dense pull, vertex step).
 static void pr_enqueue(wedge_graph* g, uint32_t iters, float damping, cudaStream_t s) {
     const int vb = g->num_sms * 8;
@@ -1369,6 +1682,80 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
     g->last_trace = false;
     g->last_stream = s;
     return WEDGE_OK;
+}
+
+wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query, uint32_t nroots,
+                                 uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts_in, wedge_stats* stats,
+                                 wedge_stream_t stream) {
+    if (!g || !roots || !d_levels) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (nqueries < 1 || nqueries > 64) return set_error(WEDGE_ERR_INVALID_ARG, "nqueries must be 1..64");
+    if (nroots < 1 || nroots > (1u << 24)) return set_error(WEDGE_ERR_INVALID_ARG, "nroots must be 1..2^24");
+    wedge_opts o;
+    if (opts_in) o = *opts_in;
+    else wedge_default_opts(WEDGE_BFS, &o);
+    WEDGE_TRY(check_opts(&o));
+    if (classify(d_levels) != PtrKind::Device) return set_error(WEDGE_ERR_INVALID_ARG, "levels must be device memory");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // roots and their queries, checked on the host
+    std::vector<uint32_t> hr((size_t)nroots * 2);
+    WEDGE_TRY_CUDA(cudaMemcpy(hr.data(), roots, (size_t)nroots * 4, cudaMemcpyDefault));
+    if (root_query) WEDGE_TRY_CUDA(cudaMemcpy(hr.data() + nroots, root_query, (size_t)nroots * 4, cudaMemcpyDefault));
+    for (uint32_t i = 0; i < nroots; ++i) {
+        if (!root_query) hr[nroots + i] = i;
+        if (hr[i] >= g->V) return set_error(WEDGE_ERR_INVALID_ARG, "root out of range");
+        if (hr[nroots + i] >= nqueries) return set_error(WEDGE_ERR_INVALID_ARG, "query id out of range");
+    }
+    WEDGE_TRY(msbfs_prepare(g, nroots));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(g->ms_roots, hr.data(), (size_t)nroots * 4, cudaMemcpyHostToDevice, s));
+    WEDGE_TRY_CUDA(
+        cudaMemcpyAsync(g->ms_roots + g->ms_cap, hr.data() + nroots, (size_t)nroots * 4, cudaMemcpyHostToDevice, s));
+    RunCtl init{};
+    init.max_iters = o.max_iters ? (o.max_iters < kDefaultMaxIters ? o.max_iters : kDefaultMaxIters) : kDefaultMaxIters;
+    init.switch_mode = o.switch_mode == WEDGE_SWITCH_LEARNED ? WEDGE_SWITCH_THRESHOLD : o.switch_mode;
+    init.tau_bp = o.tau_bp;
+    init.k = o.log2_coarsen;
+    init.E = g->E;
+    const uint32_t key[4] = {init.tau_bp, init.k, init.switch_mode, init.max_iters};
+    WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
+    const bool reuse = g->ms_exec && g->ms_exec_q == nqueries && g->ms_exec_n == nroots &&
+                       g->ms_exec_levels == d_levels && !memcmp(key, g->ms_exec_key, sizeof(key));
+    if (!reuse && !g->ms_graph_failed) {
+        if (g->ms_exec) {
+            cudaGraphExecDestroy(g->ms_exec);
+            g->ms_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+        wedge_status es = WEDGE_OK;
+        if (e == cudaSuccess) es = msbfs_enqueue(g, nroots, nqueries, d_levels, init, g->cap_stream);
+        cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(g->cap_stream, &graph) : e;
+        if (e == cudaSuccess && es == WEDGE_OK && ee == cudaSuccess &&
+            cudaGraphInstantiate(&g->ms_exec, graph, 0) == cudaSuccess) {
+            g->ms_exec_q = nqueries;
+            g->ms_exec_n = nroots;
+            g->ms_exec_levels = d_levels;
+            memcpy(g->ms_exec_key, key, sizeof(key));
+        } else {
+            g->ms_exec = nullptr;
+            g->ms_graph_failed = true;  // direct launches from now on
+            std::fprintf(stderr, "wedge: batched BFS graph capture unavailable; launching directly\n");
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+    }
+    if (g->ms_exec) {
+        WEDGE_TRY_CUDA(cudaGraphLaunch(g->ms_exec, s));
+        count_launch(4);
+    } else {
+        WEDGE_TRY(msbfs_enqueue(g, nroots, nqueries, d_levels, init, s));
+    }
+    WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
+    g->last_stream = s;
+    g->last_trace = false;
+    if (!stats) return WEDGE_OK;
+    return fill_stats(g, s, stats);
 }
 
 wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_bitmap, uint32_t log2_coarsen,

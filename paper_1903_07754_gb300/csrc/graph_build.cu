@@ -274,6 +274,12 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->split_bm);
     dev_free(g->mlp_bf16);
     dev_free(g->snap_vals);
+    dev_free(g->ms_fb[0]);
+    dev_free(g->ms_fb[1]);
+    dev_free(g->ms_seen);
+    dev_free(g->ms_roots);
+    dev_free(g->ms_bar);
+    if (g->ms_exec) cudaGraphExecDestroy(g->ms_exec);
     for (auto& e : g->loop_exec)
         if (e) cudaGraphExecDestroy(e);
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);

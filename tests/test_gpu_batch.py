@@ -1,0 +1,81 @@
+"""Batched BFS (one persistent launch, 64-bit query masks): every query's
+levels equal the oracle's single-root BFS, bit for bit, under every policy;
+the uneven batch of block-diagonal graphs gives each graph its own BFS."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from _gpu import INF, graph, opts
+from paper_1903_07754_gb300 import wedge
+
+pytestmark = pytest.mark.gpu
+
+
+def _levels(G, V, roots, rq, Q, o=None):
+    lv = torch.empty(V * Q, dtype=torch.int32, device="cuda")
+    st = wedge.wedge_run_bfs_batch(G.handle, roots, rq, Q, lv, o)
+    return lv.cpu().numpy().view(np.uint32).reshape(V, Q), st
+
+
+@pytest.fixture(scope="module")
+def g15():
+    return gg.rmat(15, 16)
+
+
+@pytest.fixture(scope="module")
+def g15_dev(g15):
+    G = graph(g15, with_weights=False)
+    yield G
+    G.close()
+
+
+@pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse3"])
+def test_64_roots_match_single_bfs(g15, g15_dev, mode):
+    roots = gg.roots(g15, 63, seed=5)
+    roots = np.append(roots, np.flatnonzero(g15.outdeg() == 0)[:1]).astype(np.uint32)  # one root without out-edges
+    o = {"default": opts("bfs"), "dense": opts("bfs", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0),
+         "sparse3": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=3)}[mode]
+    lv, st = _levels(g15_dev, g15.V, roots, None, 64, o)
+    for q, r in enumerate(roots):
+        np.testing.assert_array_equal(lv[:, q], oracle.bfs_push(g15, int(r)), err_msg=f"query {q}")
+    assert st.iters >= 1
+
+
+def test_few_queries_shared_roots_and_repeat(g15, g15_dev):
+    roots = np.array([0, 17, 17, 4000, 9], dtype=np.uint32)
+    rq = np.array([0, 1, 2, 2, 0], dtype=np.uint32)
+    for _ in range(2):  # the captured graph is replayed
+        lv, _ = _levels(g15_dev, g15.V, roots, rq, 3)
+        d0 = np.minimum(oracle.bfs_push(g15, 0), oracle.bfs_push(g15, 9))
+        d2 = np.minimum(oracle.bfs_push(g15, 17), oracle.bfs_push(g15, 4000))
+        np.testing.assert_array_equal(lv[:, 0], d0)
+        np.testing.assert_array_equal(lv[:, 1], oracle.bfs_push(g15, 17))
+        np.testing.assert_array_equal(lv[:, 2], d2)
+
+
+def test_uneven_batch_of_graphs():
+    graphs = [gg.rmat(8 + (i % 5), 8, seed=300 + i) for i in range(40)]
+    big, base = gg.block_diagonal(graphs)
+    G = graph(big, with_weights=False)
+    try:
+        roots = base.astype(np.uint32)          # vertex 0 of every graph
+        rq = (np.arange(len(graphs)) % 64).astype(np.uint32)
+        lv, _ = _levels(G, big.V, roots, rq, 64)
+        for i, g in enumerate(graphs):
+            got = lv[base[i]:base[i] + g.V, i % 64]
+            np.testing.assert_array_equal(got, oracle.bfs_push(g, 0), err_msg=f"graph {i}")
+    finally:
+        G.close()
+
+
+def test_invalid_batches_are_rejected(g15_dev):
+    lv = torch.empty(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_run_bfs_batch(g15_dev.handle, [1 << 20], None, 1, lv)
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_run_bfs_batch(g15_dev.handle, [0, 1], [0, 5], 2, lv)
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_run_bfs_batch(g15_dev.handle, [0], None, 65, lv)
