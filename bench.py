@@ -172,6 +172,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced"],
                     help="run only one small case for a profiler (no JSON line)")
+    ap.add_argument("--config", default="s22", choices=["s22", "learned-s24", "batch-s26", "grid"],
+                    help="s22: the benchmark line (R-MAT s22, four apps); the others print one line each "
+                         "for the learned switch (R-MAT s24), batched traversal (R-MAT s26, uneven "
+                         "batch) and the rewired grid")
     args = ap.parse_args()
 
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -194,6 +198,14 @@ def main():
     from paper_1903_07754_gb300 import build as wbuild
     wbuild.build()
     wedge.load()
+    if args.config != "s22":
+        line = {"learned-s24": bench_learned, "batch-s26": bench_batch, "grid": bench_grid}[args.config](
+            args, wedge, torch, dev, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     g, s = make_inputs(args.scale)
     od = oracle.outdeg(g)
@@ -354,6 +366,151 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _events(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _base_line(metric, value, unit, ms, steps, world, config, dtype="u32"):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": steps, "warmup": 3,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config}
+
+
+def bench_learned(args, wedge, torch, dev, world):
+    """Learned switch vs fixed threshold vs dense pull: BFS and SSSP on R-MAT
+    s24 ef16 (16.8 M vertices), root 0."""
+    import graphgen as gg
+    import oracle
+    from paper_1903_07754_gb300 import costmodel
+    g = gg.rmat(24, EF).with_weights(WMAX)
+    od = oracle.outdeg(g)
+    G = wedge.Graph.from_csc(g)
+    out = torch.empty(g.V, dtype=torch.int32, device=dev)
+    params = costmodel.load_params()
+    res = {}
+    total_edges, total_ms = 0, 0.0
+    for app in ("bfs", "sssp"):
+        run = (lambda o: wedge.wedge_run_bfs(G.handle, 0, out, o, False)) if app == "bfs" else \
+            (lambda o: wedge.wedge_run_sssp(G.handle, 0, out, o, False))
+        thr = wedge.wedge_default_opts(app)
+        dense = wedge.wedge_default_opts(app)
+        dense.switch_mode = wedge.SWITCH_ALWAYS_DENSE
+        learned = wedge.wedge_default_opts(app)
+        learned.switch_mode = wedge.SWITCH_LEARNED
+        t_thr = _events(torch, lambda: run(thr), 5)
+        t_dense = _events(torch, lambda: run(dense), 5)
+        wedge.wedge_set_cost_model(G.handle, params)
+        t_l = _events(torch, lambda: run(learned), 5)
+        wedge.wedge_set_cost_model(G.handle, None)
+        run(thr)
+        torch.cuda.synchronize()
+        reached = out.cpu().numpy().view(np.uint32) != 0xFFFFFFFF
+        edges = credited_edges(od, reached)
+        res[app] = {"learned_ms": t_l, "threshold_ms": t_thr, "dense_pull_ms": t_dense,
+                    "speedup_learned_vs_threshold": t_thr / t_l, "speedup_learned_vs_dense_pull": t_dense / t_l,
+                    "gteps_learned": edges / (t_l / 1e3) / 1e9}
+        total_edges += edges
+        total_ms += t_l
+    G.close()
+    line = _base_line("GTEPS (BFS+SSSP, learned switch) on R-MAT s24 ef16", total_edges / (total_ms / 1e3) / 1e9,
+                      "GTEPS", total_ms, 5, world, {"workload": "rmat-s24-ef16: bfs+sssp, learned switch",
+                                                    "V": g.V, "E": g.E})
+    line["per_app"] = res
+    return line
+
+
+def bench_batch(args, wedge, torch, dev, world):
+    """Batched BFS: 64 and 1024 roots (seeded, uniform over vertices with
+    out-edges) on R-MAT s26 ef16 in waves of 64 queries, and an uneven batch
+    of 256 R-MAT graphs of scales 12..20 (block-diagonal, one root each)."""
+    import graphgen as gg
+    from paper_1903_07754_gb300 import autotune
+    scale = 26 if args.scale == SCALE else args.scale
+    g = gg.rmat(scale, EF)
+    od = g.outdeg()
+    G = wedge.Graph.from_csc(g, with_weights=False)
+    roots = gg.roots(g, 1024, seed=3)
+    lv = torch.empty(g.V * 64, dtype=torch.int32, device=dev)
+    best, table = autotune.tune(G.handle, "bfs_batch", g.V, roots=roots[:64], nqueries=64,
+                                grid={"k": (1, 2, 3), "tau_bp": (500, 2000, 5000)}, reps=1)
+    autotune.apply(G.handle, best)
+    o = autotune.opts_for("bfs_batch", best)
+    res = {"autotuned": {k: best[k] for k in ("k", "tau_bp", "dense_loader", "blocks_per_sm")}}
+    wedge.wedge_run_bfs_batch(G.handle, roots[:64], None, 64, lv, o, False)
+    od_t = torch.from_numpy(od.astype(np.int64)).to(dev)
+    edges64 = _batch_edges(torch, lv, od_t, g.V)
+    t64 = _events(torch, lambda: wedge.wedge_run_bfs_batch(G.handle, roots[:64], None, 64, lv, o, False), 3)
+
+    def waves():
+        for w in range(16):
+            wedge.wedge_run_bfs_batch(G.handle, roots[64 * w:64 * (w + 1)], None, 64, lv, o, False)
+    t1024 = _events(torch, waves, 1)
+    res["roots64"] = {"ms": t64, "gteps": edges64 / (t64 / 1e3) / 1e9}
+    res["roots1024"] = {"ms": t1024, "gteps_est": 16 * edges64 / (t1024 / 1e3) / 1e9,
+                        "note": "traversed edges estimated from the first wave"}
+    G.close()
+    del lv
+    graphs = [gg.rmat(12 + (i % 9), EF, seed=1000 + i) for i in range(256)]
+    big, base = gg.block_diagonal(graphs)
+    B = wedge.Graph.from_csc(big, with_weights=False)
+    lvb = torch.empty(big.V * 64, dtype=torch.int32, device=dev)
+    rq = (np.arange(256) % 64).astype(np.uint32)
+    tb = _events(torch, lambda: wedge.wedge_run_bfs_batch(B.handle, base.astype(np.uint32), rq, 64, lvb, None, False), 3)
+    eb = _batch_edges(torch, lvb, torch.from_numpy(big.outdeg().astype(np.int64)).to(dev), big.V)
+    res["uneven256"] = {"ms": tb, "gteps": eb / (tb / 1e3) / 1e9, "V": big.V, "E": big.E}
+    B.close()
+    line = _base_line(f"GTEPS (batched BFS, 64 roots) on R-MAT s{scale} ef16", res["roots64"]["gteps"], "GTEPS", t64,
+                      3, world, {"workload": f"rmat-s{scale}-ef16: 64/1024-root batched BFS + 256-graph uneven batch",
+                                 "V": g.V, "E": g.E})
+    line["batch"] = res
+    return line
+
+
+def _batch_edges(torch, lv, od_t, V):
+    """Sum over queries of the out-degrees of the vertices each reached
+    (levels vertex-major, 64 queries), on the device."""
+    lvv = lv.view(V, 64)
+    return int(sum(int(od_t[lvv[:, q] != -1].sum().item()) for q in range(64)))
+
+
+def bench_grid(args, wedge, torch, dev, world):
+    """BFS and SSSP (weights in [1,1000]) from vertex 0 on the 4096^2 grid
+    with 1% rewiring, and BFS on the plain grid (8190 levels)."""
+    import graphgen as gg
+    import oracle
+    res = {}
+    total_e, total_ms = 0, 0.0
+    for p_rewire in (0.01, 0.0):
+        g = gg.grid(4096, p_rewire).with_weights(1000)
+        od = oracle.outdeg(g)
+        G = wedge.Graph.from_csc(g)
+        out = torch.empty(g.V, dtype=torch.int32, device=dev)
+        for app in (("bfs", "sssp") if p_rewire else ("bfs",)):
+            run = (lambda o: wedge.wedge_run_bfs(G.handle, 0, out, o, False)) if app == "bfs" else \
+                (lambda o: wedge.wedge_run_sssp(G.handle, 0, out, o, False))
+            o = wedge.wedge_default_opts(app)
+            t = _events(torch, lambda: run(o), 2)
+            st = wedge.wedge_run_bfs(G.handle, 0, out, o) if app == "bfs" else wedge.wedge_run_sssp(G.handle, 0, out, o)
+            edges = credited_edges(od, out.cpu().numpy().view(np.uint32) != 0xFFFFFFFF)
+            res[f"{app}_p{p_rewire:g}"] = {"ms": t, "iters": st.iters, "sparse_iters": st.sparse_iters,
+                                           "gteps": edges / (t / 1e3) / 1e9}
+            total_e += edges
+            total_ms += t
+        G.close()
+    line = _base_line("GTEPS (BFS+SSSP) on the 4096^2 grid", total_e / (total_ms / 1e3) / 1e9, "GTEPS", total_ms, 2,
+                      world, {"workload": "grid-4096x4096: p=0.01 bfs+sssp, p=0 bfs"})
+    line["per_app"] = res
+    return line
 
 
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):

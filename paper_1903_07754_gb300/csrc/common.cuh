@@ -141,6 +141,7 @@ struct wedge_graph {
     uint32_t ms_cap = 0;
     unsigned* ms_bar = nullptr;
     int ms_blocks = 0;
+    int ms_occ = 0;
     cudaGraphExec_t ms_exec = nullptr;
     uint32_t ms_exec_q = 0, ms_exec_n = 0;
     uint32_t* ms_exec_levels = nullptr;

@@ -1563,8 +1563,15 @@ static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
         int n = 0;
         WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_msbfs, kCW * 32, smem));
         if (n < 1) return set_error(WEDGE_ERR_NOT_SUPPORTED, "batched BFS kernel does not fit on an SM");
-        g->ms_blocks = g->num_sms * n;  // every block co-resident (cooperative launch)
+        g->ms_occ = n;
     }
+    int n = g->ms_occ;
+    if (g->tuning.blocks_per_sm > 0 && (int)g->tuning.blocks_per_sm < n) n = (int)g->tuning.blocks_per_sm;
+    if (g->num_sms * n != g->ms_blocks && g->ms_exec) {
+        cudaGraphExecDestroy(g->ms_exec);
+        g->ms_exec = nullptr;
+    }
+    g->ms_blocks = g->num_sms * n;  // every block co-resident (cooperative launch)
     if (nroots > g->ms_cap) {
         if (g->ms_exec) {
             cudaGraphExecDestroy(g->ms_exec);
