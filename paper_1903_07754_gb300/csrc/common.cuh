@@ -61,8 +61,22 @@ struct IterRec {
     unsigned int rowsum;          // sum |eidx row| over F_t
     unsigned long long t_pull0, t_pull1;    // globaltimer stamps of pull t
     unsigned long long t_xf0, t_xf1;        // and of the transformation for t
+    unsigned int nlist;           // F_t vertices written to the frontier list
+    unsigned int pad_;            // (the list is complete iff nlist == nfront)
 };
-static_assert(sizeof(IterRec) == 64, "IterRec layout");
+static_assert(sizeof(IterRec) == 72, "IterRec layout");
+constexpr int kListCap = 1024;  // frontier-list entries a pull block stages in shared memory
+constexpr int kMaxPullBlocks = 4096;
+
+// What one pull block found: written to its own slot (no shared counter),
+// reduced by the one-block decision kernel.
+struct BlockStat {
+    unsigned long long F;  // sum of out-degrees of the vertices it activated
+    unsigned int n;        // vertices it activated
+    unsigned int row;      // their edge-index row lengths
+    unsigned int lcnt;     // its list segment length (> kListCap: overflow)
+    unsigned int pad_;
+};
 
 // Run control block (device).
 struct RunCtl {
@@ -111,6 +125,9 @@ struct wedge_graph {
     uint32_t* wb = nullptr;        // Wedge Frontier bitmap, ceil(NC/32) words
     uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries
     uint2* pieces = nullptr;       // transformation work pieces
+    uint32_t* flist[2] = {nullptr, nullptr};  // frontier vertex lists by iteration parity
+    uint32_t* lseg = nullptr;      // per-block list segments of the last pull
+    wedge::BlockStat* bstat = nullptr;  // per-block results of the last pull
     wedge::IterRec* rec = nullptr; // per-iteration records
     uint32_t rec_cap = 0;
     wedge::RunCtl* ctl = nullptr;

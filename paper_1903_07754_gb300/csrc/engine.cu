@@ -5,6 +5,7 @@
 //   4), PageRank, and the run drivers for BFS, CC, SSSP and PageRank
 //   (Section 5).  The iteration loop runs on the device inside a CUDA graph
 //   with a conditional while node.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,9 +21,9 @@ namespace wedge {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 // Direct-load pulls are bound by the latency of their gathers: ask for enough
-// resident blocks per SM to keep 40 warps in flight.
+// resident blocks per SM to keep 32 warps in flight without spilling.
 #ifndef WEDGE_DIRECT_MIN_BLOCKS
-#define WEDGE_DIRECT_MIN_BLOCKS 5
+#define WEDGE_DIRECT_MIN_BLOCKS 4
 #endif
 constexpr int kDirectMinBlocks = WEDGE_DIRECT_MIN_BLOCKS;
 enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3, kMSBFS = 4 };
@@ -48,7 +49,6 @@ struct PullParams {
     const float* contrib;        // PageRank: pr(u)/outdeg(u)
     unsigned long long* acc;     // PageRank: fixed-point in-edge sums
     unsigned int pr_iter;
-    int decide;                  // elect a last block that takes the fullness decision
     int trace;
     int dense_tma;               // dense pulls stage tiles with bulk copies
     const __nv_bfloat16* mlp;    // learned switch weights (nullptr: threshold)
@@ -58,6 +58,9 @@ struct PullParams {
     unsigned long long* seen;    // queries that have reached each vertex
     uint32_t* levels;            // levels[v * Q + q]
     uint32_t Q;
+    uint32_t* flist[2];          // frontier vertex lists by iteration parity
+    uint32_t* lseg;              // per-block list segments (kListCap each)
+    BlockStat* bstat;            // per-block results
 };
 
 struct XformParams {
@@ -69,6 +72,7 @@ struct XformParams {
     IterRec* rec;
     RunCtl* ctl;
     uint32_t* bm[2];             // run mode: frontier bitmaps by parity
+    uint32_t* flist[2];          // run mode: frontier lists by parity
     const uint32_t* bm_in;       // standalone mode: the caller's frontier bitmap
     uint32_t V;
     unsigned long long bm_words;
@@ -245,7 +249,8 @@ template <int APP>
 __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, const uint32_t* cur, uint32_t* next,
                                               const uint32_t (&sv)[kEPL], const uint32_t (&wv)[kEPL], int nvalid,
                                               unsigned long long c, uint2 meta, unsigned next_head, bool contig,
-                                              uint32_t* s_kid, typename Traits<APP>::T* s_val, Stats& st) {
+                                              uint32_t* s_kid, typename Traits<APP>::T* s_val, Stats& st,
+                                              unsigned* s_lcnt, uint32_t* s_list) {
     using Tr = Traits<APP>;
     using T = typename Tr::T;
     const unsigned lane = threadIdx.x & 31, sub = lane & 3, o = 8 * sub;
@@ -385,6 +390,8 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
             st.F += __ldg(P.outdeg + dv);
             st.n += 1;
             st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
+            const unsigned slot = atomicAdd(s_lcnt, 1u);  // the block's frontier list
+            if (slot < (unsigned)kListCap) s_list[slot] = dv;
         }
     }
     __syncwarp();
@@ -403,11 +410,11 @@ constexpr int pull_stage_bytes() {
            + kStages * (kTileC + kMetaPad) * 8;                   // chunk metadata
 }
 
-// Shared memory of a pull: the record buffers, plus the stages when dense
-// pulls use bulk copies.
+// Shared memory of a pull: the record buffers and the block's frontier
+// list, plus the stages when dense pulls use bulk copies.
 template <int APP>
 constexpr int pull_smem_bytes(bool tma) {
-    return pull_records_bytes<APP>() + (tma ? pull_stage_bytes<APP>() : 0);
+    return pull_records_bytes<APP>() + kListCap * 4 + (tma ? pull_stage_bytes<APP>() : 0);
 }
 
 // A lane's 8 consecutive edges (and weights) straight from global memory.
@@ -438,13 +445,21 @@ __device__ __forceinline__ void load_lane_edges(const PullParams& P, unsigned lo
     }
 }
 
+// Copies a block's staged frontier list to its reserved range (base == ~0:
+// the block overflowed its stage; the iteration falls back to the bitmap).
+__device__ __forceinline__ void publish_list(uint32_t* list, const uint32_t* s_list, unsigned n, unsigned base) {
+    if (base == ~0u) return;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) list[base + i] = s_list[i];
+}
+
 // Dense pull over all chunks with direct loads: warp gw of nw takes slices
 // gw, gw + nw, ...  The next slice's edges and chunk metadata are loaded
 // before the current slice is processed, so the stream overlaps the gathers.
 template <int APP>
 __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned it, const uint32_t* cur,
                                                   uint32_t* next, uint32_t* my_kid, typename Traits<APP>::T* my_val,
-                                                  Stats& st, unsigned long long gw, unsigned long long nw) {
+                                                  Stats& st, unsigned long long gw, unsigned long long nw,
+                                                  unsigned* s_lcnt, uint32_t* s_list) {
     const unsigned lane = threadIdx.x & 31, q = lane >> 2, sub = lane & 3;
     const unsigned long long nslices = (P.NC + kSliceC - 1) / kSliceC;
     uint32_t sv[kEPL], wv[kEPL];
@@ -479,7 +494,7 @@ __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned 
         const int cnv = nvalid;
         const unsigned long long cc = c;
         fetch(sl + nw);
-        process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st);
+        process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st, s_lcnt, s_list);
     }
 }
 
@@ -490,7 +505,7 @@ template <int APP>
 __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, unsigned k, unsigned nchunks,
                                             const uint32_t* cur, uint32_t* next, uint32_t* my_kid,
                                             typename Traits<APP>::T* my_val, Stats& st, unsigned long long gw,
-                                            unsigned long long nw) {
+                                            unsigned long long nw, unsigned* s_lcnt, uint32_t* s_list) {
     const unsigned lane = threadIdx.x & 31, q = lane >> 2, sub = lane & 3;
     const unsigned long long nunits = (unsigned long long)nchunks << k;
     const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
@@ -522,7 +537,8 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
             meta = __ldg(P.cmeta + c);
             next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
         }
-        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st);
+        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st, s_lcnt,
+                           s_list);
     }
 }
 
@@ -531,7 +547,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
     using T = typename Traits<APP>::T;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row, s_last;
+    __shared__ unsigned s_n, s_row, s_lcnt;
     RunCtl* C = P.ctl;
     if (C->done) return;
     const unsigned it = C->it;
@@ -542,7 +558,8 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
     // layout: [records: values, ids][stages: barriers, src, w, metadata]
     T* s_val = reinterpret_cast<T*>(smem);
     uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
-    unsigned char* stage = smem + pull_records_bytes<APP>();
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + pull_records_bytes<APP>());
+    unsigned char* stage = smem + pull_records_bytes<APP>() + kListCap * 4;
     uint64_t* full = reinterpret_cast<uint64_t*>(stage);
     uint64_t* empty = full + kStages;
     uint32_t* s_src = reinterpret_cast<uint32_t*>(stage + 2 * kStages * 8);
@@ -556,6 +573,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
         s_F = 0;
         s_n = 0;
         s_row = 0;
+        s_lcnt = 0;
         if (P.trace && blockIdx.x == 0) P.rec[it].t_pull0 = global_timer();
         if constexpr (APP == kPR) {
             if (blockIdx.x == 0) C->dangling[(P.pr_iter + 1) & 1] = 0ull;
@@ -577,7 +595,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
     if constexpr (!TMA) {
         if (mode == 0)
             pull_dense_direct<APP>(P, it, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
-                                   (unsigned long long)gridDim.x * kCW);
+                                   (unsigned long long)gridDim.x * kCW, &s_lcnt, s_list);
     }
     if (TMA && mode == 0) {
         // ---- dense, staged: tiles of kTileC chunks streamed by bulk copies ----
@@ -653,13 +671,13 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + s);
                 process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, q > 0, my_kid, my_val,
-                                   st);
+                                   st, &s_lcnt, s_list);
             }
         }
     }
     if (mode != 0 && warp < kCW)
         pull_sparse<APP>(P, it, k, nchunks, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
-                         (unsigned long long)gridDim.x * kCW);
+                         (unsigned long long)gridDim.x * kCW, &s_lcnt, s_list);
 
     if constexpr (APP != kPR) {
 #pragma unroll
@@ -675,27 +693,19 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
         }
     }
     __syncthreads();
+    // this block's results and frontier-list segment go to its own slot
     if (threadIdx.x == 0) {
-        if (s_n) {
-            atomicAdd(&P.rec[it + 1].fullness, s_F);
-            atomicAdd(&P.rec[it + 1].nfront, s_n);
-            atomicAdd(&P.rec[it + 1].rowsum, s_row);
-        }
-        s_last = 0;
-        if (P.decide) {
-            __threadfence();
-            s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
-        }
+        BlockStat b;
+        b.F = s_F;
+        b.n = s_n;
+        b.row = s_row;
+        b.lcnt = s_lcnt;
+        b.pad_ = 0;
+        P.bstat[blockIdx.x] = b;
     }
-    __syncthreads();
-    if (s_last) {  // uniform across the block
-        __threadfence();
-        decide_block(P.rec, C, it + 1, P.mlp, P.gf, reinterpret_cast<float*>(smem));
-        if (threadIdx.x == 0) {
-            C->ticket = 0;
-            if (P.trace) P.rec[it].t_pull1 = global_timer();
-        }
-    }
+    if (s_lcnt <= (unsigned)kListCap)
+        for (unsigned i = threadIdx.x; i < s_lcnt; i += blockDim.x)
+            P.lseg[(size_t)blockIdx.x * kListCap + i] = s_list[i];
 }
 
 // ------------------------------------------------------------------------
@@ -740,6 +750,58 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
             const uint32_t rb = __ldg(eidx_off + u), rl = __ldg(eidx_off + u + 1) - rb;
             for (uint32_t qq = 0; qq < rl; qq += 32) pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
         }
+    }
+}
+
+// Same as xform_scan_words over an explicit list of n frontier vertices.
+__device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n,
+                                                const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                unsigned* npieces, unsigned long long gw, unsigned long long nw) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        uint32_t rb = 0, rl = 0;
+        if (i < n) {
+            const uint32_t u = __ldcg(list + i);
+            rb = __ldg(eidx_off + u);
+            rl = __ldg(eidx_off + u + 1) - rb;
+        }
+        const unsigned np = (rl + 31u) >> 5;
+        unsigned incl = np;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (!total) continue;
+        unsigned slot = 0;
+        if (lane == 31) slot = atomicAdd(npieces, total);
+        slot = __shfl_sync(kFull, slot, 31) + incl - np;
+        for (uint32_t qq = 0; qq < rl; qq += 32) pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
+    }
+}
+
+// Zeroes the bitmap words of a frontier: by its list when complete,
+// otherwise every word.  Optionally zeroes the vertices' query masks too.
+__device__ __forceinline__ void clear_frontier(uint32_t* bm, unsigned long long words, const uint32_t* list,
+                                               bool complete, unsigned n, unsigned long long* masks,
+                                               unsigned long long tid, unsigned long long nth) {
+    if (complete) {
+        for (unsigned long long i = tid; i < n; i += nth) {
+            const uint32_t v = __ldcg(list + i);
+            bm[v >> 5] = 0u;
+            if (masks) masks[v] = 0ull;
+        }
+    } else if (masks) {
+        for (unsigned long long wi = tid; wi < words; wi += nth) {
+            uint32_t w = __ldcg(bm + wi);
+            if (!w) continue;
+            bm[wi] = 0u;
+            for (; w; w &= w - 1) masks[wi * 32 + __ffs(w) - 1] = 0ull;
+        }
+    } else {
+        for (unsigned long long wi = tid; wi < words; wi += nth) bm[wi] = 0u;
     }
 }
 
@@ -805,12 +867,23 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
         if (C->done) return;
         const unsigned it = C->it;
         if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
-        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
-        for (unsigned long long i = tid; i < X.bm_words; i += nth) clr[i] = 0u;
+        // the bitmap that pull `it` fills held F_{it-1}: clear it (by its list
+        // when that list is complete), and the record pull `it` accumulates into
+        if (it > 0) {
+            const IterRec& pr = X.rec[it - 1];
+            uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
+            clear_frontier(clr, X.bm_words, ((it + 1) & 1) ? X.flist[1] : X.flist[0], pr.nlist == pr.nfront,
+                           pr.nfront, nullptr, tid, nth);
+        }
         if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
             reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
         r = X.rec + it;
         if (r->mode == 0) return;
+        if (r->nlist == r->nfront) {
+            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, X.pieces, &r->npieces,
+                            tid >> 5, nth >> 5);
+            return;
+        }
         bm = (it & 1) ? X.bm[1] : X.bm[0];
     }
     xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
@@ -901,7 +974,8 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
 
 // Run start: values, initial frontier F_0, records 0 and 1, control block.
 __global__ void k_run_init(int app, uint32_t V, uint32_t root, uint32_t* vals, uint32_t* bm0, uint32_t* bm1,
-                           uint32_t* wb, unsigned long long wb_words, IterRec* rec, RunCtl* C, RunCtl init) {
+                           uint32_t* wb, unsigned long long wb_words, IterRec* rec, RunCtl* C, RunCtl init,
+                           uint32_t* list0) {
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long v = tid; v < V; v += nth)
@@ -922,17 +996,123 @@ __global__ void k_run_init(int app, uint32_t V, uint32_t root, uint32_t* vals, u
     if (blockIdx.x == 0) {
         if (threadIdx.x < 2 * sizeof(IterRec) / 4) reinterpret_cast<unsigned*>(rec)[threadIdx.x] = 0u;
         if (threadIdx.x == 0) *C = init;
+        __syncthreads();
+        if (threadIdx.x == 0 && app != kCC) {  // F_0 = {root} as a list as well
+            list0[0] = root;
+            rec[0].nlist = 1;
+        }
     }
 }
 
-// Loop control of the device loop: count the body execution and keep
-// looping while the frontier is non-empty, never more than max_iters + 2
-// times.
-__global__ void k_loop_ctl(RunCtl* C, cudaGraphConditionalHandle h) {
+// Decision step, one block of 1024 threads after each pull: sums the pull
+// blocks' slots into the record of the next iteration, takes the fullness
+// decision (or the learned switch's), and, when the next iteration pulls
+// over the Wedge Frontier and every block's list segment fit, packs the
+// segments into one frontier list for the transformation.  Then the device
+// loop's control: count this body execution and keep looping while the
+// frontier is non-empty, never more than max_iters + 2 times (h = 0 outside
+// a graph).
+__global__ void __launch_bounds__(1024) k_decide(IterRec* rec, RunCtl* C, const BlockStat* __restrict__ bstat,
+                                                 unsigned nblocks, const uint32_t* __restrict__ lseg,
+                                                 uint32_t* list0, uint32_t* list1, const __nv_bfloat16* mlp,
+                                                 GraphFeat gf, int trace, cudaGraphConditionalHandle h) {
+    __shared__ float dsm[2 * kCandidates * kMlpHidden + 8];
+    __shared__ unsigned long long s_F;
+    __shared__ unsigned s_n, s_row, s_over, s_tot;
+    __shared__ unsigned s_wsum[32];
+    __shared__ unsigned s_start[kMaxPullBlocks];
+    if (!C->done) {
+        const unsigned it = C->it;
+        if (threadIdx.x == 0) {
+            s_F = 0;
+            s_n = 0;
+            s_row = 0;
+            s_over = 0;
+        }
+        __syncthreads();
+        // each thread owns a contiguous run of slots
+        const unsigned per = (nblocks + blockDim.x - 1) / blockDim.x;
+        const unsigned b0 = threadIdx.x * per, b1 = min(nblocks, b0 + per);
+        unsigned long long F = 0;
+        unsigned n = 0, row = 0, cnt = 0, over = 0;
+        for (unsigned b = b0; b < b1; ++b) {
+            const BlockStat st = bstat[b];
+            F += st.F;
+            n += st.n;
+            row += st.row;
+            cnt += st.lcnt;
+            over |= st.lcnt > (unsigned)kListCap;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            F += __shfl_down_sync(kFull, F, d);
+            n += __shfl_down_sync(kFull, n, d);
+            row += __shfl_down_sync(kFull, row, d);
+            over |= __shfl_down_sync(kFull, over, d);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_F, F);
+            atomicAdd(&s_n, n);
+            atomicAdd(&s_row, row);
+            atomicOr(&s_over, over);
+        }
+        __syncthreads();
+        IterRec* r = rec + it + 1;
+        if (threadIdx.x == 0) {
+            r->fullness = s_F;
+            r->nfront = s_n;
+            r->rowsum = s_row;
+            r->nlist = 0;
+            if (trace) rec[it].t_pull1 = global_timer();
+        }
+        __syncthreads();
+        decide_block(rec, C, it + 1, mlp, gf, dsm);
+        __syncthreads();
+        if (r->mode && !s_over && s_n) {
+            // exclusive prefix of the segment lengths (thread runs, then warps)
+            const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            unsigned incl = cnt;
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(kFull, incl, d);
+                if (lane >= (unsigned)d) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const unsigned nw = blockDim.x >> 5;
+                unsigned x = lane < nw ? s_wsum[lane] : 0u, xi = x;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned y = __shfl_up_sync(kFull, xi, d);
+                    if (lane >= (unsigned)d) xi += y;
+                }
+                s_wsum[lane] = xi - x;
+                if (lane == 31) s_tot = xi;
+            }
+            __syncthreads();
+            unsigned pos = s_wsum[warp] + incl - cnt;
+            for (unsigned b = b0; b < b1; ++b) {
+                s_start[b] = pos;
+                pos += bstat[b].lcnt;
+            }
+            __syncthreads();
+            // copy entry i from the segment whose range holds it (binary search)
+            uint32_t* out = ((it + 1) & 1) ? list1 : list0;
+            const unsigned tot = s_tot;
+            for (unsigned i = threadIdx.x; i < tot; i += blockDim.x) {
+                unsigned lo = 0, hi = nblocks - 1;
+                while (lo < hi) {
+                    const unsigned mid = (lo + hi + 1) >> 1;
+                    if (s_start[mid] <= i) lo = mid;
+                    else hi = mid - 1;
+                }
+                out[i] = lseg[(size_t)lo * kListCap + (i - s_start[lo])];
+            }
+            if (threadIdx.x == 0) r->nlist = tot;
+        }
+    }
     if (threadIdx.x == 0) {
-        const unsigned n = ++C->loops;
-        const bool more = !C->done && n < C->max_iters + 2;
-        cudaGraphSetConditional(h, more ? 1u : 0u);
+        const unsigned loops = ++C->loops;
+        const bool more = !C->done && loops < C->max_iters + 2;
+        if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
     }
 }
 
@@ -950,21 +1130,38 @@ __global__ void k_loop_ctl(RunCtl* C, cudaGraphConditionalHandle h) {
 // and seen masks, bitmaps, the Wedge list, work pieces) is read with
 // ld.global.cg: L1 is not coherent across SMs inside a launch.
 //
-// Grid-wide barrier on (count, generation).  Returns false (and records
-// kStatusTimeout) if the other blocks do not arrive within kWaitNs.
-__device__ bool grid_sync(unsigned* count, unsigned* gen, unsigned* status) {
+// Grid-wide barrier, two levels: blocks arrive on their group's counter (32
+// blocks per group, counters 128 bytes apart), the last of each group on the
+// top counter, and the last of all bumps the generation the others wait on.
+// Layout of bar: [0] top count, [1] generation, [32*(1+g)] group g's count.
+// Returns false (and records kStatusTimeout) if the generation does not
+// move within kWaitNs.
+constexpr unsigned kBarGroup = 32;
+constexpr unsigned kBarWords = 32 * (1 + kMaxPullBlocks / kBarGroup);
+
+__device__ bool grid_sync(unsigned* bar, unsigned* status) {
     __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned ok = 1;
-        volatile unsigned* vgen = gen;
+        volatile unsigned* vgen = bar + 1;
         const unsigned g = *vgen;
         __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
+        const unsigned grp = blockIdx.x / kBarGroup;
+        const unsigned ngroups = (gridDim.x + kBarGroup - 1) / kBarGroup;
+        const unsigned gsize = min(kBarGroup, gridDim.x - grp * kBarGroup);
+        bool released = false;
+        unsigned* gc = bar + 32 * (1 + grp);
+        if (atomicAdd(gc, 1u) == gsize - 1) {
+            atomicExch(gc, 0u);
+            if (atomicAdd(bar, 1u) == ngroups - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+                released = true;
+            }
+        }
+        if (!released) {
             const unsigned long long t0 = gtimer();
             for (unsigned n = 1; *vgen == g; ++n) {
                 if ((n & 127u) == 0 && gtimer() - t0 > kWaitNs) {
@@ -972,7 +1169,7 @@ __device__ bool grid_sync(unsigned* count, unsigned* gen, unsigned* status) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -999,13 +1196,10 @@ __global__ void k_msbfs_clear(uint32_t V, unsigned long long* fb0, unsigned long
         bm1[i] = 0u;
     }
     for (unsigned long long i = tid; i < wb_words; i += nth) wb[i] = 0u;
+    for (unsigned long long i = tid; i < kBarWords; i += nth) bar[i] = 0u;
     if (blockIdx.x == 0) {
         if (threadIdx.x < 2 * sizeof(IterRec) / 4) reinterpret_cast<unsigned*>(rec)[threadIdx.x] = 0u;
-        if (threadIdx.x == 0) {
-            *C = init;
-            bar[0] = 0u;
-            bar[1] = 0u;
-        }
+        if (threadIdx.x == 0) *C = init;
     }
 }
 
@@ -1026,12 +1220,13 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
     using T = unsigned long long;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row;
+    __shared__ unsigned s_n, s_row, s_lcnt, s_lbase;
     RunCtl* C = P.ctl;
     if (C->done) return;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* s_val = reinterpret_cast<T*>(smem);
     uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + pull_records_bytes<kMSBFS>());
     uint32_t* my_kid = s_kid + warp * kSliceE;
     T* my_val = s_val + warp * kSliceE;
     const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
@@ -1047,15 +1242,17 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
             s_F = 0;
             s_n = 0;
             s_row = 0;
+            s_lcnt = 0;
         }
         __syncthreads();
         Stats st{0ull, 0u, 0u};
         const uint32_t* cur = (it & 1) ? P.bm[1] : P.bm[0];
         uint32_t* next = (it & 1) ? P.bm[0] : P.bm[1];
         if (mode == 0)
-            pull_dense_direct<kMSBFS>(P, it, cur, next, my_kid, my_val, st, gw, nw);
+            pull_dense_direct<kMSBFS>(P, it, cur, next, my_kid, my_val, st, gw, nw, &s_lcnt, s_list);
         else
-            pull_sparse<kMSBFS>(P, it, k, __ldcg(&P.rec[it].nchunks), cur, next, my_kid, my_val, st, gw, nw);
+            pull_sparse<kMSBFS>(P, it, k, __ldcg(&P.rec[it].nchunks), cur, next, my_kid, my_val, st, gw, nw,
+                                &s_lcnt, s_list);
         for (int d = 16; d > 0; d >>= 1) {
             st.F += __shfl_down_sync(kFull, st.F, d);
             st.n += __shfl_down_sync(kFull, st.n, d);
@@ -1067,12 +1264,17 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
             atomicAdd(&s_row, st.row);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && s_n) {
-            atomicAdd(&P.rec[it + 1].fullness, s_F);
-            atomicAdd(&P.rec[it + 1].nfront, s_n);
-            atomicAdd(&P.rec[it + 1].rowsum, s_row);
+        if (threadIdx.x == 0) {
+            if (s_n) {
+                atomicAdd(&P.rec[it + 1].fullness, s_F);
+                atomicAdd(&P.rec[it + 1].nfront, s_n);
+                atomicAdd(&P.rec[it + 1].rowsum, s_row);
+            }
+            s_lbase = (s_lcnt && s_lcnt <= (unsigned)kListCap) ? atomicAdd(&P.rec[it + 1].nlist, s_lcnt) : ~0u;
         }
-        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        __syncthreads();
+        publish_list(P.flist[(it + 1) & 1], s_list, s_lcnt, s_lbase);
+        if (!grid_sync(bar, &C->status)) break;
         // ---- decision: every block computes it from the same sums ----
         const unsigned nit = it + 1;
         const unsigned long long F = __ldcg(&P.rec[nit].fullness);
@@ -1093,22 +1295,23 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
         }
         if (done) break;
         // ---- retire frontier it (masks and bitmap), prepare the next ----
-        uint32_t* cbm = (it & 1) ? P.bm[1] : P.bm[0];
-        unsigned long long* cfr = (it & 1) ? P.fb[1] : P.fb[0];
-        for (unsigned long long wi = tid; wi < words; wi += nth) {
-            uint32_t w = __ldcg(cbm + wi);
-            if (!w) continue;
-            cbm[wi] = 0u;
-            for (; w; w &= w - 1) cfr[wi * 32 + __ffs(w) - 1] = 0ull;
-        }
+        const unsigned nl_t = __ldcg(&P.rec[it].nlist), nf_t = __ldcg(&P.rec[it].nfront);
+        clear_frontier((it & 1) ? P.bm[1] : P.bm[0], words, (it & 1) ? P.flist[1] : P.flist[0], nl_t == nf_t, nf_t,
+                       (it & 1) ? P.fb[1] : P.fb[0], tid, nth);
         if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
             reinterpret_cast<unsigned*>(P.rec + nit + 1)[threadIdx.x] = 0u;
-        if (sparse) xform_scan_words(next, X.V, words, X.eidx_off, X.pieces, &P.rec[nit].npieces, gw, nw);
-        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        if (sparse) {
+            if (__ldcg(&P.rec[nit].nlist) == nf)
+                xform_scan_list((nit & 1) ? P.flist[1] : P.flist[0], nf, X.eidx_off, X.pieces, &P.rec[nit].npieces,
+                                gw, nw);
+            else
+                xform_scan_words(next, X.V, words, X.eidx_off, X.pieces, &P.rec[nit].npieces, gw, nw);
+        }
+        if (!grid_sync(bar, &C->status)) break;
         if (sparse)
             xform_expand_pieces(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
                                 &P.rec[nit].nchunks, gw, nw);
-        if (!grid_sync(bar, bar + 1, &C->status)) break;
+        if (!grid_sync(bar, &C->status)) break;
         it = nit;
         mode = sparse;
         k = C->k;
@@ -1204,10 +1407,28 @@ __global__ void k_rec_set(IterRec* rec, unsigned t, IterRec v) {
     if (threadIdx.x == 0) rec[t] = v;
 }
 
-__global__ void k_standalone_out(const IterRec* rec, unsigned iter, unsigned long long* fullness, uint32_t* nfront) {
+// Frontier size and fullness of a standalone pull, summed over the blocks' slots.
+__global__ void k_standalone_out(const BlockStat* __restrict__ bstat, unsigned nblocks, unsigned long long* fullness,
+                                 uint32_t* nfront) {
+    __shared__ unsigned long long s_F;
+    __shared__ unsigned s_n;
     if (threadIdx.x == 0) {
-        *fullness = rec[iter + 1].fullness;
-        *nfront = rec[iter + 1].nfront;
+        s_F = 0;
+        s_n = 0;
+    }
+    __syncthreads();
+    unsigned long long F = 0;
+    unsigned n = 0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        F += bstat[b].F;
+        n += bstat[b].n;
+    }
+    atomicAdd(&s_F, F);
+    atomicAdd(&s_n, n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *fullness = s_F;
+        *nfront = s_n;
     }
 }
 
@@ -1284,6 +1505,8 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY_CUDA(cudaMemset(g->wb, 0, ((NC + 31) / 32 + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->flist[1], (V + 1) * 4));
     g->rec_cap = kDefaultMaxIters + 2;
     WEDGE_TRY(dev_alloc(g, (void**)&g->rec, (uint64_t)g->rec_cap * sizeof(IterRec)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->ctl, sizeof(RunCtl)));
@@ -1298,6 +1521,11 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     WEDGE_TRY(configure_pulls(g));
     g->xform_blocks = g->num_sms * 4;
+    int nb = 0;
+    for (int a = 0; a < 4; ++a) nb = std::max(nb, std::max(g->pull_blocks_app[a], g->pull_blocks_tma[a]));
+    if (nb > kMaxPullBlocks) return set_error(WEDGE_ERR_NOT_SUPPORTED, "too many pull blocks for this device");
+    WEDGE_TRY(dev_alloc(g, (void**)&g->lseg, (uint64_t)nb * kListCap * 4));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->bstat, (uint64_t)nb * sizeof(BlockStat)));
     return WEDGE_OK;
 }
 
@@ -1333,9 +1561,12 @@ static PullParams pull_params(wedge_graph* g, int trace, int app = kCC) {
     P.ctl = g->ctl;
     P.contrib = g->contrib;
     P.acc = g->acc;
-    P.decide = 1;
     P.trace = trace;
     P.dense_tma = g->tuning.dense_loader == 1 ? 1 : 0;
+    P.flist[0] = g->flist[0];
+    P.flist[1] = g->flist[1];
+    P.lseg = g->lseg;
+    P.bstat = g->bstat;
     return P;
 }
 
@@ -1350,6 +1581,8 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.ctl = g->ctl;
     X.bm[0] = g->bm[0];
     X.bm[1] = g->bm[1];
+    X.flist[0] = g->flist[0];
+    X.flist[1] = g->flist[1];
     X.bm_in = nullptr;
     X.V = g->V;
     X.bm_words = ((uint64_t)g->V + 31) / 32;
@@ -1357,6 +1590,18 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.standalone_k = -1;
     X.trace = trace;
     return X;
+}
+
+// Grid size of the pull variant that P selects.
+static unsigned pull_grid(const wedge_graph* g, int app, const PullParams& P) {
+    return (unsigned)(P.dense_tma ? g->pull_blocks_tma[app] : g->pull_blocks_app[app]);
+}
+
+static void launch_decide(const wedge_graph* g, int app, const PullParams& P, cudaGraphConditionalHandle h,
+                          cudaStream_t s) {
+    k_decide<<<1, 1024, 0, s>>>(g->rec, g->ctl, g->bstat, pull_grid(g, app, P), g->lseg, g->flist[0], g->flist[1],
+                                P.mlp, P.gf, P.trace, h);
+    count_launch();
 }
 
 static void launch_xform(const wedge_graph* g, const XformParams& X, cudaStream_t s) {
@@ -1392,8 +1637,8 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
     PullParams P = pull_params(g, 0, app);
     XformParams X = xform_params(g, 0);
     launch_pull_app(g, app, P, cs);
+    launch_decide(g, app, P, handle, cs);
     launch_xform(g, X, cs);
-    k_loop_ctl<<<1, 32, 0, cs>>>(g->ctl, handle);
     cudaError_t le = cudaGetLastError();
     cudaGraph_t captured = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &captured);
@@ -1451,6 +1696,7 @@ static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, cons
     for (;;) {
         for (int b = 0; b < batch; ++b) {
             launch_pull_app(g, app, P, s);
+            launch_decide(g, app, P, 0, s);
             launch_xform(g, X, s);
         }
         launched += batch;
@@ -1491,7 +1737,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words, g->rec,
-                                              g->ctl, init);
+                                              g->ctl, init, g->flist[0]);
     PullParams P = pull_params(g, trace, app);
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, P.mlp,
                                                     P.gf);
@@ -1528,7 +1774,6 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     P.seen = g->ms_seen;
     P.levels = levels;
     P.Q = Q;
-    P.decide = 0;
     XformParams X = xform_params(g, 0);
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);
@@ -1538,7 +1783,7 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(g->ms_blocks);
     cfg.blockDim = dim3(kCW * 32);
-    cfg.dynamicSmemBytes = pull_records_bytes<kMSBFS>();
+    cfg.dynamicSmemBytes = pull_records_bytes<kMSBFS>() + kListCap * 4;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1557,8 +1802,8 @@ static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_seen, V * 8));
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_fb[0], V * 8));
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_fb[1], V * 8));
-        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_bar, 64));
-        const int smem = pull_records_bytes<kMSBFS>();
+        WEDGE_TRY(dev_alloc(g, (void**)&g->ms_bar, kBarWords * 4));
+        const int smem = pull_records_bytes<kMSBFS>() + kListCap * 4;
         WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_msbfs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int n = 0;
         WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_msbfs, kCW * 32, smem));
@@ -1590,8 +1835,7 @@ static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
 // PageRank: iters x (dense pull, vertex step).
 static void pr_enqueue(wedge_graph* g, uint32_t iters, float damping, cudaStream_t s) {
     const int vb = g->num_sms * 8;
-    PullParams P = pull_params(g, 0);
-    P.decide = 0;
+    PullParams P = pull_params(g, 0, kPR);
     const float base = (1.0f - damping) / (float)g->V;
     for (uint32_t t = 0; t < iters; ++t) {
         P.pr_iter = t;
@@ -1810,9 +2054,9 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     P.bm[(iter + 1) & 1] = d_next_bitmap;
     P.clist = d_chunk_list ? d_chunk_list : g->clist;
     P.wb = nullptr;  // a caller's list has no library bitmap behind it
-    P.decide = 0;
     launch_pull_app(g, app, P, s);
-    k_standalone_out<<<1, 32, 0, s>>>(g->rec, iter, reinterpret_cast<unsigned long long*>(d_fullness), d_nfront);
+    k_standalone_out<<<1, 256, 0, s>>>(g->bstat, pull_grid(g, app, P), reinterpret_cast<unsigned long long*>(d_fullness),
+                                       d_nfront);
     count_launch(2);
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
@@ -1878,7 +2122,7 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
     P.mlp = nullptr;
     XformParams X = xform_params(g, 0);
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb,
-                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init);
+                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->flist[0]);
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);
     count_launch(2);
@@ -1905,14 +2149,16 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                 cr.k = c > 0 ? (unsigned)(c - 1) : hr.k;
             }
             WEDGE_TRY_CUDA(cudaMemcpyAsync(g->vals, g->snap_vals, vbytes, cudaMemcpyDeviceToDevice, s));
+            // a previous candidate's pull marked its frontier in the next bitmap
+            WEDGE_TRY_CUDA(cudaMemsetAsync(g->bm[(t + 1) & 1], 0, ((uint64_t)g->V + 31) / 32 * 4, s));
             k_ctl_init<<<1, 32, 0, s>>>(g->ctl, hc);
             k_rec_set<<<1, 32, 0, s>>>(g->rec, t, cr);
             count_launch(2);
-            P.decide = c == kCandidates ? 1 : 0;
             WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
             launch_xform(g, X, s);
             launch_pull_app(g, app, P, s);
             WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
+            if (c == kCandidates) launch_decide(g, app, P, 0, s);  // advance with the threshold's choice
             WEDGE_TRY_CUDA(cudaGetLastError());
             if (c < kCandidates) {
                 WEDGE_TRY_CUDA(cudaEventSynchronize(g->ev1));

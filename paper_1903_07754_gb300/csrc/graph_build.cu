@@ -265,6 +265,10 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->wb);
     dev_free(g->clist);
     dev_free(g->pieces);
+    dev_free(g->flist[0]);
+    dev_free(g->flist[1]);
+    dev_free(g->lseg);
+    dev_free(g->bstat);
     dev_free(g->rec);
     dev_free(g->ctl);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
