@@ -126,6 +126,7 @@ struct wedge_graph {
     uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries
     uint2* pieces = nullptr;       // transformation work pieces
     uint32_t* flist[2] = {nullptr, nullptr};  // frontier vertex lists by iteration parity
+    uint32_t* visk = nullptr;      // BFS: visited destinations by index into vid, ceil(NZ/32)+1 words
     uint32_t* lseg = nullptr;      // per-block list segments of the last pull
     wedge::BlockStat* bstat = nullptr;  // per-block results of the last pull
     wedge::IterRec* rec = nullptr; // per-iteration records
@@ -151,6 +152,7 @@ struct wedge_graph {
     bool has_model = false;
     uint32_t max_outdeg = 0;
     uint32_t* snap_vals = nullptr;   // candidate-timing trace: value snapshot
+    uint32_t* snap_visk = nullptr;   // candidate-timing trace: visited-bitmap snapshot
     // batched BFS
     unsigned long long* ms_fb[2] = {nullptr, nullptr};
     unsigned long long* ms_seen = nullptr;

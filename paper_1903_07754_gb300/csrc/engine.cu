@@ -20,13 +20,28 @@
 namespace wedge {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-// Direct-load pulls are bound by the latency of their gathers: ask for enough
-// resident blocks per SM to keep 32 warps in flight without spilling.
-#ifndef WEDGE_DIRECT_MIN_BLOCKS
-#define WEDGE_DIRECT_MIN_BLOCKS 4
-#endif
-constexpr int kDirectMinBlocks = WEDGE_DIRECT_MIN_BLOCKS;
 enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3, kMSBFS = 4 };
+// Resident 256-thread blocks per SM that the register allocation of a
+// direct-load pull must allow.  Measured on R-MAT s22: 4 blocks (64
+// registers) beat 5 (48 registers) for every application -- BFS by 25%, as
+// the fifth block's shared memory comes out of the L1 that caches the
+// frontier bitmap, and PageRank by 15%, as 48 registers spill.
+#ifndef WEDGE_MIN_BLOCKS_BFS
+#define WEDGE_MIN_BLOCKS_BFS 4
+#endif
+#ifndef WEDGE_MIN_BLOCKS_CC
+#define WEDGE_MIN_BLOCKS_CC 4
+#endif
+#ifndef WEDGE_MIN_BLOCKS_SSSP
+#define WEDGE_MIN_BLOCKS_SSSP 4
+#endif
+#ifndef WEDGE_MIN_BLOCKS_PR
+#define WEDGE_MIN_BLOCKS_PR 4
+#endif
+constexpr int direct_min_blocks(int app) {
+    return app == kBFS ? WEDGE_MIN_BLOCKS_BFS
+                       : app == kCC ? WEDGE_MIN_BLOCKS_CC : app == kSSSP ? WEDGE_MIN_BLOCKS_SSSP : WEDGE_MIN_BLOCKS_PR;
+}
 
 // ------------------------------------------------------------------------
 // Kernel parameter blocks
@@ -61,6 +76,7 @@ struct PullParams {
     uint32_t* flist[2];          // frontier vertex lists by iteration parity
     uint32_t* lseg;              // per-block list segments (kListCap each)
     BlockStat* bstat;            // per-block results
+    uint32_t* visk;              // BFS runs: visited bit per destination index (nullptr: no skipping)
 };
 
 struct XformParams {
@@ -248,7 +264,8 @@ struct Stats {
 template <int APP>
 __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, const uint32_t* cur, uint32_t* next,
                                               const uint32_t (&sv)[kEPL], const uint32_t (&wv)[kEPL], int nvalid,
-                                              unsigned long long c, uint2 meta, unsigned next_head, bool contig,
+                                              uint32_t live, unsigned long long c, uint2 meta, unsigned next_head,
+                                              bool contig,
                                               uint32_t* s_kid, typename Traits<APP>::T* s_val, Stats& st,
                                               unsigned* s_lcnt, uint32_t* s_list) {
     using Tr = Traits<APP>;
@@ -258,42 +275,42 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
     const uint32_t vmask = (nvalid >= 8) ? 0xFFu : ((1u << nvalid) - 1u);
     const uint32_t hb = (heads >> o) & vmask;
     const uint32_t brk = (hb | ((sub == 0 && !contig) ? 1u : 0u)) & vmask;
+    live &= vmask;
 
     T inc[kEPL];
     T run = Tr::neutral();
 #pragma unroll
     for (int i = 0; i < kEPL; ++i) {
-        const T cv = (i < nvalid) ? candidate<APP>(P, cur, sv[i], wv[i], it) : Tr::neutral();
+        const T cv = ((live >> i) & 1u) ? candidate<APP>(P, cur, sv[i], wv[i], it) : Tr::neutral();
         run = ((brk >> i) & 1u) ? cv : Tr::op(run, cv);
         inc[i] = run;
     }
-    // segmented scan across lanes: (lane has a break, tail value, tail starts at a head)
+    // Segmented scan of the lanes' tail values.  A lane with a break (or no
+    // edges) starts a run of lanes; lane L's run starts at the highest such
+    // lane <= L, found by ballot, so only the values move through shuffles.
+    const unsigned below_me = (1u << lane) - 1u;
     const int last_brk = brk ? 31 - __clz(brk) : -1;
-    bool f = brk != 0 || nvalid == 0;
+    const unsigned Fm = __ballot_sync(kFull, brk != 0 || nvalid == 0);
+    // does the tail segment of a breaking lane start at a destination's first edge?
+    const unsigned Sm = __ballot_sync(kFull, brk ? ((hb >> last_brk) & 1u) : 0u);
+    const unsigned fle = Fm & (below_me | (1u << lane));
+    const unsigned start = fle ? 31 - __clz(fle) : 0u;
     T v = run;
-    unsigned sr = brk ? ((hb >> last_brk) & 1u) : 0u;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const unsigned f2 = __shfl_up_sync(kFull, (unsigned)f, d);
         const T v2 = __shfl_up_sync(kFull, v, d);
-        const unsigned sr2 = __shfl_up_sync(kFull, sr, d);
-        if (lane >= (unsigned)d && !f) {
-            v = Tr::op(v2, v);
-            sr = sr2;
-            f = f2;
-        }
+        if (lane >= start + d) v = Tr::op(v2, v);
     }
     T carry = __shfl_up_sync(kFull, v, 1);
-    unsigned carry_sr = __shfl_up_sync(kFull, sr, 1);
-    if (lane == 0) {
-        carry = Tr::neutral();
-        carry_sr = 0;
-    }
+    if (lane == 0) carry = Tr::neutral();
+    const unsigned flt = Fm & below_me;
+    const unsigned carry_sr = flt ? (Sm >> (31 - __clz(flt))) & 1u : 0u;
     // does this lane's last segment end at its last edge?
-    const unsigned mine = (brk & 1u) | ((nvalid > 0) << 1);
-    const unsigned nx = __shfl_down_sync(kFull, mine, 1);
-    const bool nx_valid = lane < 31 && (nx & 2u);
-    const bool tail_close = nvalid > 0 && (nvalid < kEPL || !nx_valid || (nx & 1u));
+    const unsigned nb0 = __ballot_sync(kFull, brk & 1u);
+    const unsigned nbv = __ballot_sync(kFull, nvalid > 0);
+    const unsigned up = lane < 31 ? 2u << lane : 0u;
+    const bool nx_valid = (nbv & up) != 0;
+    const bool tail_close = nvalid > 0 && (nvalid < kEPL || !nx_valid || (nb0 & up) != 0);
     const bool next_past_end = c * 32 + o + kEPL >= P.E;
     const bool tail_real = nvalid < kEPL || next_past_end ||
                            ((sub == 3) ? (next_head != 0) : (((heads >> (o + kEPL)) & 1u) != 0));
@@ -319,16 +336,16 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
             }
         }
     }
-    // compact the records of the warp into its shared buffer
+    // compact the records of the warp into its shared buffer: the exclusive
+    // prefix of the lanes' record counts (at most 8, four bits) by ballots
     const unsigned cnt = __popc(K);
-    unsigned incl = cnt;
+    unsigned slot = 0, total = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= (unsigned)d) incl += y;
+    for (int b = 0; b < 4; ++b) {
+        const unsigned Bb = __ballot_sync(kFull, (cnt >> b) & 1u);
+        slot += (unsigned)__popc(Bb & below_me) << b;
+        total += (unsigned)__popc(Bb) << b;
     }
-    const unsigned total = __shfl_sync(kFull, incl, 31);
-    unsigned slot = incl - cnt;
 #pragma unroll
     for (int e = 0; e < kEPL; ++e) {
         if ((K >> e) & 1u) {
@@ -349,6 +366,10 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
             if (P.vals[dv] == kInf) {
                 P.vals[dv] = it + 1;
                 act = set_bit(next, dv);
+                if (P.visk) {
+                    const uint32_t kid = kx & 0x7FFFFFFFu;
+                    atomicOr(P.visk + (kid >> 5), 1u << (kid & 31));
+                }
             }
         } else if constexpr (APP == kMSBFS) {
             // queries reaching dv for the first time take level it+1
@@ -417,13 +438,45 @@ constexpr int pull_smem_bytes(bool tma) {
     return pull_records_bytes<APP>() + kListCap * 4 + (tma ? pull_stage_bytes<APP>() : 0);
 }
 
-// A lane's 8 consecutive edges (and weights) straight from global memory.
+// Which of a lane's edges still have to be pulled: bit i is set if edge
+// o + i of the chunk is valid and, for BFS runs, its destination is not yet
+// visited (Section 5: the BFS pull skips visited vertices whatever the
+// frontier).  The destinations of the lane's 8 edges are the consecutive
+// indices kid0 .. kid0 + 7 at most, so one or two bitmap words cover them.
+// The bitmap only gains bits during a run, so a stale word only costs work.
+template <int APP>
+__device__ __forceinline__ uint32_t lane_live(const PullParams& P, uint2 meta, unsigned o, int nvalid) {
+    const uint32_t vmask = (nvalid >= kEPL) ? 0xFFu : ((1u << nvalid) - 1u);
+    if constexpr (APP != kBFS) {
+        return vmask;
+    } else {
+        if (!P.visk || nvalid == 0) return vmask;
+        const uint32_t heads = meta.x;
+        const uint32_t kid0 = meta.y + __popc(heads & ~1u & ((2u << o) - 1u));
+        const uint32_t* wp = P.visk + (kid0 >> 5);
+        unsigned long long win = wp[0];
+        if ((kid0 & 31) > 32 - kEPL) win |= (unsigned long long)wp[1] << 32;
+        win >>= (kid0 & 31);
+        const uint32_t hn = heads >> (o + 1);
+        uint32_t live = 0;
+#pragma unroll
+        for (int i = 0; i < kEPL; ++i) {
+            const unsigned r = __popc(hn & ((1u << i) - 1u));
+            live |= (((unsigned)(win >> r) & 1u) ^ 1u) << i;
+        }
+        return live & vmask;
+    }
+}
+
+// A lane's 8 consecutive edges (and weights) straight from global memory;
+// a half whose edges are all skipped (live) is not loaded.
 template <int APP>
 __device__ __forceinline__ void load_lane_edges(const PullParams& P, unsigned long long e_lane, int nvalid,
-                                                uint32_t (&sv)[kEPL], uint32_t (&wv)[kEPL]) {
+                                                uint32_t live, uint32_t (&sv)[kEPL], uint32_t (&wv)[kEPL]) {
     if (nvalid == kEPL) {
-        const uint4 a = ld_stream(P.src + e_lane);
-        const uint4 b = ld_stream(P.src + e_lane + 4);
+        uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+        if (live & 0x0Fu) a = ld_stream(P.src + e_lane);
+        if (live & 0xF0u) b = ld_stream(P.src + e_lane + 4);
         sv[0] = a.x; sv[1] = a.y; sv[2] = a.z; sv[3] = a.w;
         sv[4] = b.x; sv[5] = b.y; sv[6] = b.z; sv[7] = b.w;
         if constexpr (APP == kSSSP) {
@@ -438,7 +491,7 @@ __device__ __forceinline__ void load_lane_edges(const PullParams& P, unsigned lo
     } else {
 #pragma unroll
         for (int i = 0; i < kEPL; ++i) {
-            sv[i] = i < nvalid ? P.src[e_lane + i] : 0u;
+            sv[i] = ((live >> i) & 1u) ? P.src[e_lane + i] : 0u;
             wv[i] = 0;
             if constexpr (APP == kSSSP) wv[i] = i < nvalid ? P.w[e_lane + i] : 0u;
         }
@@ -466,6 +519,7 @@ __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned 
     uint2 meta = make_uint2(0u, 0u);
     unsigned next_head = 1u;
     int nvalid = 0;
+    uint32_t live = 0;
     unsigned long long c = 0;
     auto fetch = [&](unsigned long long sl) {
         c = sl * kSliceC + q;
@@ -479,7 +533,8 @@ __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned 
             meta = __ldg(P.cmeta + c);
             next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
         }
-        load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
+        live = lane_live<APP>(P, meta, 8 * sub, nvalid);
+        load_lane_edges<APP>(P, e_lane, nvalid, live, sv, wv);
     };
     if (gw < nslices) fetch(gw);
     for (unsigned long long sl = gw; sl < nslices; sl += nw) {
@@ -492,9 +547,11 @@ __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned 
         const uint2 cmeta = meta;
         const unsigned cnh = next_head;
         const int cnv = nvalid;
+        const uint32_t clive = live;
         const unsigned long long cc = c;
         fetch(sl + nw);
-        process_slice<APP>(P, it, cur, next, cs, cw, cnv, cc, cmeta, cnh, q > 0, my_kid, my_val, st, s_lcnt, s_list);
+        process_slice<APP>(P, it, cur, next, cs, cw, cnv, clive, cc, cmeta, cnh, q > 0, my_kid, my_val, st, s_lcnt,
+                           s_list);
     }
 }
 
@@ -525,25 +582,25 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
         const bool contig = q > 0 && pvalid && uvalid && c == cprev + 1;
         const unsigned long long e_lane = c * 32 + 8 * sub;
         int nvalid = 0;
-        if (uvalid) {
-            const long long left = (long long)P.E - (long long)e_lane;
-            nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
-        }
-        uint32_t sv[kEPL], wv[kEPL];
-        load_lane_edges<APP>(P, e_lane, nvalid, sv, wv);
         uint2 meta = make_uint2(0u, 0u);
         unsigned next_head = 1u;
         if (uvalid) {
+            const long long left = (long long)P.E - (long long)e_lane;
+            nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
             meta = __ldg(P.cmeta + c);
             next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
         }
-        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, contig, my_kid, my_val, st, s_lcnt,
-                           s_list);
+        const uint32_t live = lane_live<APP>(P, meta, 8 * sub, nvalid);
+        uint32_t sv[kEPL], wv[kEPL];
+        load_lane_edges<APP>(P, e_lane, nvalid, live, sv, wv);
+        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, contig, my_kid, my_val, st,
+                           s_lcnt, s_list);
     }
 }
 
 template <int APP, bool TMA>
-__global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDirectMinBlocks) k_pull(const PullParams P) {
+__global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direct_min_blocks(APP))
+    k_pull(const PullParams P) {
     using T = typename Traits<APP>::T;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_F;
@@ -670,8 +727,9 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : kDire
                 // the stage is no longer read past this point
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + s);
-                process_slice<APP>(P, it, cur, next, sv, wv, nvalid, c, meta, next_head, q > 0, my_kid, my_val,
-                                   st, &s_lcnt, s_list);
+                const uint32_t live = lane_live<APP>(P, meta, 8 * (lane & 3), nvalid);
+                process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, q > 0, my_kid,
+                                   my_val, st, &s_lcnt, s_list);
             }
         }
     }
@@ -975,9 +1033,11 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
 // Run start: values, initial frontier F_0, records 0 and 1, control block.
 __global__ void k_run_init(int app, uint32_t V, uint32_t root, uint32_t* vals, uint32_t* bm0, uint32_t* bm1,
                            uint32_t* wb, unsigned long long wb_words, IterRec* rec, RunCtl* C, RunCtl init,
-                           uint32_t* list0) {
+                           uint32_t* list0, uint32_t* visk, unsigned long long visk_words) {
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    if (app == kBFS)  // nothing visited: the root's own in-edges are pulled and find it set
+        for (unsigned long long i = tid; i < visk_words; i += nth) visk[i] = 0u;
     for (unsigned long long v = tid; v < V; v += nth)
         vals[v] = (app == kCC) ? (uint32_t)v : ((uint32_t)v == root ? 0u : kInf);
     const unsigned long long words = ((unsigned long long)V + 31) / 32;
@@ -1494,6 +1554,8 @@ static wedge_status configure_pulls(wedge_graph* g) {
     return WEDGE_OK;
 }
 
+static uint64_t visk_words(const wedge_graph* g) { return ((uint64_t)g->NZ + 31) / 32 + 1; }
+
 wedge_status ensure_run_scratch(wedge_graph* g) {
     if (g->ctl) return WEDGE_OK;
     const uint64_t V = g->V, NC = g->NC;
@@ -1507,6 +1569,7 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[1], (V + 1) * 4));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->visk, visk_words(g) * 4));
     g->rec_cap = kDefaultMaxIters + 2;
     WEDGE_TRY(dev_alloc(g, (void**)&g->rec, (uint64_t)g->rec_cap * sizeof(IterRec)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->ctl, sizeof(RunCtl)));
@@ -1567,6 +1630,7 @@ static PullParams pull_params(wedge_graph* g, int trace, int app = kCC) {
     P.flist[1] = g->flist[1];
     P.lseg = g->lseg;
     P.bstat = g->bstat;
+    P.visk = app == kBFS ? g->visk : nullptr;
     return P;
 }
 
@@ -1737,7 +1801,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words, g->rec,
-                                              g->ctl, init, g->flist[0]);
+                                              g->ctl, init, g->flist[0], g->visk, visk_words(g));
     PullParams P = pull_params(g, trace, app);
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, P.mlp,
                                                     P.gf);
@@ -1769,6 +1833,7 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
                                                        g->ms_seen, levels, g->bm[0]);
     PullParams P = pull_params(g, 0, kBFS);
     P.mlp = nullptr;
+    P.visk = nullptr;  // per-query visits live in the seen masks
     P.fb[0] = g->ms_fb[0];
     P.fb[1] = g->ms_fb[1];
     P.seen = g->ms_seen;
@@ -2110,6 +2175,8 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!g->snap_vals) WEDGE_TRY(dev_alloc(g, (void**)&g->snap_vals, (uint64_t)g->V * 4));
+    if (!g->snap_visk) WEDGE_TRY(dev_alloc(g, (void**)&g->snap_visk, visk_words(g) * 4));
+    const uint64_t kbytes = visk_words(g) * 4;
     const uint32_t limit = max_iters ? (max_iters < kDefaultMaxIters ? max_iters : kDefaultMaxIters)
                                      : kDefaultMaxIters;
     RunCtl init{};
@@ -2122,7 +2189,8 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
     P.mlp = nullptr;
     XformParams X = xform_params(g, 0);
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb,
-                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->flist[0]);
+                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->flist[0], g->visk,
+                                              visk_words(g));
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);
     count_launch(2);
@@ -2141,6 +2209,8 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                          h_features + ((size_t)t * kCandidates + c) * kMlpIn);
         h_chosen[t] = hr.mode ? hr.k + 1 : 0;
         WEDGE_TRY_CUDA(cudaMemcpyAsync(g->snap_vals, g->vals, vbytes, cudaMemcpyDeviceToDevice, s));
+        if (app == kBFS)
+            WEDGE_TRY_CUDA(cudaMemcpyAsync(g->snap_visk, g->visk, kbytes, cudaMemcpyDeviceToDevice, s));
         for (int c = 0; c <= kCandidates; ++c) {
             // c < kCandidates: time candidate c; c == kCandidates: advance
             IterRec cr = hr;
@@ -2149,6 +2219,8 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                 cr.k = c > 0 ? (unsigned)(c - 1) : hr.k;
             }
             WEDGE_TRY_CUDA(cudaMemcpyAsync(g->vals, g->snap_vals, vbytes, cudaMemcpyDeviceToDevice, s));
+            if (app == kBFS)
+                WEDGE_TRY_CUDA(cudaMemcpyAsync(g->visk, g->snap_visk, kbytes, cudaMemcpyDeviceToDevice, s));
             // a previous candidate's pull marked its frontier in the next bitmap
             WEDGE_TRY_CUDA(cudaMemsetAsync(g->bm[(t + 1) & 1], 0, ((uint64_t)g->V + 31) / 32 * 4, s));
             k_ctl_init<<<1, 32, 0, s>>>(g->ctl, hc);

@@ -267,6 +267,7 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->pieces);
     dev_free(g->flist[0]);
     dev_free(g->flist[1]);
+    dev_free(g->visk);
     dev_free(g->lseg);
     dev_free(g->bstat);
     dev_free(g->rec);
@@ -278,6 +279,7 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->split_bm);
     dev_free(g->mlp_bf16);
     dev_free(g->snap_vals);
+    dev_free(g->snap_visk);
     dev_free(g->ms_fb[0]);
     dev_free(g->ms_fb[1]);
     dev_free(g->ms_seen);
