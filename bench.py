@@ -220,15 +220,28 @@ def main():
         if args.profile_case == "cc-dense":
             print(json.dumps(roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)))
         elif args.profile_case == "step":
+            # the step's kernels with the profiler on only around the steps
+            # (ncu --profile-from-start off); BFS, CC and SSSP run their
+            # iterations through the host-polled loop (traced runs: the same
+            # kernels and launch shapes) so that every launch is visible
             o = [wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")]
+            for x in o:
+                x.trace = 1
             out = torch.empty(g.V, dtype=torch.int32, device=dev)
             r = torch.empty(g.V, dtype=torch.float32, device=dev)
-            for _ in range(args.steps):
+
+            def one():
                 wedge.wedge_run_bfs(G.handle, 0, out, o[0], False)
                 wedge.wedge_run_cc(S.handle, out, o[1], False)
                 wedge.wedge_run_sssp(G.handle, 0, out, o[2], False)
                 wedge.wedge_run_pr(G.handle, r, PR_ITERS, DAMPING, None, False)
+            one()
             torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+            for _ in range(args.steps):
+                one()
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
         elif args.profile_case == "pr":
             r = torch.empty(g.V, dtype=torch.float32, device=dev)
             for _ in range(2):
@@ -348,10 +361,12 @@ def main():
         per_app[name]["iters"] = sx.iters
         per_app[name]["sparse_iters"] = sx.sparse_iters
 
-    # roofline of the dominant kernel: the dense pull, measured on the
-    # PageRank pull (20 of them per step) with CUDA events around single
-    # launches through the pull entry point on the same stream
-    roof = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
+    # roofline of the dominant kernel, PageRank's dense pull (20 launches per
+    # step), with CUDA events around single launches through its entry point
+    # on the same stream; and of the first dense CC pull
+    roof = roofline_pr_pull(wedge, torch, G, g, stream, dev, clk.summary())
+    roof["share_of_step"] = PR_ITERS * roof["ms"] / ms_per_step
+    roof_cc = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -359,7 +374,7 @@ def main():
             "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp+pr{PR_ITERS}",
                        "V": V, "E": g.E, "E_sym": s.E, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20)},
-            "per_app": per_app, "roofline": roof, "gpu_launches": int(launches),
+            "per_app": per_app, "roofline": roof, "roofline_cc_dense_pull": roof_cc, "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_measure(wedge, torch, g, s, od, edges, args, dev)
@@ -518,6 +533,68 @@ def bench_grid(args, wedge, torch, dev, world):
     return line
 
 
+# DRAM traffic of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+# and a digest of the kernel sources it was measured on: reported only while
+# those sources are unchanged.
+TRAFFIC = {"pr": (320955136, "b060e7c00ebd782a"), "cc": (607611392, "b060e7c00ebd782a")}
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("engine.cu", "common.cuh", "tma.cuh", "mlp.cuh"):
+        with open(os.path.join(ROOT, "paper_1903_07754_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key):
+    val, digest = TRAFFIC[key]
+    return val if val is not None and digest == _kernel_digest() else None
+
+
+def _gather_bound(torch, dev, edges, t, clocks):
+    """Every edge costs one random gather, and each distinct 128-byte line a
+    gather instruction touches is one L1 wavefront; the L1 data pipe retires
+    one wavefront per clock per SM (ncu: l1tex__data_pipe_lsu_wavefronts)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = sms * mhz * 1e6 / 1e9
+    achieved = edges / t / 1e9
+    return {"unit": "G gathers/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x 1 L1 wavefront/clock"}
+
+
+def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
+    """PageRank's dense pull (k_pull<PR>) on the contributions of pr0, one
+    launch per CUDA-event pair (the sums are zeroed outside the pair)."""
+    V, E = g.V, g.E
+    od = torch.from_numpy(g.outdeg().astype(np.float32)).to(dev)
+    contrib = torch.where(od > 0, (1.0 / V) / torch.clamp(od, min=1.0), torch.zeros_like(od)).contiguous()
+    sums = torch.zeros(V, dtype=torch.int64, device=dev)
+    times = []
+    for r in range(12):
+        sums.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wedge.wedge_pr_pull(G.handle, contrib, sums)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    t = float(np.mean(times)) / 1e3
+    # algorithmic bytes: offsets 4(V+1), sources 4E, each contribution
+    # gathered once 4V (V*4 <= L2), 64-bit fixed-point sums written 8V
+    alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
+    peak, kind = peaks()
+    achieved = alg / t / 1e9
+    return {"kernel": "k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic("pr"), "alg_bytes": alg, "ms": t * 1e3,
+            "gather_bound": _gather_bound(torch, dev, E, t, clocks)}
+
+
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     """Dense CC pull on the symmetric graph from the initial labels (every
     destination changes), one launch per CUDA-event pair."""
@@ -550,7 +627,8 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     achieved = alg / t / 1e9
     return {"kernel": "k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "bound": "hbm",
             "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "alg_bytes": alg, "ms": t * 1e3}
+            "traffic": _traffic("cc"), "alg_bytes": alg, "ms": t * 1e3,
+            "gather_bound": _gather_bound(torch, dev, E, t, None)}
 
 
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev):

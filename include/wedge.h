@@ -248,6 +248,15 @@ wedge_status wedge_run_sssp(wedge_graph_t g, uint32_t root, uint32_t* d_dist,
  * on the schedule. */
 wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float damping,
                           const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+/* The in-edge pass of one PageRank iteration on its own (the dense pull of
+ * Sections 2.1 and 3.2 with PageRank's sum): on return
+ *   d_sums[v] = sum over in-edges (u, v) of round(d_contrib[u] * 2^62),
+ * an exact 64-bit fixed-point sum (1.0 = 2^62) that does not depend on the
+ * schedule.  d_contrib: V floats (device), finite, >= 0, and small enough
+ * that every sum stays below 4.0 (pr(u)/outdeg(u) always is); not checked.
+ * d_sums: V uint64 (device), must hold zeros on entry; vertices without
+ * in-edges keep 0.  Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums, wedge_stream_t stream);
 
 /* ---- Learned switch (not in the paper) --------------------------------
  * A cost model replaces the fixed fullness threshold and the fixed

@@ -55,6 +55,7 @@ def _load():
             "or_sssp_push": (None, [u32, p, p, p, p, u32, p]),
             "or_pr_pull": (None, [u32, p, p, p, dbl, u32, p]),
             "or_pr_push": (None, [u32, p, p, dbl, u32, p]),
+            "or_in_sums": (None, [u32, p, p, p, p]),
             "or_wedge_groups_scan": (u64, [u64, p, p, u64, p]),
             "or_edge_index": (u64, [u32, u64, p, p, u64, p, p]),
             "or_wedge_groups_index": (u64, [u32, p, p, p, u64, p]),
@@ -135,6 +136,16 @@ def pr_pull(g, damping: float = 0.85, iters: int = 20) -> np.ndarray:
     pr = np.empty(V, dtype=np.float64)
     _load().or_pr_pull(V, _P(off), _P(src), _P(od), damping, iters, _P(pr))
     return pr
+
+
+def in_sums(g, x) -> np.ndarray:
+    """FP64 in-edge sums of the per-vertex values x (PageRank's in-edge pass
+    when x = pr/outdeg)."""
+    _, off, src = _graph(g)
+    xx = _c(np.asarray(x, dtype=np.float64), np.float64)
+    out = np.empty(int(g.V), dtype=np.float64)
+    _load().or_in_sums(int(g.V), _P(off), _P(src), _P(xx), _P(out))
+    return out
 
 
 def pr_push(g, damping: float = 0.85, iters: int = 20) -> np.ndarray:

@@ -269,6 +269,17 @@ void or_pr_pull(uint32_t V, const uint32_t* off, const uint32_t* src, const uint
     free(contrib);
 }
 
+/* The pull's aggregation on its own (Section 2.1): out[v] = sum of x[u]
+ * over the in-edges (u, v), in FP64, in CSC order.  PageRank's in-edge pass
+ * is this with x[u] = pr(u)/outdeg(u). */
+void or_in_sums(uint32_t V, const uint32_t* off, const uint32_t* src, const double* x, double* out) {
+    for (uint32_t v = 0; v < V; ++v) {
+        double sum = 0.0;
+        for (uint64_t p = off[v]; p < off[v + 1]; ++p) sum += x[src[p]];
+        out[v] = sum;
+    }
+}
+
 /* PageRank in FP64, push form: scatter pr(u)/outdeg(u) along out-edges. */
 void or_pr_push(uint32_t V, const uint64_t* csr_off, const uint32_t* csr_dst, double d,
                 uint32_t iters, double* pr) {

@@ -1412,24 +1412,57 @@ __global__ void k_pr_init(uint32_t V, const uint32_t* __restrict__ outdeg, float
     block_add_u64(dang, &C->dangling[0]);
 }
 
+// One vertex of the PageRank step: rank from the fixed-point in-edge sum,
+// the next contribution, and the dangling mass it adds.
+__device__ __forceinline__ void pr_vertex(unsigned long long a, uint32_t od, float dv, float base, float d, int last,
+                                          float& out, float& contrib, unsigned long long& dang) {
+    const float pr = fmaf(d, __ull2float_rn(a) * 0x1p-62f + dv, base);
+    if (last) {
+        out = pr;
+    } else {
+        contrib = od ? pr / (float)od : 0.0f;
+        if (!od) dang += __float2ull_rn(pr * 0x1p62f);
+    }
+}
+
+// The vertex step, four consecutive vertices per thread and iteration with
+// 16- and 32-byte accesses (a grid-stride scalar loop kept too few bytes in
+// flight to reach HBM rates).  Sums of destinations split across pull
+// slices are zeroed for the next pull's atomics.
 __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, const uint32_t* __restrict__ split_bm,
                            unsigned long long* __restrict__ acc, float* __restrict__ contrib,
                            float* __restrict__ out, RunCtl* C, unsigned t, int last, float base, float d) {
     const float dv = __ull2float_rn(__ldcg(&C->dangling[t & 1])) * 0x1p-62f / (float)V;
     unsigned long long dang = 0;
-    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
-         v += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long nq = V / 4;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const unsigned long long v = 4 * q;
+        const ulonglong2 a01 = reinterpret_cast<const ulonglong2*>(acc)[2 * q];
+        const ulonglong2 a23 = reinterpret_cast<const ulonglong2*>(acc)[2 * q + 1];
+        const uint4 od = last ? make_uint4(0u, 0u, 0u, 0u) : reinterpret_cast<const uint4*>(outdeg)[q];
+        const uint32_t split = (__ldg(split_bm + (v >> 5)) >> (v & 31)) & 0xFu;
+        if (split) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((split >> i) & 1u) acc[v + i] = 0ull;
+        }
+        float4 o, c;
+        pr_vertex(a01.x, od.x, dv, base, d, last, o.x, c.x, dang);
+        pr_vertex(a01.y, od.y, dv, base, d, last, o.y, c.y, dang);
+        pr_vertex(a23.x, od.z, dv, base, d, last, o.z, c.z, dang);
+        pr_vertex(a23.y, od.w, dv, base, d, last, o.w, c.w, dang);
+        if (last) reinterpret_cast<float4*>(out)[q] = o;
+        else reinterpret_cast<float4*>(contrib)[q] = c;
+    }
+    // the tail of V mod 4 vertices
+    for (unsigned long long v = 4 * nq + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V; v += stride) {
         const unsigned long long a = acc[v];
         if ((__ldg(split_bm + (v >> 5)) >> (v & 31)) & 1u) acc[v] = 0ull;
-        const float s = __ull2float_rn(a) * 0x1p-62f + dv;
-        const float pr = fmaf(d, s, base);
-        if (last) {
-            out[v] = pr;
-        } else {
-            const uint32_t od = outdeg[v];
-            contrib[v] = od ? pr / (float)od : 0.0f;
-            if (!od) dang += __float2ull_rn(pr * 0x1p62f);
-        }
+        float o = 0.f, c = 0.f;
+        pr_vertex(a, last ? 0u : outdeg[v], dv, base, d, last, o, c, dang);
+        if (last) out[v] = o;
+        else contrib[v] = c;
     }
     if (!last) block_add_u64(dang, &C->dangling[(t + 1) & 1]);
 }
@@ -2000,6 +2033,24 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
     return WEDGE_OK;
 }
 
+wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums, wedge_stream_t stream) {
+    if (!g || !d_contrib || !d_sums) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // a dense pull at iteration 0; the caller's zeros take the place of the
+    // vertex step that clears split destinations between iterations
+    k_standalone_prep<<<1, 32, 0, s>>>(g->rec, g->ctl, 0, 0, 0, nullptr, 0);
+    PullParams P = pull_params(g, 0, kPR);
+    P.contrib = d_contrib;
+    P.acc = reinterpret_cast<unsigned long long*>(d_sums);
+    P.pr_iter = 0;
+    launch_pull_app(g, kPR, P, s);
+    count_launch();
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    g->last_stream = s;
+    return WEDGE_OK;
+}
+
 wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query, uint32_t nroots,
                                  uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts_in, wedge_stats* stats,
                                  wedge_stream_t stream) {
@@ -2209,7 +2260,7 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                          h_features + ((size_t)t * kCandidates + c) * kMlpIn);
         h_chosen[t] = hr.mode ? hr.k + 1 : 0;
         WEDGE_TRY_CUDA(cudaMemcpyAsync(g->snap_vals, g->vals, vbytes, cudaMemcpyDeviceToDevice, s));
-        if (app == kBFS)
+        if (app == WEDGE_BFS)
             WEDGE_TRY_CUDA(cudaMemcpyAsync(g->snap_visk, g->visk, kbytes, cudaMemcpyDeviceToDevice, s));
         for (int c = 0; c <= kCandidates; ++c) {
             // c < kCandidates: time candidate c; c == kCandidates: advance
@@ -2219,7 +2270,7 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
                 cr.k = c > 0 ? (unsigned)(c - 1) : hr.k;
             }
             WEDGE_TRY_CUDA(cudaMemcpyAsync(g->vals, g->snap_vals, vbytes, cudaMemcpyDeviceToDevice, s));
-            if (app == kBFS)
+            if (app == WEDGE_BFS)
                 WEDGE_TRY_CUDA(cudaMemcpyAsync(g->visk, g->snap_visk, kbytes, cudaMemcpyDeviceToDevice, s));
             // a previous candidate's pull marked its frontier in the next bitmap
             WEDGE_TRY_CUDA(cudaMemsetAsync(g->bm[(t + 1) & 1], 0, ((uint64_t)g->V + 31) / 32 * 4, s));

@@ -68,6 +68,7 @@ EXPORTS = [
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
+    "wedge_pr_pull",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
+        "wedge_pr_pull": (st, [P, P, P, P]),
         "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
                               ctypes.POINTER(wedge_stats), P]),
         "wedge_get_trace": (st, [P, ctypes.POINTER(wedge_iter_record), u32, ctypes.POINTER(u32)]),
@@ -233,6 +235,12 @@ def wedge_run_pr(handle, rank, iters=20, damping=0.85, opts=None, want_stats=Tru
     _check(load().wedge_run_pr(handle, _ptr(rank), int(iters), float(damping), _opts(opts),
                                ctypes.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
+
+
+def wedge_pr_pull(handle, contrib, sums, stream=None):
+    """One PageRank in-edge pass: sums (int64 view of uint64, zeroed by the
+    caller) = exact 2^-62 fixed-point in-edge sums of contrib (float32)."""
+    _check(load().wedge_pr_pull(handle, _ptr(contrib), _ptr(sums), _stream(stream)))
 
 
 def wedge_get_trace(handle, cap=1 << 16):

@@ -154,6 +154,27 @@ def test_pagerank_l1(rmat, rmat_dev):
     assert torch.equal(rank, rank2)
 
 
+@pytest.mark.parametrize("which", ["rmat", "sym"])
+def test_pr_pull_in_sums(rmat, rmat_dev, sym, sym_dev, which):
+    """PageRank's in-edge pass alone: the exact 2^-62 fixed-point sums
+    against the oracle's FP64 in-edge sums of the same FP32 values; a sum of
+    n terms differs by at most n/2 units of 2^-62 plus FP64 rounding."""
+    g, G = (rmat, rmat_dev) if which == "rmat" else (sym, sym_dev)
+    x = (np.random.default_rng(7).random(g.V) / g.V).astype(np.float32)
+    sums = torch.zeros(g.V, dtype=torch.int64, device="cuda")
+    wedge.wedge_pr_pull(G.handle, torch.from_numpy(x).cuda(), sums)
+    got = sums.cpu().numpy().view(np.uint64)
+    want = oracle.in_sums(g, x.astype(np.float64))
+    indeg = np.diff(g.offsets.astype(np.int64))
+    err = np.abs(got.astype(np.float64) * 2.0**-62 - want)
+    assert np.all(err <= (indeg + 1) * 2.0**-62 + 4e-16 * want), err.max()
+    assert np.all(got[indeg == 0] == 0)
+    # same values, same sums: the schedule does not show
+    again = torch.zeros_like(sums)
+    wedge.wedge_pr_pull(G.handle, torch.from_numpy(x).cuda(), again)
+    assert torch.equal(sums, again)
+
+
 def test_pull_iterate_bfs_step(rmat, rmat_dev):
     """One BFS iteration from the oracle's level-t state, dense and over the
     Wedge Frontier, yields exactly the level-(t+1) set."""

@@ -59,3 +59,26 @@ def test_fixed_point_matches_networkx():
     want = np.array([ref[v] for v in range(g.V)])
     got = oracle.pr_pull(g, 0.85, 400)
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_in_sums_hand_graph_and_identities():
+    # 0->2, 1->2, 3->2, 2->0: in-sums by hand
+    g = gg.from_edges(4, [0, 1, 3, 2], [2, 2, 2, 0])
+    x = np.array([1.0, 10.0, 100.0, 1000.0])
+    np.testing.assert_array_equal(oracle.in_sums(g, x), [100.0, 0.0, 1011.0, 0.0])
+    # every source value is counted once per out-edge
+    h = gg.rmat(10, 8, seed=5)
+    y = np.random.default_rng(1).random(h.V)
+    od = oracle.outdeg(h).astype(np.float64)
+    assert abs(oracle.in_sums(h, y).sum() - (y * od).sum()) < 1e-9 * (y * od).sum()
+
+
+def test_in_sums_is_pagerank_first_pass():
+    # with d = 1, one PageRank iterate is the in-edge sum of pr0/outdeg plus D/V
+    g = gg.rmat(10, 8, seed=6)
+    V = g.V
+    od = oracle.outdeg(g)
+    pr0 = np.full(V, 1.0 / V)
+    contrib = np.where(od > 0, pr0 / np.maximum(od, 1), 0.0)
+    D = pr0[od == 0].sum()
+    np.testing.assert_allclose(oracle.in_sums(g, contrib) + D / V, oracle.pr_pull(g, 1.0, 1), rtol=1e-13, atol=0)
