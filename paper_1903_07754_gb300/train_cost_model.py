@@ -1,7 +1,7 @@
 """Trains the learned switch's cost model on the GPU and writes
 `cost_model.npy` (and `cost_model.json`, a summary) next to this file.
 
-Training mix: R-MAT scales 18, 20 and 22 (edge factor 16) with a in
+Training mix: R-MAT scales 18, 20, 22 and 24 (edge factor 16) with a in
 {0.45, 0.57, 0.70} (b = c = (1-a)*0.19/0.43, d the rest), and rewired grids
 (1024^2 and 2048^2, p = 0.01), BFS and SSSP from seeded roots and CC on the
 symmetrised graph, every candidate timed at every iteration (up to 128 per
@@ -54,7 +54,7 @@ def grid_case(n, p, seed):
 def main():
     quick = "--quick" in sys.argv
     wedge.load()
-    scales = (16, 17) if quick else (18, 20, 22)
+    scales = (16, 17) if quick else (18, 20, 22, 24)
     t0 = time.time()
     train = []
     for i, scale in enumerate(scales):
