@@ -331,6 +331,13 @@ wedge_status wedge_get_trace(wedge_graph_t g, wedge_iter_record* out, uint32_t c
  * accounting of device work). */
 uint64_t wedge_kernel_launches(void);
 
+/* Device memory of the library (graphs, their scratch) comes from one
+ * memory pool per GPU that keeps what destroyed graphs release, so a new
+ * graph maps no new memory.  This returns the kept memory of `device`
+ * (-1: every GPU) to the driver.  Memory of live graphs is not touched.
+ * Errors: INVALID_ARG (device < -1), CUDA. */
+wedge_status wedge_trim_memory(int device);
+
 const char* wedge_last_error(void);
 const char* wedge_version(void);
 

@@ -202,6 +202,9 @@ void count_launch(uint64_t n = 1);
 // Allocation helper that records the bytes owned by g.
 wedge_status dev_alloc(wedge_graph* g, void** p, size_t bytes);
 void dev_free(void* p);
+wedge_status trim_pools(int device);
+void* pinned_small_alloc(size_t bytes);  // at most 256 bytes; nullptr on failure
+void pinned_small_free(void* p);
 
 // Exclusive scan of n uint32 values into out[0..n] (out[n] = total), on the
 // device, using tmp scratch of scan_tmp_words(n) words.  Totals must fit in

@@ -777,6 +777,29 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
 //     entry b at coarsening k) and append every newly set bit to the list:
 //     the bitmap removes duplicates (Section 4).
 // ------------------------------------------------------------------------
+// The warp's rows (lane L: row start rb, length rl, np pieces, exclusive
+// piece offset excl among the warp's pieces) written as pieces of at most 32
+// entries to pieces[slot0 ...] by all 32 lanes: piece i goes to the lane
+// whose range holds it (binary search over the lanes' offsets), so one long
+// row (a hub's) is written by the whole warp.
+__device__ __forceinline__ void write_pieces(uint2* pieces, unsigned slot0, unsigned total, uint32_t rb, uint32_t rl,
+                                             unsigned excl) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned i0 = 0; i0 < total; i0 += 32) {
+        const unsigned i = i0 + lane;
+        unsigned jx = 0;
+#pragma unroll
+        for (unsigned stp = 16; stp >= 1; stp >>= 1) {
+            const unsigned ex = __shfl_sync(kFull, excl, jx + stp);
+            if (ex <= i) jx += stp;
+        }
+        const uint32_t b = __shfl_sync(kFull, rb, jx);
+        const uint32_t l = __shfl_sync(kFull, rl, jx);
+        const unsigned q = (i - __shfl_sync(kFull, excl, jx)) * 32u;
+        if (i < total) pieces[slot0 + i] = make_uint2(b + q, min(32u, l - q));
+    }
+}
+
 // Warp-level scan of bitmap words [gw*32, ...) step nw*32: pieces of the
 // active vertices' edge-index rows, one reservation per warp on *npieces.
 __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V, unsigned long long words,
@@ -802,11 +825,27 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
         if (!total) continue;
         unsigned slot = 0;
         if (lane == 31) slot = atomicAdd(npieces, total);
-        slot = __shfl_sync(kFull, slot, 31) + incl - np;
-        for (uint32_t w = word; w; w &= w - 1) {
-            const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
-            const uint32_t rb = __ldg(eidx_off + u), rl = __ldg(eidx_off + u + 1) - rb;
-            for (uint32_t qq = 0; qq < rl; qq += 32) pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
+        slot = __shfl_sync(kFull, slot, 31);
+        // one vertex per lane and round: every round's rows go out together
+        unsigned rem = word, done = 0;
+        while (__any_sync(kFull, rem != 0)) {
+            uint32_t rb = 0, rl = 0;
+            if (rem) {
+                const uint32_t u = (uint32_t)(wi * 32 + __ffs(rem) - 1);
+                rem &= rem - 1;
+                rb = __ldg(eidx_off + u);
+                rl = __ldg(eidx_off + u + 1) - rb;
+            }
+            const unsigned p = (rl + 31u) >> 5;
+            unsigned pi = p;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(kFull, pi, d);
+                if (lane >= (unsigned)d) pi += y;
+            }
+            const unsigned rt = __shfl_sync(kFull, pi, 31);
+            write_pieces(pieces, slot + done, rt, rb, rl, pi - p);
+            done += rt;
         }
     }
 }
@@ -835,8 +874,8 @@ __device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n
         if (!total) continue;
         unsigned slot = 0;
         if (lane == 31) slot = atomicAdd(npieces, total);
-        slot = __shfl_sync(kFull, slot, 31) + incl - np;
-        for (uint32_t qq = 0; qq < rl; qq += 32) pieces[slot++] = make_uint2(rb + qq, min(32u, rl - qq));
+        slot = __shfl_sync(kFull, slot, 31);
+        write_pieces(pieces, slot, total, rb, rl, incl - np);
     }
 }
 
@@ -865,14 +904,19 @@ __device__ __forceinline__ void clear_frontier(uint32_t* bm, unsigned long long 
 
 // Warp-level expansion of n pieces: Wedge bitmap bits (entry = chunk >> k),
 // fresh bits appended to list with a warp-aggregated reservation on *count.
+// A warp task is up to 32 pieces, fewer when there are too few pieces to
+// give every warp a task (one hub's row): a task's entries are walked 32 at
+// a time, so its length is the latency that matters.
 __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw) {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
+    const unsigned long long per = (unsigned long long)n / nw;
+    const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
+    for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
         const unsigned long long idx = base + lane;
-        const uint2 pc = idx < n ? __ldcg(pieces + idx) : make_uint2(0u, 0u);
+        const uint2 pc = (lane < ppt && idx < n) ? __ldcg(pieces + idx) : make_uint2(0u, 0u);
         unsigned incl = pc.y;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -893,13 +937,32 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
             }
             const unsigned st = __shfl_sync(kFull, pc.x, jx);
             const unsigned ex = __shfl_sync(kFull, excl, jx);
-            bool fresh = false;
-            uint32_t b = 0;
-            if (act) {
-                b = __ldg(eidx + st + (e - ex)) >> k;
-                const uint32_t bit = 1u << (b & 31);
-                fresh = (atomicOr(wb + (b >> 5), bit) & bit) == 0;
+            // Lanes are runs of consecutive rows' entries, so neighbouring
+            // lanes often hit the same bitmap word (always for a hub's row
+            // at coarse precision).  Each run of lanes on one word sets its
+            // bits with one atomicOr by the run's last lane; within the
+            // run, the first lane holding an entry owns it, and it is fresh
+            // if the word did not have its bit before.
+            const uint32_t b = act ? __ldg(eidx + st + (e - ex)) >> k : 0xFFFFFFFFu;
+            const uint32_t word = b >> 5;
+            const uint32_t bit = act ? 1u << (b & 31) : 0u;
+            const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
+            const unsigned starts = __ballot_sync(kFull, lane == 0 || word != wprev);
+            const unsigned rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
+            const unsigned above = starts & ~(lt_mask | (1u << lane));
+            const unsigned re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
+            uint32_t bits = bit;
+#pragma unroll
+            for (unsigned d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, bits, d);
+                if (lane >= rs + d) bits |= y;
             }
+            uint32_t old = 0;
+            if (lane == re && act) old = atomicOr(wb + word, bits);
+            old = __shfl_sync(kFull, old, re);
+            const unsigned run = (re == 31 ? kFull : ((2u << re) - 1u)) & ~((1u << rs) - 1u);
+            const unsigned same = __match_any_sync(kFull, b) & run;
+            const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
             const unsigned m = __ballot_sync(kFull, fresh);
             if (m) {
                 const unsigned leader = __ffs(m) - 1;
@@ -1607,7 +1670,9 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->rec, (uint64_t)g->rec_cap * sizeof(IterRec)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->ctl, sizeof(RunCtl)));
     WEDGE_TRY_CUDA(cudaMemset(g->ctl, 0, sizeof(RunCtl)));
-    WEDGE_TRY_CUDA(cudaMallocHost((void**)&g->h_ctl, sizeof(RunCtl)));
+    static_assert(sizeof(RunCtl) <= 256, "control block mirror must fit a pinned block");
+    g->h_ctl = static_cast<RunCtl*>(pinned_small_alloc(sizeof(RunCtl)));
+    if (!g->h_ctl) return set_error(WEDGE_ERR_OUT_OF_MEMORY, "pinned host memory for the control block");
     memset(g->h_ctl, 0, sizeof(RunCtl));
     WEDGE_TRY(dev_alloc(g, (void**)&g->contrib, V * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->acc, V * 8));

@@ -272,7 +272,7 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->bstat);
     dev_free(g->rec);
     dev_free(g->ctl);
-    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    pinned_small_free(g->h_ctl);
     dev_free(g->contrib);
     dev_free(g->acc);
     dev_free(g->rank);
@@ -470,14 +470,15 @@ wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offset
     cudaStream_t s = (cudaStream_t)stream;
     wedge_graph* g = new wedge_graph();
     cudaGetDevice(&g->device);
-    cudaDeviceProp prop;
-    cudaError_t e = cudaGetDeviceProperties(&prop, g->device);
+    int sms = 0, smem = 0;  // two attributes: far cheaper than the whole property set
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device);
     if (e != cudaSuccess) {
         delete g;
-        return cuda_error(e, "cudaGetDeviceProperties");
+        return cuda_error(e, "cudaDeviceGetAttribute");
     }
-    g->num_sms = prop.multiProcessorCount;
-    g->smem_per_sm = prop.sharedMemPerMultiprocessor;
+    g->num_sms = sms;
+    g->smem_per_sm = (size_t)smem;
     g->V = V;
     g->E = E;
     g->NC = (E + kChunk - 1) / kChunk;

@@ -260,6 +260,25 @@ def test_small_and_degenerate_graphs(idx):
         G.close()
 
 
+def test_graphs_reuse_pooled_memory_and_trim():
+    """Graph memory comes from the library's pool: create/destroy cycles and
+    a trim in between leave every run exact."""
+    g = gg.rmat(12, 8, seed=11).with_weights(255)
+    want = oracle.sssp_dijkstra(g, 0)
+    for i in range(4):
+        G = graph(g)
+        try:
+            got, _ = _run(G, "sssp", 0, opts("sssp"))
+            np.testing.assert_array_equal(got, want)
+        finally:
+            G.close()
+        if i == 1:
+            wedge.wedge_trim_memory(-1)
+    wedge.wedge_trim_memory(0)
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_trim_memory(-2)
+
+
 def test_host_buffers_and_caller_edge_index():
     """Host (numpy) CSC and outputs go through the same entry points; a
     caller-supplied edge index gives the same results as the built one."""
