@@ -127,7 +127,6 @@ struct wedge_graph {
     uint2* pieces = nullptr;       // transformation work pieces
     uint32_t* flist[2] = {nullptr, nullptr};  // frontier vertex lists by iteration parity
     uint32_t* visk = nullptr;      // BFS: visited destinations by index into vid, ceil(NZ/32)+1 words
-    uint32_t* lseg = nullptr;      // per-block list segments of the last pull
     wedge::BlockStat* bstat = nullptr;  // per-block results of the last pull
     wedge::IterRec* rec = nullptr; // per-iteration records
     uint32_t rec_cap = 0;

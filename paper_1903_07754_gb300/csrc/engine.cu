@@ -20,6 +20,10 @@
 namespace wedge {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+// Sparse BFS pulls over fewer listed chunks than this do not check visited
+// destinations (measured on the rewired 4096^2 grid: the extra dependent
+// load cost 4% there, while R-MAT's large sparse pulls gain from the check).
+constexpr unsigned long long kSkipVisitedMinChunks = 1ull << 14;
 enum AppId { kBFS = 0, kCC = 1, kSSSP = 2, kPR = 3, kMSBFS = 4 };
 // Resident 256-thread blocks per SM that the register allocation of a
 // direct-load pull must allow.  Measured on R-MAT s22: 4 blocks (64
@@ -74,9 +78,10 @@ struct PullParams {
     uint32_t* levels;            // levels[v * Q + q]
     uint32_t Q;
     uint32_t* flist[2];          // frontier vertex lists by iteration parity
-    uint32_t* lseg;              // per-block list segments (kListCap each)
     BlockStat* bstat;            // per-block results
     uint32_t* visk;              // BFS runs: visited bit per destination index (nullptr: no skipping)
+    int decide;                  // runs: the pull's last block takes the decision for the next pull
+    cudaGraphConditionalHandle cond;  // device loop: the while node's condition (0 outside a graph)
 };
 
 struct XformParams {
@@ -356,63 +361,76 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
         }
     }
     __syncwarp();
-    for (unsigned r = lane; r < total; r += 32) {
-        const uint32_t kx = s_kid[r];
-        const T m = s_val[r];
-        const bool excl = kx >> 31;
-        const uint32_t dv = __ldg(P.vid + (kx & 0x7FFFFFFFu));
+    for (unsigned r0 = 0; r0 < total; r0 += 32) {
+        const unsigned r = r0 + lane;
         bool act = false;
-        if constexpr (APP == kBFS) {
-            if (P.vals[dv] == kInf) {
-                P.vals[dv] = it + 1;
-                act = set_bit(next, dv);
-                if (P.visk) {
-                    const uint32_t kid = kx & 0x7FFFFFFFu;
-                    atomicOr(P.visk + (kid >> 5), 1u << (kid & 31));
+        uint32_t dv = 0;
+        if (r < total) {
+            const uint32_t kx = s_kid[r];
+            const T m = s_val[r];
+            const bool excl = kx >> 31;
+            dv = __ldg(P.vid + (kx & 0x7FFFFFFFu));
+            if constexpr (APP == kBFS) {
+                if (P.vals[dv] == kInf) {
+                    P.vals[dv] = it + 1;
+                    act = set_bit(next, dv);
+                    if (P.visk) {
+                        const uint32_t kid = kx & 0x7FFFFFFFu;
+                        atomicOr(P.visk + (kid >> 5), 1u << (kid & 31));
+                    }
                 }
-            }
-        } else if constexpr (APP == kMSBFS) {
-            // queries reaching dv for the first time take level it+1
-            unsigned long long* nxt = (it & 1) ? P.fb[0] : P.fb[1];
-            unsigned long long fresh, prev;
-            if (excl) {
-                const unsigned long long old = __ldcg(P.seen + dv);
-                fresh = m & ~old;
-                if (fresh) P.seen[dv] = old | fresh;
-            } else {
-                fresh = m & ~atomicOr(P.seen + dv, m);
-            }
-            if (fresh) {
-                for (unsigned long long b = fresh; b; b &= b - 1)
-                    P.levels[(size_t)dv * P.Q + (__ffsll((long long)b) - 1)] = it + 1;
+            } else if constexpr (APP == kMSBFS) {
+                // queries reaching dv for the first time take level it+1
+                unsigned long long* nxt = (it & 1) ? P.fb[0] : P.fb[1];
+                unsigned long long fresh, prev;
                 if (excl) {
-                    prev = __ldcg(nxt + dv);
-                    nxt[dv] = prev | fresh;
+                    const unsigned long long old = __ldcg(P.seen + dv);
+                    fresh = m & ~old;
+                    if (fresh) P.seen[dv] = old | fresh;
                 } else {
-                    prev = atomicOr(nxt + dv, fresh);
+                    fresh = m & ~atomicOr(P.seen + dv, m);
                 }
-                act = prev == 0ull && set_bit(next, dv);
-            }
-        } else if constexpr (APP == kPR) {
-            if (excl) P.acc[dv] = m;
-            else if (m) atomicAdd(P.acc + dv, m);
-        } else {
-            bool changed;
-            if (excl) {
-                const uint32_t old = P.vals[dv];
-                changed = m < old;
-                if (changed) P.vals[dv] = m;
+                if (fresh) {
+                    for (unsigned long long b = fresh; b; b &= b - 1)
+                        P.levels[(size_t)dv * P.Q + (__ffsll((long long)b) - 1)] = it + 1;
+                    if (excl) {
+                        prev = __ldcg(nxt + dv);
+                        nxt[dv] = prev | fresh;
+                    } else {
+                        prev = atomicOr(nxt + dv, fresh);
+                    }
+                    act = prev == 0ull && set_bit(next, dv);
+                }
+            } else if constexpr (APP == kPR) {
+                if (excl) P.acc[dv] = m;
+                else if (m) atomicAdd(P.acc + dv, m);
             } else {
-                changed = m < atomicMin(P.vals + dv, m);
+                bool changed;
+                if (excl) {
+                    const uint32_t old = P.vals[dv];
+                    changed = m < old;
+                    if (changed) P.vals[dv] = m;
+                } else {
+                    changed = m < atomicMin(P.vals + dv, m);
+                }
+                act = changed && set_bit(next, dv);
             }
-            act = changed && set_bit(next, dv);
+            if (act) {
+                st.F += __ldg(P.outdeg + dv);
+                st.n += 1;
+                st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
+            }
         }
-        if (act) {
-            st.F += __ldg(P.outdeg + dv);
-            st.n += 1;
-            st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
-            const unsigned slot = atomicAdd(s_lcnt, 1u);  // the block's frontier list
-            if (slot < (unsigned)kListCap) s_list[slot] = dv;
+        // the block's frontier list: one reservation per warp and round,
+        // none once the block's stage has overflowed (PageRank has none)
+        const unsigned am = (APP == kPR) ? 0u : __ballot_sync(kFull, act);
+        if (am && *reinterpret_cast<volatile unsigned*>(s_lcnt) <= (unsigned)kListCap) {
+            const unsigned leader = __ffs(am) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(s_lcnt, (unsigned)__popc(am));
+            base = __shfl_sync(kFull, base, leader);
+            const unsigned slot = base + __popc(am & ((1u << lane) - 1u));
+            if (act && slot < (unsigned)kListCap) s_list[slot] = dv;
         }
     }
     __syncwarp();
@@ -445,12 +463,13 @@ constexpr int pull_smem_bytes(bool tma) {
 // indices kid0 .. kid0 + 7 at most, so one or two bitmap words cover them.
 // The bitmap only gains bits during a run, so a stale word only costs work.
 template <int APP>
-__device__ __forceinline__ uint32_t lane_live(const PullParams& P, uint2 meta, unsigned o, int nvalid) {
+__device__ __forceinline__ uint32_t lane_live(const PullParams& P, uint2 meta, unsigned o, int nvalid,
+                                              bool skip_visited = true) {
     const uint32_t vmask = (nvalid >= kEPL) ? 0xFFu : ((1u << nvalid) - 1u);
     if constexpr (APP != kBFS) {
         return vmask;
     } else {
-        if (!P.visk || nvalid == 0) return vmask;
+        if (!P.visk || !skip_visited || nvalid == 0) return vmask;
         const uint32_t heads = meta.x;
         const uint32_t kid0 = meta.y + __popc(heads & ~1u & ((2u << o) - 1u));
         const uint32_t* wp = P.visk + (kid0 >> 5);
@@ -567,6 +586,9 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
     const unsigned long long nunits = (unsigned long long)nchunks << k;
     const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
     const unsigned long long kmask = (1ull << k) - 1;
+    // a small pull is bound by its chain of dependent loads: the visited
+    // check would add one more link than the gathers it saves
+    const bool skip_visited = nunits >= kSkipVisitedMinChunks;
     for (unsigned long long sl = gw; sl < nslices; sl += nw) {
         const unsigned long long j = sl * kSliceC + q;
         bool uvalid = j < nunits;
@@ -590,13 +612,15 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
             meta = __ldg(P.cmeta + c);
             next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
         }
-        const uint32_t live = lane_live<APP>(P, meta, 8 * sub, nvalid);
+        const uint32_t live = lane_live<APP>(P, meta, 8 * sub, nvalid, skip_visited);
         uint32_t sv[kEPL], wv[kEPL];
         load_lane_edges<APP>(P, e_lane, nvalid, live, sv, wv);
         process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, contig, my_kid, my_val, st,
                            s_lcnt, s_list);
     }
 }
+
+__device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nblocks, float* dsm);
 
 template <int APP, bool TMA>
 __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direct_min_blocks(APP))
@@ -606,7 +630,11 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     __shared__ unsigned long long s_F;
     __shared__ unsigned s_n, s_row, s_lcnt;
     RunCtl* C = P.ctl;
-    if (C->done) return;
+    if (C->done) {
+        // nothing left to pull: end the device loop
+        if (P.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(P.cond, 0u);
+        return;
+    }
     const unsigned it = C->it;
     const unsigned mode = P.rec[it].mode;
     const unsigned k = P.rec[it].k;
@@ -750,8 +778,12 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
             atomicAdd(&s_row, st.row);
         }
     }
+    // this block's frontier sums go to its own slot; its staged frontier
+    // list goes to a range of the next list reserved with one atomic (none
+    // if the stage overflowed: the list then stays short of the frontier
+    // and the transformation scans the bitmap instead)
+    __shared__ unsigned s_lbase;
     __syncthreads();
-    // this block's results and frontier-list segment go to its own slot
     if (threadIdx.x == 0) {
         BlockStat b;
         b.F = s_F;
@@ -760,10 +792,22 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
         b.lcnt = s_lcnt;
         b.pad_ = 0;
         P.bstat[blockIdx.x] = b;
+        s_lbase = (s_lcnt && s_lcnt <= (unsigned)kListCap) ? atomicAdd(&P.rec[it + 1].nlist, s_lcnt) : ~0u;
     }
-    if (s_lcnt <= (unsigned)kListCap)
-        for (unsigned i = threadIdx.x; i < s_lcnt; i += blockDim.x)
-            P.lseg[(size_t)blockIdx.x * kListCap + i] = s_list[i];
+    __syncthreads();
+    publish_list(P.flist[(it + 1) & 1], s_list, s_lcnt, s_lbase);
+    if (P.decide) {
+        __shared__ unsigned s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            decide_after_pull(P, it, gridDim.x, reinterpret_cast<float*>(smem));
+            if (threadIdx.x == 0) C->ticket = 0;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -1127,115 +1171,56 @@ __global__ void k_run_init(int app, uint32_t V, uint32_t root, uint32_t* vals, u
     }
 }
 
-// Decision step, one block of 1024 threads after each pull: sums the pull
-// blocks' slots into the record of the next iteration, takes the fullness
-// decision (or the learned switch's), and, when the next iteration pulls
-// over the Wedge Frontier and every block's list segment fit, packs the
-// segments into one frontier list for the transformation.  Then the device
-// loop's control: count this body execution and keep looping while the
-// frontier is non-empty, never more than max_iters + 2 times (h = 0 outside
-// a graph).
-__global__ void __launch_bounds__(1024) k_decide(IterRec* rec, RunCtl* C, const BlockStat* __restrict__ bstat,
-                                                 unsigned nblocks, const uint32_t* __restrict__ lseg,
-                                                 uint32_t* list0, uint32_t* list1, const __nv_bfloat16* mlp,
-                                                 GraphFeat gf, int trace, cudaGraphConditionalHandle h) {
-    __shared__ float dsm[2 * kCandidates * kMlpHidden + 8];
-    __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row, s_over, s_tot;
-    __shared__ unsigned s_wsum[32];
-    __shared__ unsigned s_start[kMaxPullBlocks];
-    if (!C->done) {
-        const unsigned it = C->it;
-        if (threadIdx.x == 0) {
-            s_F = 0;
-            s_n = 0;
-            s_row = 0;
-            s_over = 0;
-        }
-        __syncthreads();
-        // each thread owns a contiguous run of slots
-        const unsigned per = (nblocks + blockDim.x - 1) / blockDim.x;
-        const unsigned b0 = threadIdx.x * per, b1 = min(nblocks, b0 + per);
-        unsigned long long F = 0;
-        unsigned n = 0, row = 0, cnt = 0, over = 0;
-        for (unsigned b = b0; b < b1; ++b) {
-            const BlockStat st = bstat[b];
-            F += st.F;
-            n += st.n;
-            row += st.row;
-            cnt += st.lcnt;
-            over |= st.lcnt > (unsigned)kListCap;
-        }
-        for (int d = 16; d > 0; d >>= 1) {
-            F += __shfl_down_sync(kFull, F, d);
-            n += __shfl_down_sync(kFull, n, d);
-            row += __shfl_down_sync(kFull, row, d);
-            over |= __shfl_down_sync(kFull, over, d);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&s_F, F);
-            atomicAdd(&s_n, n);
-            atomicAdd(&s_row, row);
-            atomicOr(&s_over, over);
-        }
-        __syncthreads();
-        IterRec* r = rec + it + 1;
-        if (threadIdx.x == 0) {
-            r->fullness = s_F;
-            r->nfront = s_n;
-            r->rowsum = s_row;
-            r->nlist = 0;
-            if (trace) rec[it].t_pull1 = global_timer();
-        }
-        __syncthreads();
-        decide_block(rec, C, it + 1, mlp, gf, dsm);
-        __syncthreads();
-        if (r->mode && !s_over && s_n) {
-            // exclusive prefix of the segment lengths (thread runs, then warps)
-            const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            unsigned incl = cnt;
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned y = __shfl_up_sync(kFull, incl, d);
-                if (lane >= (unsigned)d) incl += y;
-            }
-            if (lane == 31) s_wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                const unsigned nw = blockDim.x >> 5;
-                unsigned x = lane < nw ? s_wsum[lane] : 0u, xi = x;
-                for (int d = 1; d < 32; d <<= 1) {
-                    const unsigned y = __shfl_up_sync(kFull, xi, d);
-                    if (lane >= (unsigned)d) xi += y;
-                }
-                s_wsum[lane] = xi - x;
-                if (lane == 31) s_tot = xi;
-            }
-            __syncthreads();
-            unsigned pos = s_wsum[warp] + incl - cnt;
-            for (unsigned b = b0; b < b1; ++b) {
-                s_start[b] = pos;
-                pos += bstat[b].lcnt;
-            }
-            __syncthreads();
-            // copy entry i from the segment whose range holds it (binary search)
-            uint32_t* out = ((it + 1) & 1) ? list1 : list0;
-            const unsigned tot = s_tot;
-            for (unsigned i = threadIdx.x; i < tot; i += blockDim.x) {
-                unsigned lo = 0, hi = nblocks - 1;
-                while (lo < hi) {
-                    const unsigned mid = (lo + hi + 1) >> 1;
-                    if (s_start[mid] <= i) lo = mid;
-                    else hi = mid - 1;
-                }
-                out[i] = lseg[(size_t)lo * kListCap + (i - s_start[lo])];
-            }
-            if (threadIdx.x == 0) r->nlist = tot;
-        }
+// Decision step (Section 3.4, Fig. 5), taken by the last pull block to
+// finish (a block ticket): sums the pull blocks' slots into the record of
+// the next iteration and takes the fullness decision (or the learned
+// switch's).  Then the device loop's control: count this body execution and
+// keep looping while the frontier is non-empty, never more than
+// max_iters + 2 times.  `dsm` (the cost model's activations) lives in the
+// block's record buffer, free once the block's own slices are done.
+__device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nblocks, float* dsm) {
+    __shared__ unsigned long long d_F;
+    __shared__ unsigned d_n, d_row;
+    IterRec* rec = P.rec;
+    RunCtl* C = P.ctl;
+    if (threadIdx.x == 0) {
+        d_F = 0;
+        d_n = 0;
+        d_row = 0;
     }
+    __syncthreads();
+    // the slots were written by other blocks of this launch: read through L2
+    unsigned long long F = 0;
+    unsigned n = 0, row = 0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        F += __ldcg(&P.bstat[b].F);
+        n += __ldcg(&P.bstat[b].n);
+        row += __ldcg(&P.bstat[b].row);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        F += __shfl_down_sync(kFull, F, d);
+        n += __shfl_down_sync(kFull, n, d);
+        row += __shfl_down_sync(kFull, row, d);
+    }
+    if ((threadIdx.x & 31) == 0 && n) {
+        atomicAdd(&d_F, F);
+        atomicAdd(&d_n, n);
+        atomicAdd(&d_row, row);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        IterRec* r = rec + it + 1;
+        r->fullness = d_F;
+        r->nfront = d_n;
+        r->rowsum = d_row;
+        if (P.trace) rec[it].t_pull1 = global_timer();
+    }
+    __syncthreads();
+    decide_block(rec, C, it + 1, P.mlp, P.gf, dsm);
     if (threadIdx.x == 0) {
         const unsigned loops = ++C->loops;
         const bool more = !C->done && loops < C->max_iters + 2;
-        if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
+        if (P.cond) cudaGraphSetConditional(P.cond, more ? 1u : 0u);
     }
 }
 
@@ -1685,7 +1670,8 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     int nb = 0;
     for (int a = 0; a < 4; ++a) nb = std::max(nb, std::max(g->pull_blocks_app[a], g->pull_blocks_tma[a]));
     if (nb > kMaxPullBlocks) return set_error(WEDGE_ERR_NOT_SUPPORTED, "too many pull blocks for this device");
-    WEDGE_TRY(dev_alloc(g, (void**)&g->lseg, (uint64_t)nb * kListCap * 4));
+    static_assert((2 * kCandidates * kMlpHidden + 8) * 4 <= pull_records_bytes<kBFS>(),
+                  "the decision's activations live in the pull's record buffer");
     WEDGE_TRY(dev_alloc(g, (void**)&g->bstat, (uint64_t)nb * sizeof(BlockStat)));
     return WEDGE_OK;
 }
@@ -1726,9 +1712,10 @@ static PullParams pull_params(wedge_graph* g, int trace, int app = kCC) {
     P.dense_tma = g->tuning.dense_loader == 1 ? 1 : 0;
     P.flist[0] = g->flist[0];
     P.flist[1] = g->flist[1];
-    P.lseg = g->lseg;
     P.bstat = g->bstat;
     P.visk = app == kBFS ? g->visk : nullptr;
+    P.decide = (app == kBFS || app == kCC || app == kSSSP) ? 1 : 0;
+    P.cond = 0;
     return P;
 }
 
@@ -1757,13 +1744,6 @@ static XformParams xform_params(wedge_graph* g, int trace) {
 // Grid size of the pull variant that P selects.
 static unsigned pull_grid(const wedge_graph* g, int app, const PullParams& P) {
     return (unsigned)(P.dense_tma ? g->pull_blocks_tma[app] : g->pull_blocks_app[app]);
-}
-
-static void launch_decide(const wedge_graph* g, int app, const PullParams& P, cudaGraphConditionalHandle h,
-                          cudaStream_t s) {
-    k_decide<<<1, 1024, 0, s>>>(g->rec, g->ctl, g->bstat, pull_grid(g, app, P), g->lseg, g->flist[0], g->flist[1],
-                                P.mlp, P.gf, P.trace, h);
-    count_launch();
 }
 
 static void launch_xform(const wedge_graph* g, const XformParams& X, cudaStream_t s) {
@@ -1797,9 +1777,9 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
     cudaStream_t cs = g->cap_stream;
     WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     PullParams P = pull_params(g, 0, app);
+    P.cond = handle;
     XformParams X = xform_params(g, 0);
     launch_pull_app(g, app, P, cs);
-    launch_decide(g, app, P, handle, cs);
     launch_xform(g, X, cs);
     cudaError_t le = cudaGetLastError();
     cudaGraph_t captured = nullptr;
@@ -1858,7 +1838,6 @@ static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, cons
     for (;;) {
         for (int b = 0; b < batch; ++b) {
             launch_pull_app(g, app, P, s);
-            launch_decide(g, app, P, 0, s);
             launch_xform(g, X, s);
         }
         launched += batch;
@@ -1932,6 +1911,7 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     PullParams P = pull_params(g, 0, kBFS);
     P.mlp = nullptr;
     P.visk = nullptr;  // per-query visits live in the seen masks
+    P.decide = 0;      // the persistent launch takes its own decisions
     P.fb[0] = g->ms_fb[0];
     P.fb[1] = g->ms_fb[1];
     P.seen = g->ms_seen;
@@ -2230,6 +2210,7 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     const unsigned cap = (unsigned)((g->NC + (1ull << log2_coarsen) - 1) >> log2_coarsen);
     k_standalone_prep<<<1, 32, 0, s>>>(g->rec, g->ctl, iter, sparse, log2_coarsen, d_chunk_count, cap);
     PullParams P = pull_params(g, 0);
+    P.decide = 0;  // one pull: k_standalone_out reduces the block slots
     P.vals = d_values;
     P.bm[iter & 1] = const_cast<uint32_t*>(d_cur_bitmap ? d_cur_bitmap : d_next_bitmap);
     P.bm[(iter + 1) & 1] = d_next_bitmap;
@@ -2346,7 +2327,6 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
             launch_xform(g, X, s);
             launch_pull_app(g, app, P, s);
             WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
-            if (c == kCandidates) launch_decide(g, app, P, 0, s);  // advance with the threshold's choice
             WEDGE_TRY_CUDA(cudaGetLastError());
             if (c < kCandidates) {
                 WEDGE_TRY_CUDA(cudaEventSynchronize(g->ev1));

@@ -144,9 +144,13 @@ __global__ void k_chunk_meta(const uint32_t* __restrict__ off, uint32_t V, const
 
 // One warp per chunk: the sources that appear in the chunk, each counted once
 // (__match_any_sync groups equal sources; the lowest lane of a group keeps it).
+// The counting pass also adds each group's size to the source's out-degree
+// when outdeg is given (one atomic per distinct source and chunk instead of
+// one per edge).
 template <bool FILL>
 __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64_t NC,
-                            uint32_t* __restrict__ counter, uint32_t* __restrict__ eidx) {
+                            uint32_t* __restrict__ counter, uint32_t* __restrict__ eidx,
+                            uint32_t* __restrict__ outdeg) {
     const unsigned lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -163,6 +167,7 @@ __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64
             eidx[pos] = (uint32_t)c;
         } else {
             atomicAdd(&counter[s], 1u);
+            if (outdeg) atomicAdd(&outdeg[s], (unsigned)__popc(same));
         }
     }
 }
@@ -268,7 +273,6 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->flist[0]);
     dev_free(g->flist[1]);
     dev_free(g->visk);
-    dev_free(g->lseg);
     dev_free(g->bstat);
     dev_free(g->rec);
     dev_free(g->ctl);
@@ -333,7 +337,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     WEDGE_TRY(validate(g, s));  // CSC only: no index yet
     WEDGE_TRY(dev_alloc(g, (void**)&g->outdeg, (uint64_t)V * 4));
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->outdeg, 0, (uint64_t)V * 4, s));
-    if (E) {
+    if (E && user_eoff) {  // otherwise the edge-index counting pass counts them
         k_outdeg<<<grid_for(E, 256, sms), 256, 0, s>>>(g->src, E, g->outdeg);
         count_launch();
     }
@@ -406,7 +410,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         WEDGE_TRY_CUDA(cudaMemsetAsync(tmp, 0, ((uint64_t)V + 1) * 4, s));
         const unsigned eg = grid_for(NC * 32, 256, sms);
         if (NC) {
-            k_eidx_pass<false><<<eg, 256, 0, s>>>(g->src, E, NC, tmp, nullptr);
+            k_eidx_pass<false><<<eg, 256, 0, s>>>(g->src, E, NC, tmp, nullptr, g->outdeg);
             count_launch();
         }
         WEDGE_TRY(exclusive_scan_u32(tmp, g->eidx_off, V, nullptr, s));
@@ -417,7 +421,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         // cursor = eidx_off; fill rows
         WEDGE_TRY_CUDA(cudaMemcpyAsync(knz, g->eidx_off, ((uint64_t)V + 1) * 4, cudaMemcpyDeviceToDevice, s));
         if (NC) {
-            k_eidx_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, knz, g->eidx);
+            k_eidx_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, knz, g->eidx, nullptr);
             count_launch();
         }
     }
