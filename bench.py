@@ -123,43 +123,76 @@ def peaks():
 # --------------------------------------------------------------------------
 # Reference arm: the oracle on the host cores
 # --------------------------------------------------------------------------
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
+REF_BUDGET_S = 90.0   # timed seconds of the reference arm at most
+
+
+def reference_units(g, s, od):
+    """The reference arm's bounded samples of the step, in rotation: the
+    oracle's full-size BFS (push), CC (union-find), SSSP (Dijkstra) and two
+    PageRank iterations (FP64 pull); each returns the edges it is credited
+    with, counted as in our arm."""
     import oracle
+
+    def bfs():
+        return credited_edges(od, oracle.bfs_push(g, 0) != 0xFFFFFFFF)
+
+    def cc():
+        oracle.cc_union_find(s)
+        return s.E
+
+    def sssp():
+        return credited_edges(od, oracle.sssp_dijkstra(g, 0) != 0xFFFFFFFF)
+
+    def pr2():
+        oracle.pr_pull(g, DAMPING, 2)
+        return 2 * g.E
+    return [("bfs", bfs), ("cc", cc), ("sssp", sssp), ("pr2", pr2)]
+
+
+def reduce_max(value, world, device):
+    """Max over ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores, rank 0 only (other ranks exit at
+    once).  A step is one bounded sample (reference_units, in rotation);
+    steps stop early once REF_BUDGET_S timed seconds are spent, so the run
+    ends within a few minutes for any --steps."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
     g, s = make_inputs(args.scale)
     od = oracle.outdeg(g)
-    oracle.build()
-
-    def step():
+    units = reference_units(g, s, od)
+    for i in range(min(max(args.warmup, 0), 1)):
+        units[i % len(units)][1]()
+    t_total, edges, done = 0.0, 0, 0
+    while done < args.steps and (t_total < REF_BUDGET_S or done < len(units)):
         t0 = time.perf_counter()
-        lvl = oracle.bfs_push(g, 0)
-        lab = oracle.cc_union_find(s)
-        dist = oracle.sssp_dijkstra(g, 0)
-        pr = oracle.pr_pull(g, DAMPING, args.ref_pr_iters)
-        t = time.perf_counter() - t0
-        edges = (credited_edges(od, lvl != 0xFFFFFFFF) + s.E + credited_edges(od, dist != 0xFFFFFFFF)
-                 + args.ref_pr_iters * g.E)
-        return t, edges, (lvl, lab, dist, pr)
-
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        step()
-    times, edges = [], 0
-    for _ in range(args.steps):
-        t, e, _ = step()
-        times.append(t)
-        edges += e
-    total = sum(times)
-    value = edges / total / 1e9
-    sample = (f"oracle (single-threaded C) on the full workload: push BFS, union-find CC, Dijkstra SSSP, "
-              f"FP64 pull PageRank with {args.ref_pr_iters} iterations; {args.steps} steps")
+        edges += units[done % len(units)][1]()
+        t_total += time.perf_counter() - t0
+        done += 1
+    value = edges / t_total / 1e9
+    sample = (f"oracle (single-threaded C) on the full-size graphs, one unit per step in rotation: push BFS, "
+              f"union-find CC, Dijkstra SSSP, 2 FP64 PageRank iterations; {done} of {args.steps} steps "
+              f"({t_total:.1f} s timed, budget {REF_BUDGET_S:.0f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "steps": done, "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * t_total / done,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-            "data": "synthetic", "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc+sssp+pr"},
+            "data": "synthetic", "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp+pr{PR_ITERS}"},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------------------
@@ -305,10 +338,7 @@ def main():
         barrier()
     launches = wedge.wedge_kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms = float(t_local.item())
+    ms = reduce_max(ms, world, dev)
     ms_per_step = ms / args.steps
     value = world * step_edges * args.steps / (ms / 1e3) / 1e9
 
@@ -527,6 +557,22 @@ def bench_grid(args, wedge, torch, dev, world):
             total_e += edges
             total_ms += t
         G.close()
+    # multi-hop study (Section 5.2, "Frontier Precision"): with in-place
+    # updates, coarser Wedge Frontier entries pull more superfluous edges but
+    # carry distances several hops per iteration
+    g = gg.grid(4096, 0.01).with_weights(1000)
+    G = wedge.Graph.from_csc(g)
+    out = torch.empty(g.V, dtype=torch.int32, device=dev)
+    study = {}
+    for k in (0, 2, 4, 6):
+        o = wedge.wedge_default_opts("sssp")
+        o.log2_coarsen = k
+        o.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
+        t = _events(torch, lambda: wedge.wedge_run_sssp(G.handle, 0, out, o, False), 2)
+        st = wedge.wedge_run_sssp(G.handle, 0, out, o)
+        study[f"k{k}"] = {"ms": t, "iters": st.iters, "edges_pulled": st.edges_pulled}
+    G.close()
+    res["sssp_p0.01_always_sparse_by_precision"] = study
     line = _base_line("GTEPS (BFS+SSSP) on the 4096^2 grid", total_e / (total_ms / 1e3) / 1e9, "GTEPS", total_ms, 2,
                       world, {"workload": "grid-4096x4096: p=0.01 bfs+sssp, p=0 bfs"})
     line["per_app"] = res
