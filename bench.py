@@ -111,6 +111,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -342,33 +345,48 @@ def main():
     ms_per_step = ms / args.steps
     value = world * step_edges * args.steps / (ms / 1e3) / 1e9
 
-    # per-app times, Wedge (default options) against dense pull every iteration
+    # per-app ms/run (median of 10 runs after 2 warm-ups, CUDA events per
+    # run) in every mode: Wedge with the fixed threshold (default options),
+    # dense pull every iteration, Wedge Frontier every iteration, learned
     per_app = {}
     dense = {a: wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")}
+    sparse = {a: wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")}
     for a in dense.values():
         a.switch_mode = wedge.SWITCH_ALWAYS_DENSE
+    for a in sparse.values():
+        a.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
 
-    def time_fn(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
+    def time_fn(fn, reps=10):
+        for _ in range(2):
             fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
 
     runs = {
         "bfs": (lambda o: wedge.wedge_run_bfs(G.handle, 0, lvl, o, False), o_bfs, dense["bfs"]),
         "cc": (lambda o: wedge.wedge_run_cc(S.handle, lab, o, False), o_cc, dense["cc"]),
         "sssp": (lambda o: wedge.wedge_run_sssp(G.handle, 0, dist_, o, False), o_sssp, dense["sssp"]),
     }
+    stat_fn = {"bfs": lambda o: wedge.wedge_run_bfs(G.handle, 0, lvl, o),
+               "cc": lambda o: wedge.wedge_run_cc(S.handle, lab, o),
+               "sssp": lambda o: wedge.wedge_run_sssp(G.handle, 0, dist_, o)}
     for name, (fn, ow, odn) in runs.items():
         t_w = time_fn(lambda: fn(ow))
         t_d = time_fn(lambda: fn(odn))
+        t_s = time_fn(lambda: fn(sparse[name]))
+        sd = stat_fn[name](odn)
         per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "dense_pull_ms": t_d,
-                         "speedup_vs_dense_pull": t_d / t_w}
+                         "speedup_vs_dense_pull": t_d / t_w, "always_sparse_ms": t_s,
+                         "speedup_vs_always_sparse": t_s / t_w,
+                         "dense_pull_edges_per_s": sd.edges_pulled / (t_d / 1e3)}
     # learned switch (cost model trained by paper_1903_07754_gb300.train_cost_model)
     from paper_1903_07754_gb300 import costmodel
     if os.path.exists(costmodel.DEFAULT_MODEL):
@@ -391,6 +409,22 @@ def main():
         per_app[name]["iters"] = sx.iters
         per_app[name]["sparse_iters"] = sx.sparse_iters
 
+    # graph + edge-index build (setup, not in the step): device-resident CSC
+    build_ms = {}
+    for name, gx, wx in (("rmat", g, True), ("sym", s, False)):
+        dev_arr = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+                   for a in ((gx.offsets, gx.src, gx.w) if wx else (gx.offsets, gx.src))]
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = wedge.wedge_graph_create(gx.V, gx.E, *dev_arr)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+            wedge.wedge_graph_destroy(h)
+        build_ms[name] = float(np.median(ts))
+        del dev_arr
+
     # roofline of the dominant kernel, PageRank's dense pull (20 launches per
     # step), with CUDA events around single launches through its entry point
     # on the same stream; and of the first dense CC pull
@@ -404,7 +438,8 @@ def main():
             "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp+pr{PR_ITERS}",
                        "V": V, "E": g.E, "E_sym": s.E, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20)},
-            "per_app": per_app, "roofline": roof, "roofline_cc_dense_pull": roof_cc, "gpu_launches": int(launches),
+            "per_app": per_app, "graph_build_ms": build_ms, "roofline": roof, "roofline_cc_dense_pull": roof_cc,
+            "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_measure(wedge, torch, g, s, od, edges, args, dev)
@@ -582,7 +617,7 @@ def bench_grid(args, wedge, torch, dev, world):
 # DRAM traffic of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
 # and a digest of the kernel sources it was measured on: reported only while
 # those sources are unchanged.
-TRAFFIC = {"pr": (320955136, "b060e7c00ebd782a"), "cc": (607611392, "b060e7c00ebd782a")}
+TRAFFIC = {"pr": (321087744, "12f6668d5eb4580c"), "cc": (607208192, "12f6668d5eb4580c")}
 
 
 def _kernel_digest():
@@ -631,14 +666,25 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
             times.append(e0.elapsed_time(e1))
     t = float(np.mean(times)) / 1e3
     # algorithmic bytes: offsets 4(V+1), sources 4E, each contribution
-    # gathered once 4V (V*4 <= L2), 64-bit fixed-point sums written 8V
+    # gathered once 4V (V*4 <= L2), 64-bit fixed-point sums written 8V; the
+    # other count takes every gather as one 32-byte sector
     alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
+    alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 8 * V
+    return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", alg, alg_sectors, t, dev,
+                     _traffic("pr"), _gather_bound(torch, dev, E, t, clocks))
+
+
+def _roofline(kernel, alg, alg_sectors, t, dev, traffic, gather):
+    import torch
     peak, kind = peaks()
     achieved = alg / t / 1e9
-    return {"kernel": "k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "bound": "hbm",
-            "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic("pr"), "alg_bytes": alg, "ms": t * 1e3,
-            "gather_bound": _gather_bound(torch, dev, E, t, clocks)}
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "alg_bytes": alg, "ms": t * 1e3,
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+            "gathers_counted": f"once per vertex (V*4 <= L2 = {l2 >> 20} MB)",
+            "alg_bytes_gather_sectors": alg_sectors, "achieved_gather_sectors": alg_sectors / t / 1e9,
+            "gather_bound": gather}
 
 
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
@@ -669,12 +715,9 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     # label gathered once 4V (V*4 <= L2), destination labels read 4V,
     # changed labels written 4*changed, next-frontier bitmap V/8
     alg = 4 * (V + 1) + 4 * E + 4 * V + 4 * V + 4 * nchanged + V / 8
-    peak, kind = peaks()
-    achieved = alg / t / 1e9
-    return {"kernel": "k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "bound": "hbm",
-            "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic("cc"), "alg_bytes": alg, "ms": t * 1e3,
-            "gather_bound": _gather_bound(torch, dev, E, t, None)}
+    alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 4 * V + 4 * nchanged + V / 8
+    return _roofline("k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", alg, alg_sectors, t, dev,
+                     _traffic("cc"), _gather_bound(torch, dev, E, t, None))
 
 
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev):

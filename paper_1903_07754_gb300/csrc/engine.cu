@@ -631,8 +631,12 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     __shared__ unsigned s_n, s_row, s_lcnt;
     RunCtl* C = P.ctl;
     if (C->done) {
-        // nothing left to pull: end the device loop
-        if (P.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(P.cond, 0u);
+        // nothing left to pull: end the device loop (PageRank's pulls never
+        // decide, and carry no conditional-node code, so that profilers see
+        // them inside graphs)
+        if constexpr (APP != kPR) {
+            if (P.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(P.cond, 0u);
+        }
         return;
     }
     const unsigned it = C->it;
@@ -796,16 +800,18 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     }
     __syncthreads();
     publish_list(P.flist[(it + 1) & 1], s_list, s_lcnt, s_lbase);
-    if (P.decide) {
-        __shared__ unsigned s_last;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
-        __syncthreads();
-        if (s_last) {
+    if constexpr (APP != kPR) {
+        if (P.decide) {
+            __shared__ unsigned s_last;
             __threadfence();
-            decide_after_pull(P, it, gridDim.x, reinterpret_cast<float*>(smem));
-            if (threadIdx.x == 0) C->ticket = 0;
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                decide_after_pull(P, it, gridDim.x, reinterpret_cast<float*>(smem));
+                if (threadIdx.x == 0) C->ticket = 0;
+            }
         }
     }
 }
