@@ -1,0 +1,101 @@
+"""Parity at the full sizes of the benchmark's other configurations, in the
+launch configuration `bench.py` times, checked on the GPU by the equations
+that define the result (the oracle would take minutes per root here).
+
+BFS levels and SSSP distances from a root are the unique solution of
+Bellman's equations: d(root) = 0 and, for every other vertex,
+d(v) = min over in-edges (u, v) of d(u) + w(u, v) (w = 1 for BFS), with
+unreached vertices (and additions past the saturation value) at
+0xFFFFFFFF / 0xFFFFFFFE as the engine defines them.  Checking every vertex's
+equation therefore checks the whole output exactly.
+Workloads: R-MAT scale 24 with the learned switch (BFS, SSSP), the rewired
+4096^2 grid (BFS, SSSP) and R-MAT scale 26 batched BFS (64 roots; two
+queries checked)."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+from _gpu import graph, opts
+from paper_1903_07754_gb300 import costmodel, wedge
+
+pytestmark = pytest.mark.gpu
+
+INF = 0xFFFFFFFF
+SAT = 0xFFFFFFFE
+
+
+def _edges(g):
+    """(dst, src) per CSC position as int64 CUDA tensors."""
+    off = torch.from_numpy(g.offsets.astype(np.int64)).cuda()
+    src = torch.from_numpy(g.src.astype(np.int64)).cuda()
+    dst = torch.repeat_interleave(torch.arange(g.V, device="cuda"), off[1:] - off[:-1])
+    return dst, src
+
+
+def _bellman(dst, src, w, V, root, d):
+    """Asserts d (int64 CUDA, INF = unreached) solves Bellman's equations."""
+    du = d[src]
+    cand = torch.where(du == INF, torch.full_like(du, INF), torch.clamp(du + w, max=SAT))
+    best = torch.full((V,), INF, dtype=torch.int64, device="cuda").scatter_reduce(
+        0, dst, cand, reduce="amin", include_self=True)
+    best[root] = 0
+    bad = int((best != d).sum().item())
+    assert bad == 0, f"{bad} vertices violate the equations"
+    assert int((d != INF).sum().item()) > 1
+
+
+def _u32(t):
+    return t.to(torch.int64) & 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def g24():
+    return gg.rmat(24, 16).with_weights(255)
+
+
+def test_learned_switch_scale24(g24):
+    dst, src = _edges(g24)
+    w = torch.from_numpy(g24.w.astype(np.int64)).cuda()
+    G = graph(g24)
+    try:
+        wedge.wedge_set_cost_model(G.handle, costmodel.load_params())
+        out = torch.empty(g24.V, dtype=torch.int32, device="cuda")
+        st = wedge.wedge_run_bfs(G.handle, 0, out, opts("bfs", switch=wedge.SWITCH_LEARNED))
+        _bellman(dst, src, torch.ones_like(w), g24.V, 0, _u32(out))
+        assert st.iters > 1
+        wedge.wedge_run_sssp(G.handle, 0, out, opts("sssp", switch=wedge.SWITCH_LEARNED))
+        _bellman(dst, src, w, g24.V, 0, _u32(out))
+    finally:
+        G.close()
+
+
+def test_rewired_grid_4096():
+    g = gg.grid(4096, 0.01).with_weights(1000)
+    dst, src = _edges(g)
+    w = torch.from_numpy(g.w.astype(np.int64)).cuda()
+    G = graph(g)
+    try:
+        out = torch.empty(g.V, dtype=torch.int32, device="cuda")
+        wedge.wedge_run_bfs(G.handle, 0, out, opts("bfs"))
+        _bellman(dst, src, torch.ones_like(w), g.V, 0, _u32(out))
+        wedge.wedge_run_sssp(G.handle, 0, out, opts("sssp"))
+        _bellman(dst, src, w, g.V, 0, _u32(out))
+    finally:
+        G.close()
+
+
+def test_batched_bfs_scale26():
+    g = gg.rmat(26, 16)
+    roots = gg.roots(g, 64, seed=3)
+    G = graph(g, with_weights=False)
+    try:
+        lv = torch.empty(g.V * 64, dtype=torch.int32, device="cuda")
+        wedge.wedge_run_bfs_batch(G.handle, roots, None, 64, lv)
+        lv = lv.view(g.V, 64)
+        dst, src = _edges(g)
+        one = torch.ones(1, dtype=torch.int64, device="cuda").expand(src.numel())
+        for q in (0, 37):
+            _bellman(dst, src, one, g.V, int(roots[q]), _u32(lv[:, q].contiguous()))
+    finally:
+        G.close()
