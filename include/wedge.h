@@ -327,6 +327,17 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
  * Synchronises the stream of that run. */
 wedge_status wedge_get_trace(wedge_graph_t g, wedge_iter_record* out, uint32_t cap, uint32_t* n);
 
+/* Self-test of the bounded device waits (not in the paper).  Every wait in
+ * the library's kernels -- mbarrier phases of the staged pull, the grid
+ * barrier of the batched traversal -- gives up after 200 ms of device time
+ * and records a timeout that the call returns as WEDGE_ERR_TIMEOUT, leaving
+ * the device usable.  This runs one such wait that can never be satisfied
+ * on the current device: kind 0 = an mbarrier that receives one of two
+ * arrivals, kind 1 = a two-block grid barrier that one block never reaches.
+ * Synchronous.  Returns WEDGE_ERR_TIMEOUT when the wait gave up as it must
+ * (WEDGE_OK would mean it did not); INVALID_ARG for another kind; CUDA. */
+wedge_status wedge_selftest_timeout(int kind);
+
 /* Number of kernel launches the library has enqueued since load (for
  * accounting of device work). */
 uint64_t wedge_kernel_launches(void);

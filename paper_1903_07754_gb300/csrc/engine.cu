@@ -1294,6 +1294,26 @@ __device__ bool grid_sync(unsigned* bar, unsigned* status) {
     return s_ok != 0;
 }
 
+// Self-test of the bounded waits: each kernel waits for something that
+// never happens and must come back with kStatusTimeout.
+//  kind 0: an mbarrier expecting two arrivals receives one.
+//  kind 1: a grid barrier of two blocks where block 1 leaves without
+//          arriving (an ordinary launch: block 1 simply exits).
+__global__ void k_selftest_wait(int kind, unsigned* bar, unsigned* status) {
+    if (kind == 0) {
+        __shared__ __align__(8) uint64_t mb;
+        if (threadIdx.x == 0) {
+            mbar_init(&mb, 2);
+            fence_mbar_init();
+            mbar_arrive(&mb);
+            mbar_wait(&mb, 0, status);
+        }
+    } else {
+        if (blockIdx.x == 1) return;
+        grid_sync(bar, status);
+    }
+}
+
 __global__ void k_msbfs_clear(uint32_t V, unsigned long long* fb0, unsigned long long* fb1, unsigned long long* seen,
                               uint32_t* bm0, uint32_t* bm1, uint32_t* wb, unsigned long long wb_words, IterRec* rec,
                               RunCtl* C, RunCtl init, unsigned* bar) {
@@ -2099,6 +2119,25 @@ wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_
     count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());
     g->last_stream = s;
+    return WEDGE_OK;
+}
+
+wedge_status wedge_selftest_timeout(int kind) {
+    if (kind != 0 && kind != 1) return set_error(WEDGE_ERR_INVALID_ARG, "kind must be 0 or 1");
+    unsigned* d = nullptr;  // [status, barrier words ...]
+    WEDGE_TRY(dev_alloc(nullptr, (void**)&d, (1 + kBarWords) * sizeof(unsigned)));
+    cudaError_t e = cudaMemset(d, 0, (1 + kBarWords) * sizeof(unsigned));
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<kind == 0 ? 1 : 2, 32>>>(kind, d + 1, d);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    dev_free(d);
+    if (e != cudaSuccess) return cuda_error(e, "wait self-test");
+    if (status & kStatusTimeout) return set_error(WEDGE_ERR_TIMEOUT, "the self-test wait timed out, as it must");
     return WEDGE_OK;
 }
 

@@ -99,3 +99,38 @@ def test_batched_bfs_scale26():
             _bellman(dst, src, one, g.V, int(roots[q]), _u32(lv[:, q].contiguous()))
     finally:
         G.close()
+
+
+def test_more_than_2_31_edges():
+    """Edge positions past 2^31 (signed 32-bit overflow territory): a
+    structured graph with V = 2^26 and in-degree 32 (+ a ragged tail), built
+    on the device; BFS and SSSP checked through Bellman's equations."""
+    V, d, stride = 1 << 26, 32, 1 << 20
+    v = torch.arange(V, device="cuda", dtype=torch.int64)
+    j = torch.arange(d, device="cuda", dtype=torch.int64)
+    src2 = torch.sort((v[:, None] * 3 + j[None, :] * stride + 1) % V, dim=1).values
+    extra = torch.arange(5, 42, device="cuda", dtype=torch.int64)   # 37 more in-edges of the last vertex
+    last = torch.unique(torch.cat([src2[-1], extra]))
+    src = torch.cat([src2[:-1].reshape(-1), last]).to(torch.int32)
+    deg = torch.full((V,), d, device="cuda", dtype=torch.int64)
+    deg[-1] = last.numel()
+    off = torch.zeros(V + 1, device="cuda", dtype=torch.int64)
+    off[1:] = torch.cumsum(deg, 0)
+    E = int(off[-1].item())
+    assert E > 2**31
+    w = ((src.to(torch.int64) * 7 + torch.repeat_interleave(v, deg)) % 13 + 1).to(torch.int32)
+    off32 = off.to(torch.int32)
+    del src2
+    h = wedge.wedge_graph_create(V, E, off32, src, w)
+    G = wedge.Graph(h, keep=[off32, src, w])
+    try:
+        out = torch.empty(V, dtype=torch.int32, device="cuda")
+        st = wedge.wedge_run_bfs(G.handle, 0, out, opts("bfs"))
+        dst = torch.repeat_interleave(v, deg)
+        s64 = src.to(torch.int64)
+        _bellman(dst, s64, torch.ones(1, dtype=torch.int64, device="cuda").expand(E), V, 0, _u32(out))
+        assert st.iters > 2
+        wedge.wedge_run_sssp(G.handle, 0, out, opts("sssp"))
+        _bellman(dst, s64, w.to(torch.int64), V, 0, _u32(out))
+    finally:
+        G.close()
