@@ -515,15 +515,16 @@ def bench_learned(args, wedge, torch, dev, world):
 
 
 def bench_batch(args, wedge, torch, dev, world):
-    """Batched BFS: 64 and 1024 roots (seeded, uniform over vertices with
-    out-edges) on R-MAT s26 ef16 in waves of 64 queries, and an uneven batch
-    of 256 R-MAT graphs of scales 12..20 (block-diagonal, one root each)."""
+    """Batched BFS and SSSP: 64 and 1024 roots (seeded, uniform over vertices
+    with out-edges) on R-MAT s26 ef16 in waves of 64 queries, and an uneven
+    batch of 256 R-MAT graphs of scales 12..20 (block-diagonal, one root
+    each)."""
     import graphgen as gg
     from paper_1903_07754_gb300 import autotune
     scale = 26 if args.scale == SCALE else args.scale
-    g = gg.rmat(scale, EF)
+    g = gg.rmat(scale, EF).with_weights(WMAX)
     od = g.outdeg()
-    G = wedge.Graph.from_csc(g, with_weights=False)
+    G = wedge.Graph.from_csc(g)
     roots = gg.roots(g, 1024, seed=3)
     lv = torch.empty(g.V * 64, dtype=torch.int32, device=dev)
     best, table = autotune.tune(G.handle, "bfs_batch", g.V, roots=roots[:64], nqueries=64,
@@ -543,19 +544,34 @@ def bench_batch(args, wedge, torch, dev, world):
     res["roots64"] = {"ms": t64, "gteps": edges64 / (t64 / 1e3) / 1e9}
     res["roots1024"] = {"ms": t1024, "gteps_est": 16 * edges64 / (t1024 / 1e3) / 1e9,
                         "note": "traversed edges estimated from the first wave"}
+    # batched SSSP (weights in [1, 255]) from the same roots
+    wedge.wedge_run_sssp_batch(G.handle, roots[:64], None, 64, lv, None, False)
+    sedges64 = _batch_edges(torch, lv, od_t, g.V)
+    ts64 = _events(torch, lambda: wedge.wedge_run_sssp_batch(G.handle, roots[:64], None, 64, lv, None, False), 3)
+
+    def swaves():
+        for w in range(16):
+            wedge.wedge_run_sssp_batch(G.handle, roots[64 * w:64 * (w + 1)], None, 64, lv, None, False)
+    ts1024 = _events(torch, swaves, 1)
+    res["sssp_roots64"] = {"ms": ts64, "gteps": sedges64 / (ts64 / 1e3) / 1e9}
+    res["sssp_roots1024"] = {"ms": ts1024, "gteps_est": 16 * sedges64 / (ts1024 / 1e3) / 1e9}
     G.close()
     del lv
-    graphs = [gg.rmat(12 + (i % 9), EF, seed=1000 + i) for i in range(256)]
+    graphs = [gg.rmat(12 + (i % 9), EF, seed=1000 + i).with_weights(WMAX) for i in range(256)]
     big, base = gg.block_diagonal(graphs)
-    B = wedge.Graph.from_csc(big, with_weights=False)
+    B = wedge.Graph.from_csc(big)
     lvb = torch.empty(big.V * 64, dtype=torch.int32, device=dev)
     rq = (np.arange(256) % 64).astype(np.uint32)
     tb = _events(torch, lambda: wedge.wedge_run_bfs_batch(B.handle, base.astype(np.uint32), rq, 64, lvb, None, False), 3)
     eb = _batch_edges(torch, lvb, torch.from_numpy(big.outdeg().astype(np.int64)).to(dev), big.V)
     res["uneven256"] = {"ms": tb, "gteps": eb / (tb / 1e3) / 1e9, "V": big.V, "E": big.E}
+    tsb = _events(torch, lambda: wedge.wedge_run_sssp_batch(B.handle, base.astype(np.uint32), rq, 64, lvb, None,
+                                                            False), 3)
+    esb = _batch_edges(torch, lvb, torch.from_numpy(big.outdeg().astype(np.int64)).to(dev), big.V)
+    res["sssp_uneven256"] = {"ms": tsb, "gteps": esb / (tsb / 1e3) / 1e9}
     B.close()
     line = _base_line(f"GTEPS (batched BFS, 64 roots) on R-MAT s{scale} ef16", res["roots64"]["gteps"], "GTEPS", t64,
-                      3, world, {"workload": f"rmat-s{scale}-ef16: 64/1024-root batched BFS + 256-graph uneven batch",
+                      3, world, {"workload": f"rmat-s{scale}-ef16: 64/1024-root batched BFS and SSSP + 256-graph uneven batch",
                                  "V": g.V, "E": g.E})
     line["batch"] = res
     return line

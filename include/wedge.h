@@ -322,6 +322,20 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
                                  uint32_t nroots, uint32_t nqueries, uint32_t* d_levels,
                                  const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
 
+/* Batched SSSP (not in the paper): up to 64 single-source shortest-path
+ * queries in one run (multi-source Bellman-Ford), with the arguments,
+ * layout and errors of wedge_run_bfs_batch:
+ *  d_dist[v * nqueries + q] = distance of v from query q's nearest root
+ *  (weights, saturation at 0xFFFFFFFE and 0xFFFFFFFF for unreached as in
+ *  wedge_run_sssp).  Each vertex carries a 64-bit mask of the queries whose
+ *  distance it improved in the last iteration; the union of those masks is
+ *  the frontier that drives the fullness decision and the Wedge Frontier
+ *  (Sections 3.3, 3.4).  Distances improve in place (atomic minima).
+ *  INVALID_ARG also when g has no weights. */
+wedge_status wedge_run_sssp_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
+                                  uint32_t nroots, uint32_t nqueries, uint32_t* d_dist,
+                                  const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+
 /* Per-iteration records of the last run of g (needs opts.trace).  Copies up
  * to cap records into host memory, sets *n to the number available.
  * Synchronises the stream of that run. */

@@ -159,11 +159,12 @@ struct wedge_graph {
     uint32_t ms_cap = 0;
     unsigned* ms_bar = nullptr;
     int ms_blocks = 0;
-    int ms_occ = 0;
+    int ms_occ = 0;                  // resident blocks per SM of the batched BFS kernel
+    int ms_occ_sssp = 0;             // ... and of the batched SSSP kernel
     cudaGraphExec_t ms_exec = nullptr;
     uint32_t ms_exec_q = 0, ms_exec_n = 0;
     uint32_t* ms_exec_levels = nullptr;
-    uint32_t ms_exec_key[4] = {0, 0, 0, 0};
+    uint32_t ms_exec_key[5] = {0, 0, 0, 0, 0};  // tau, k, switch, max_iters, SSSP
     bool ms_graph_failed = false;
     uint64_t device_bytes = 0;
     int num_sms = 0;

@@ -1350,6 +1350,116 @@ __global__ void k_msbfs_roots(const uint32_t* __restrict__ roots, const uint32_t
     }
 }
 
+// ---- Batched SSSP pull (multi-source Bellman-Ford; not in the paper) ----
+// A warp takes one 32-edge chunk at a time and lane L holds query L (and
+// L + 32 when there are more than 32 queries): distances are vertex-major,
+// dist[v * Q + q], so a source's distances for all queries are one or two
+// coalesced lines.  The chunk's edges are visited in order, eight at a time
+// with their distance loads issued together; each destination's running
+// minima are applied (atomicMin, only where they improve) when the chunk
+// passes its last edge, and the queries that improved join the
+// destination's next-frontier mask.
+__device__ __forceinline__ void mssp_flush(const PullParams& P, uint32_t kid, uint32_t acc0, uint32_t acc1,
+                                           unsigned long long* fnext, uint32_t* next, Stats& st, unsigned* s_lcnt,
+                                           uint32_t* s_list) {
+    const unsigned lane = threadIdx.x & 31;
+    const bool a = acc0 != kInf, b = acc1 != kInf;
+    if (!__any_sync(kFull, a || b)) return;
+    const uint32_t dv = __ldg(P.vid + kid);
+    uint32_t* row = P.levels + (size_t)dv * P.Q;
+    bool i0 = false, i1 = false;
+    if (a && acc0 < __ldcg(row + lane)) i0 = acc0 < atomicMin(row + lane, acc0);
+    if (b && acc1 < __ldcg(row + lane + 32)) i1 = acc1 < atomicMin(row + lane + 32, acc1);
+    const unsigned long long ch =
+        (unsigned long long)__ballot_sync(kFull, i0) | ((unsigned long long)__ballot_sync(kFull, i1) << 32);
+    if (ch && lane == 0) {
+        const unsigned long long prev = atomicOr(fnext + dv, ch);
+        if (prev == 0ull && set_bit(next, dv)) {
+            st.F += __ldg(P.outdeg + dv);
+            st.n += 1;
+            st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
+            if (*reinterpret_cast<volatile unsigned*>(s_lcnt) <= (unsigned)kListCap) {
+                const unsigned slot = atomicAdd(s_lcnt, 1u);
+                if (slot < (unsigned)kListCap) s_list[slot] = dv;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mssp_chunk(const PullParams& P, unsigned long long c, const unsigned long long* fcur,
+                           unsigned long long* fnext, uint32_t* next, Stats& st, unsigned* s_lcnt, uint32_t* s_list) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long e0 = c * 32;
+    const unsigned nv = (unsigned)(P.E - e0 < 32ull ? P.E - e0 : 32ull);
+    uint32_t su = 0, sw = 0;
+    unsigned long long sm = 0;
+    if (lane < nv) {
+        su = P.src[e0 + lane];
+        sw = P.w[e0 + lane];
+        sm = __ldcg(fcur + su);
+    }
+    if (!__any_sync(kFull, sm != 0ull)) return;
+    const uint2 meta = __ldg(P.cmeta + c);
+    uint32_t kid = meta.y;
+    const unsigned Q = P.Q;
+    const bool q0 = lane < Q, q1 = lane + 32 < Q;
+    uint32_t acc0 = kInf, acc1 = kInf;
+    for (unsigned g8 = 0; g8 < nv; g8 += 8) {
+        uint32_t d0[8], d1[8], wv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned i = g8 + j;  // < 32
+            const unsigned long long m = i < nv ? __shfl_sync(kFull, sm, i) : 0ull;
+            const uint32_t u = __shfl_sync(kFull, su, i);
+            wv[j] = __shfl_sync(kFull, sw, i);
+            const uint32_t* row = P.levels + (size_t)u * Q;
+            d0[j] = (q0 && ((m >> lane) & 1ull)) ? __ldcg(row + lane) : kInf;
+            d1[j] = (q1 && ((m >> (lane + 32)) & 1ull)) ? __ldcg(row + lane + 32) : kInf;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned i = g8 + j;
+            if (i > 0 && i < nv && ((meta.x >> i) & 1u)) {  // a new destination starts at position i
+                mssp_flush(P, kid, acc0, acc1, fnext, next, st, s_lcnt, s_list);
+                acc0 = kInf;
+                acc1 = kInf;
+                ++kid;
+            }
+            if (d0[j] != kInf) {
+                const unsigned long long x = (unsigned long long)d0[j] + wv[j];
+                acc0 = min(acc0, x > kSat ? kSat : (uint32_t)x);
+            }
+            if (d1[j] != kInf) {
+                const unsigned long long x = (unsigned long long)d1[j] + wv[j];
+                acc1 = min(acc1, x > kSat ? kSat : (uint32_t)x);
+            }
+        }
+    }
+    mssp_flush(P, kid, acc0, acc1, fnext, next, st, s_lcnt, s_list);
+}
+
+// Dense (every chunk) or sparse (the listed Wedge Frontier entries, whose
+// bitmap words are zeroed as consumed) batched SSSP pull of iteration it.
+__device__ __forceinline__ void mssp_pull(const PullParams& P, unsigned it, unsigned mode, unsigned k, unsigned nchunks,
+                          uint32_t* next, Stats& st, unsigned long long gw, unsigned long long nw, unsigned* s_lcnt,
+                          uint32_t* s_list) {
+    const unsigned long long* fcur = (it & 1) ? P.fb[1] : P.fb[0];
+    unsigned long long* fnext = (it & 1) ? P.fb[0] : P.fb[1];
+    if (mode == 0) {
+        for (unsigned long long c = gw; c < P.NC; c += nw) mssp_chunk(P, c, fcur, fnext, next, st, s_lcnt, s_list);
+        return;
+    }
+    const unsigned long long nunits = (unsigned long long)nchunks << k;
+    const unsigned long long kmask = (1ull << k) - 1;
+    for (unsigned long long j = gw; j < nunits; j += nw) {
+        const uint32_t b = __ldcg(P.clist + (j >> k));
+        const unsigned long long c = ((unsigned long long)b << k) | (j & kmask);
+        if ((j & kmask) == 0 && (threadIdx.x & 31) == 0) P.wb[b >> 5] = 0u;
+        if (c < P.NC) mssp_chunk(P, c, fcur, fnext, next, st, s_lcnt, s_list);
+    }
+}
+
+template <bool SSSP>
 __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const XformParams X, unsigned* bar) {
     using T = unsigned long long;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1382,7 +1492,9 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
         Stats st{0ull, 0u, 0u};
         const uint32_t* cur = (it & 1) ? P.bm[1] : P.bm[0];
         uint32_t* next = (it & 1) ? P.bm[0] : P.bm[1];
-        if (mode == 0)
+        if constexpr (SSSP)
+            mssp_pull(P, it, mode, k, __ldcg(&P.rec[it].nchunks), next, st, gw, nw, &s_lcnt, s_list);
+        else if (mode == 0)
             pull_dense_direct<kMSBFS>(P, it, cur, next, my_kid, my_val, st, gw, nw, &s_lcnt, s_list);
         else
             pull_sparse<kMSBFS>(P, it, k, __ldcg(&P.rec[it].nchunks), cur, next, my_kid, my_val, st, gw, nw,
@@ -1928,7 +2040,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
 // Batched BFS: everything after the roots' upload, enqueued on s (also the
 // body of the captured graph).
 static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, uint32_t* levels, const RunCtl& init,
-                                  cudaStream_t s) {
+                                  bool sssp, cudaStream_t s) {
     WEDGE_TRY_CUDA(cudaMemsetAsync(levels, 0xFF, (size_t)g->V * Q * 4, s));
     k_msbfs_clear<<<g->num_sms * 4, 256, 0, s>>>(g->V, g->ms_fb[0], g->ms_fb[1], g->ms_seen, g->bm[0], g->bm[1], g->wb,
                                                  (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->ms_bar);
@@ -1959,13 +2071,13 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    WEDGE_TRY_CUDA(cudaLaunchKernelExC(&cfg, (const void*)k_msbfs, args));
+    WEDGE_TRY_CUDA(cudaLaunchKernelExC(&cfg, sssp ? (const void*)k_msbfs<true> : (const void*)k_msbfs<false>, args));
     count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
 }
 
-static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
+static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots, bool sssp) {
     const uint64_t V = g->V;
     if (!g->ms_seen) {
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_seen, V * 8));
@@ -1973,13 +2085,16 @@ static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots) {
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_fb[1], V * 8));
         WEDGE_TRY(dev_alloc(g, (void**)&g->ms_bar, kBarWords * 4));
         const int smem = pull_records_bytes<kMSBFS>() + kListCap * 4;
-        WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_msbfs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int n = 0;
-        WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_msbfs, kCW * 32, smem));
-        if (n < 1) return set_error(WEDGE_ERR_NOT_SUPPORTED, "batched BFS kernel does not fit on an SM");
+        WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_msbfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_msbfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int n = 0, m = 0;
+        WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_msbfs<false>, kCW * 32, smem));
+        WEDGE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_msbfs<true>, kCW * 32, smem));
+        if (n < 1 || m < 1) return set_error(WEDGE_ERR_NOT_SUPPORTED, "batched kernel does not fit on an SM");
         g->ms_occ = n;
+        g->ms_occ_sssp = m;
     }
-    int n = g->ms_occ;
+    int n = sssp ? g->ms_occ_sssp : g->ms_occ;
     if (g->tuning.blocks_per_sm > 0 && (int)g->tuning.blocks_per_sm < n) n = (int)g->tuning.blocks_per_sm;
     if (g->num_sms * n != g->ms_blocks && g->ms_exec) {
         cudaGraphExecDestroy(g->ms_exec);
@@ -2141,19 +2256,23 @@ wedge_status wedge_selftest_timeout(int kind) {
     return WEDGE_OK;
 }
 
-wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query, uint32_t nroots,
-                                 uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts_in, wedge_stats* stats,
-                                 wedge_stream_t stream) {
+}  // extern "C"
+
+namespace wedge {
+// Batched BFS (sssp = false) or SSSP (sssp = true) of up to 64 queries.
+static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, const uint32_t* root_query,
+                              uint32_t nroots, uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts_in,
+                              wedge_stats* stats, cudaStream_t s) {
     if (!g || !roots || !d_levels) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (sssp && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
     if (nqueries < 1 || nqueries > 64) return set_error(WEDGE_ERR_INVALID_ARG, "nqueries must be 1..64");
     if (nroots < 1 || nroots > (1u << 24)) return set_error(WEDGE_ERR_INVALID_ARG, "nroots must be 1..2^24");
     wedge_opts o;
     if (opts_in) o = *opts_in;
-    else wedge_default_opts(WEDGE_BFS, &o);
+    else wedge_default_opts(sssp ? WEDGE_SSSP : WEDGE_BFS, &o);
     WEDGE_TRY(check_opts(&o));
     if (classify(d_levels) != PtrKind::Device) return set_error(WEDGE_ERR_INVALID_ARG, "levels must be device memory");
     DeviceGuard dg(g->device);
-    cudaStream_t s = (cudaStream_t)stream;
     // roots and their queries, checked on the host
     std::vector<uint32_t> hr((size_t)nroots * 2);
     WEDGE_TRY_CUDA(cudaMemcpy(hr.data(), roots, (size_t)nroots * 4, cudaMemcpyDefault));
@@ -2163,7 +2282,7 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
         if (hr[i] >= g->V) return set_error(WEDGE_ERR_INVALID_ARG, "root out of range");
         if (hr[nroots + i] >= nqueries) return set_error(WEDGE_ERR_INVALID_ARG, "query id out of range");
     }
-    WEDGE_TRY(msbfs_prepare(g, nroots));
+    WEDGE_TRY(msbfs_prepare(g, nroots, sssp));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->ms_roots, hr.data(), (size_t)nroots * 4, cudaMemcpyHostToDevice, s));
     WEDGE_TRY_CUDA(
         cudaMemcpyAsync(g->ms_roots + g->ms_cap, hr.data() + nroots, (size_t)nroots * 4, cudaMemcpyHostToDevice, s));
@@ -2173,7 +2292,7 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
     init.tau_bp = o.tau_bp;
     init.k = o.log2_coarsen;
     init.E = g->E;
-    const uint32_t key[4] = {init.tau_bp, init.k, init.switch_mode, init.max_iters};
+    const uint32_t key[5] = {init.tau_bp, init.k, init.switch_mode, init.max_iters, sssp ? 1u : 0u};
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     const bool reuse = g->ms_exec && g->ms_exec_q == nqueries && g->ms_exec_n == nroots &&
                        g->ms_exec_levels == d_levels && !memcmp(key, g->ms_exec_key, sizeof(key));
@@ -2185,7 +2304,7 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
         wedge_status es = WEDGE_OK;
-        if (e == cudaSuccess) es = msbfs_enqueue(g, nroots, nqueries, d_levels, init, g->cap_stream);
+        if (e == cudaSuccess) es = msbfs_enqueue(g, nroots, nqueries, d_levels, init, sssp, g->cap_stream);
         cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(g->cap_stream, &graph) : e;
         if (e == cudaSuccess && es == WEDGE_OK && ee == cudaSuccess &&
             cudaGraphInstantiate(&g->ms_exec, graph, 0) == cudaSuccess) {
@@ -2196,7 +2315,7 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
         } else {
             g->ms_exec = nullptr;
             g->ms_graph_failed = true;  // direct launches from now on
-            std::fprintf(stderr, "wedge: batched BFS graph capture unavailable; launching directly\n");
+            std::fprintf(stderr, "wedge: batched run graph capture unavailable; launching directly\n");
         }
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
@@ -2205,7 +2324,7 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
         WEDGE_TRY_CUDA(cudaGraphLaunch(g->ms_exec, s));
         count_launch(4);
     } else {
-        WEDGE_TRY(msbfs_enqueue(g, nroots, nqueries, d_levels, init, s));
+        WEDGE_TRY(msbfs_enqueue(g, nroots, nqueries, d_levels, init, sssp, s));
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
@@ -2213,6 +2332,21 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
     g->last_trace = false;
     if (!stats) return WEDGE_OK;
     return fill_stats(g, s, stats);
+}
+}  // namespace wedge
+
+extern "C" {
+
+wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query, uint32_t nroots,
+                                 uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts, wedge_stats* stats,
+                                 wedge_stream_t stream) {
+    return run_batch(g, false, roots, root_query, nroots, nqueries, d_levels, opts, stats, (cudaStream_t)stream);
+}
+
+wedge_status wedge_run_sssp_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
+                                  uint32_t nroots, uint32_t nqueries, uint32_t* d_dist, const wedge_opts* opts,
+                                  wedge_stats* stats, wedge_stream_t stream) {
+    return run_batch(g, true, roots, root_query, nroots, nqueries, d_dist, opts, stats, (cudaStream_t)stream);
 }
 
 wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_bitmap, uint32_t log2_coarsen,

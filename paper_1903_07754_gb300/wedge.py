@@ -68,7 +68,7 @@ EXPORTS = [
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
-    "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout",
+    "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
         "wedge_get_trace": (st, [P, ctypes.POINTER(wedge_iter_record), u32, ctypes.POINTER(u32)]),
         "wedge_graph_set_tuning": (st, [P, ctypes.POINTER(wedge_tuning)]),
         "wedge_run_bfs_batch": (st, [P, P, P, u32, u32, P, ctypes.POINTER(wedge_opts),
+                                     ctypes.POINTER(wedge_stats), P]),
+        "wedge_run_sssp_batch": (st, [P, P, P, u32, u32, P, ctypes.POINTER(wedge_opts),
                                      ctypes.POINTER(wedge_stats), P]),
         "wedge_mlp_forward": (st, [P, P, u32, P, P]),
         "wedge_mlp_forward_bf16": (st, [P, P, u32, P, P]),
@@ -283,6 +285,16 @@ def wedge_run_bfs_batch(handle, roots, root_query, nqueries, levels, opts=None, 
     st = wedge_stats()
     _check(load().wedge_run_bfs_batch(handle, _ptr(r), _ptr(q), int(r.size), int(nqueries), _ptr(levels), _opts(opts),
                                       ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_run_sssp_batch(handle, roots, root_query, nqueries, dist, opts=None, want_stats=True, stream=None):
+    """dist: device tensor of V * nqueries uint32 (vertex-major)."""
+    r = np.ascontiguousarray(roots, dtype=np.uint32)
+    q = None if root_query is None else np.ascontiguousarray(root_query, dtype=np.uint32)
+    st = wedge_stats()
+    _check(load().wedge_run_sssp_batch(handle, _ptr(r), _ptr(q), int(r.size), int(nqueries), _ptr(dist), _opts(opts),
+                                       ctypes.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
 
 

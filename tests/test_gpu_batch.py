@@ -79,3 +79,68 @@ def test_invalid_batches_are_rejected(g15_dev):
         wedge.wedge_run_bfs_batch(g15_dev.handle, [0, 1], [0, 5], 2, lv)
     with pytest.raises(wedge.WedgeError):
         wedge.wedge_run_bfs_batch(g15_dev.handle, [0], None, 65, lv)
+
+
+# ---- batched SSSP: every query's distances equal Dijkstra's -------------
+def _dists(G, V, roots, rq, Q, o=None):
+    d = torch.empty(V * Q, dtype=torch.int32, device="cuda")
+    st = wedge.wedge_run_sssp_batch(G.handle, roots, rq, Q, d, o)
+    return d.cpu().numpy().view(np.uint32).reshape(V, Q), st
+
+
+@pytest.fixture(scope="module")
+def g15w():
+    return gg.rmat(15, 16, seed=21).with_weights(255)
+
+
+@pytest.fixture(scope="module")
+def g15w_dev(g15w):
+    G = graph(g15w)
+    yield G
+    G.close()
+
+
+@pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse3"])
+def test_sssp_batch_matches_dijkstra(g15w, g15w_dev, mode):
+    roots = gg.roots(g15w, 64, seed=6)
+    o = {"default": opts("sssp"), "dense": opts("sssp", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("sssp", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0),
+         "sparse3": opts("sssp", switch=wedge.SWITCH_ALWAYS_SPARSE, k=3)}[mode]
+    d, st = _dists(g15w_dev, g15w.V, roots, None, 64, o)
+    for q in range(0, 64, 7 if mode != "default" else 1):
+        np.testing.assert_array_equal(d[:, q], oracle.sssp_dijkstra(g15w, int(roots[q])), err_msg=f"query {q}")
+    assert st.iters >= 1
+
+
+@pytest.mark.parametrize("Q", [1, 5, 33])
+def test_sssp_batch_query_counts_and_shared_roots(g15w, g15w_dev, Q):
+    # Q = 33 uses the second lane half (queries 32..63); several roots per query
+    rng = np.random.default_rng(Q)
+    roots = gg.roots(g15w, 2 * Q, seed=40 + Q)
+    rq = np.concatenate([np.arange(Q), rng.integers(0, Q, Q)]).astype(np.uint32)
+    for _ in range(2):  # the captured graph is replayed
+        d, _ = _dists(g15w_dev, g15w.V, roots, rq, Q)
+        for q in sorted({0, Q - 1, Q // 2}):
+            want = np.full(g15w.V, 0xFFFFFFFF, dtype=np.uint32)
+            for r in roots[rq == q]:
+                want = np.minimum(want, oracle.sssp_dijkstra(g15w, int(r)))
+            np.testing.assert_array_equal(d[:, q], want, err_msg=f"Q={Q} query {q}")
+
+
+def test_sssp_uneven_batch_of_graphs():
+    graphs = [gg.rmat(8 + (i % 5), 8, seed=500 + i).with_weights(255) for i in range(40)]
+    big, base = gg.block_diagonal(graphs)
+    G = graph(big)
+    try:
+        d, _ = _dists(G, big.V, base.astype(np.uint32), (np.arange(len(graphs)) % 64).astype(np.uint32), 64)
+        for i, g in enumerate(graphs):
+            np.testing.assert_array_equal(d[base[i]:base[i] + g.V, i % 64], oracle.sssp_dijkstra(g, 0),
+                                          err_msg=f"graph {i}")
+    finally:
+        G.close()
+
+
+def test_sssp_batch_needs_weights(g15_dev):
+    d = torch.empty(g15_dev.V * 2, dtype=torch.int32, device="cuda")
+    with pytest.raises(wedge.WedgeError):
+        wedge.wedge_run_sssp_batch(g15_dev.handle, [0, 1], None, 2, d)

@@ -9,8 +9,8 @@ unreached vertices (and additions past the saturation value) at
 0xFFFFFFFF / 0xFFFFFFFE as the engine defines them.  Checking every vertex's
 equation therefore checks the whole output exactly.
 Workloads: R-MAT scale 24 with the learned switch (BFS, SSSP), the rewired
-4096^2 grid (BFS, SSSP) and R-MAT scale 26 batched BFS (64 roots; two
-queries checked)."""
+4096^2 grid (BFS, SSSP) and R-MAT scale 26 batched BFS and SSSP (64 roots;
+two queries of each checked)."""
 import numpy as np
 import pytest
 import torch
@@ -85,18 +85,22 @@ def test_rewired_grid_4096():
         G.close()
 
 
-def test_batched_bfs_scale26():
-    g = gg.rmat(26, 16)
+def test_batched_bfs_and_sssp_scale26():
+    g = gg.rmat(26, 16).with_weights(255)
     roots = gg.roots(g, 64, seed=3)
-    G = graph(g, with_weights=False)
+    G = graph(g)
     try:
         lv = torch.empty(g.V * 64, dtype=torch.int32, device="cuda")
-        wedge.wedge_run_bfs_batch(G.handle, roots, None, 64, lv)
-        lv = lv.view(g.V, 64)
         dst, src = _edges(g)
+        wedge.wedge_run_bfs_batch(G.handle, roots, None, 64, lv)
         one = torch.ones(1, dtype=torch.int64, device="cuda").expand(src.numel())
         for q in (0, 37):
-            _bellman(dst, src, one, g.V, int(roots[q]), _u32(lv[:, q].contiguous()))
+            _bellman(dst, src, one, g.V, int(roots[q]), _u32(lv.view(g.V, 64)[:, q].contiguous()))
+        del one
+        wedge.wedge_run_sssp_batch(G.handle, roots, None, 64, lv)
+        w = torch.from_numpy(g.w.astype(np.int64)).cuda()
+        for q in (5, 63):
+            _bellman(dst, src, w, g.V, int(roots[q]), _u32(lv.view(g.V, 64)[:, q].contiguous()))
     finally:
         G.close()
 
