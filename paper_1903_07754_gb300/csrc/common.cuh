@@ -69,12 +69,12 @@ constexpr int kListCap = 1024;  // frontier-list entries a pull block stages in 
 constexpr int kMaxPullBlocks = 4096;
 
 // What one pull block found: written to its own slot (no shared counter),
-// reduced by the one-block decision kernel.
+// summed by the pull's last block when it takes the decision.
 struct BlockStat {
     unsigned long long F;  // sum of out-degrees of the vertices it activated
     unsigned int n;        // vertices it activated
     unsigned int row;      // their edge-index row lengths
-    unsigned int lcnt;     // its list segment length (> kListCap: overflow)
+    unsigned int lcnt;     // vertices it staged for the next frontier list (> kListCap: overflow)
     unsigned int pad_;
 };
 
