@@ -630,10 +630,11 @@ def bench_grid(args, wedge, torch, dev, world):
     return line
 
 
-# DRAM traffic of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-# and a digest of the kernel sources it was measured on: reported only while
-# those sources are unchanged.
-TRAFFIC = {"pr": (321343744, "f2a89bbf5ce18837"), "cc": (607487232, "f2a89bbf5ce18837")}
+# DRAM traffic of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum),
+# that launch's ncu gpu__time_duration in us, and a digest of the kernel
+# sources they were measured on: reported only while those sources are
+# unchanged.
+TRAFFIC = {"pr": (321343744, 294.912, "f2a89bbf5ce18837"), "cc": (607487232, 514.944, "f2a89bbf5ce18837")}
 
 
 def _kernel_digest():
@@ -646,8 +647,14 @@ def _kernel_digest():
 
 
 def _traffic(key):
-    val, digest = TRAFFIC[key]
+    val, _, digest = TRAFFIC[key]
     return val if val is not None and digest == _kernel_digest() else None
+
+
+def _ncu_gbs(key):
+    """DRAM bytes over the launch's duration, both from the ncu capture."""
+    val, us, digest = TRAFFIC[key]
+    return val / (us * 1e-6) / 1e9 if val is not None and digest == _kernel_digest() else None
 
 
 def _gather_bound(torch, dev, edges, t, clocks):
@@ -686,21 +693,21 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
     # other count takes every gather as one 32-byte sector
     alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 8 * V
-    return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", alg, alg_sectors, t, dev,
-                     _traffic("pr"), _gather_bound(torch, dev, E, t, clocks))
+    return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "pr", alg, alg_sectors, t, dev,
+                     _gather_bound(torch, dev, E, t, clocks))
 
 
-def _roofline(kernel, alg, alg_sectors, t, dev, traffic, gather):
+def _roofline(kernel, key, alg, alg_sectors, t, dev, gather):
     import torch
     peak, kind = peaks()
     achieved = alg / t / 1e9
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "alg_bytes": alg, "ms": t * 1e3,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(key), "alg_bytes": alg, "ms": t * 1e3,
             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "gathers_counted": f"once per vertex (V*4 <= L2 = {l2 >> 20} MB)",
             "alg_bytes_gather_sectors": alg_sectors, "achieved_gather_sectors": alg_sectors / t / 1e9,
-            "gather_bound": gather}
+            "ncu_dram_gbs": _ncu_gbs(key), "gather_bound": gather}
 
 
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
@@ -732,8 +739,8 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     # changed labels written 4*changed, next-frontier bitmap V/8
     alg = 4 * (V + 1) + 4 * E + 4 * V + 4 * V + 4 * nchanged + V / 8
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 4 * V + 4 * nchanged + V / 8
-    return _roofline("k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", alg, alg_sectors, t, dev,
-                     _traffic("cc"), _gather_bound(torch, dev, E, t, None))
+    return _roofline("k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "cc", alg, alg_sectors, t, dev,
+                     _gather_bound(torch, dev, E, t, None))
 
 
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev):
