@@ -634,15 +634,21 @@ def bench_grid(args, wedge, torch, dev, world):
 # that launch's ncu gpu__time_duration in us, and a digest of the kernel
 # sources they were measured on: reported only while those sources are
 # unchanged.
-TRAFFIC = {"pr": (321343744, 294.912, "f2a89bbf5ce18837"), "cc": (607487232, 514.944, "f2a89bbf5ce18837")}
+TRAFFIC = {"pr": (321343744, 294.912, "a2872923204098ab"), "cc": (607487232, 514.944, "a2872923204098ab")}
 
 
 def _kernel_digest():
+    """Digest of the kernel sources' code: comments and whitespace are
+    dropped, so that only a change of code invalidates the counters."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("engine.cu", "common.cuh", "tma.cuh", "mlp.cuh"):
-        with open(os.path.join(ROOT, "paper_1903_07754_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1903_07754_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).strip().encode())
     return h.hexdigest()[:16]
 
 

@@ -1,10 +1,12 @@
 // The Wedge hot path on the device:
 //   pull (dense over all chunks, or over the listed Wedge Frontier chunks)
-//   with the frontier-fullness epilogue and the fullness decision
-//   (Sections 3.2, 3.4, Fig. 5), the frontier transformation (Sections 3.3,
-//   4), PageRank, and the run drivers for BFS, CC, SSSP and PageRank
-//   (Section 5).  The iteration loop runs on the device inside a CUDA graph
-//   with a conditional while node.
+//   with the frontier-fullness epilogue and the fullness decision taken by
+//   its last block (Sections 3.2, 3.4, Fig. 5), the frontier transformation
+//   (Sections 3.3, 4), PageRank, the run drivers for BFS, CC, SSSP and
+//   PageRank (Section 5), and -- beyond the paper -- the learned switch's
+//   in-loop inference, batched BFS/SSSP in one persistent launch and a
+//   self-test of the bounded waits.  The iteration loop runs on the device
+//   inside a CUDA graph with a conditional while node.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
