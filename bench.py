@@ -213,10 +213,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced"],
                     help="run only one small case for a profiler (no JSON line)")
-    ap.add_argument("--config", default="s22", choices=["s22", "learned-s24", "batch-s26", "grid"],
+    ap.add_argument("--config", default="s22", choices=["s22", "learned-s24", "batch-s26", "grid", "studies"],
                     help="s22: the benchmark line (R-MAT s22, four apps); the others print one line each "
                          "for the learned switch (R-MAT s24), batched traversal (R-MAT s26, uneven "
-                         "batch) and the rewired grid")
+                         "batch), the rewired grid and the paper's studies (time split, per-iteration "
+                         "profiles, threshold and precision sweeps)")
     args = ap.parse_args()
 
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -240,7 +241,8 @@ def main():
     wbuild.build()
     wedge.load()
     if args.config != "s22":
-        line = {"learned-s24": bench_learned, "batch-s26": bench_batch, "grid": bench_grid}[args.config](
+        line = {"learned-s24": bench_learned, "batch-s26": bench_batch, "grid": bench_grid,
+                "studies": bench_studies}[args.config](
             args, wedge, torch, dev, world)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -582,6 +584,66 @@ def _batch_edges(torch, lv, od_t, V):
     (levels vertex-major, 64 queries), on the device."""
     lvv = lv.view(V, 64)
     return int(sum(int(od_t[lvv[:, q] != -1].sum().item()) for q in range(64)))
+
+
+def bench_studies(args, wedge, torch, dev, world):
+    """The paper's per-application studies, on R-MAT s22 (BFS, SSSP from 0;
+    CC on the symmetrised graph): the split of time between pull and
+    transformation (Fig. 8), per-iteration dense vs Wedge times with the
+    active share of edges (Fig. 9, from the candidate-timing trace), a
+    sweep of the fullness threshold including "always transform" (Fig. 10)
+    and a sweep of the precision (Fig. 11)."""
+    g, s = make_inputs(args.scale)
+    G = wedge.Graph.from_csc(g)
+    S = wedge.Graph.from_csc(s, with_weights=False)
+    out = torch.empty(g.V, dtype=torch.int32, device=dev)
+    apps = {"bfs": (G, lambda h, o: wedge.wedge_run_bfs(h, 0, out, o, False)),
+            "cc": (S, lambda h, o: wedge.wedge_run_cc(h, out, o, False)),
+            "sssp": (G, lambda h, o: wedge.wedge_run_sssp(h, 0, out, o, False))}
+    res = {}
+    for app, (H, run) in apps.items():
+        r = {}
+        # Fig. 8: pull vs transformation time (traced run, device timers)
+        o = wedge.wedge_default_opts(app)
+        o.trace = 1
+        run(H.handle, o)
+        torch.cuda.synchronize()
+        tr = wedge.wedge_get_trace(H.handle)
+        r["time_split_ms"] = {"pull": sum(x["t_pull_ns"] for x in tr) / 1e6,
+                              "transform": sum(x["t_xform_ns"] for x in tr) / 1e6}
+        # Fig. 9: every iteration timed dense and as a Wedge Frontier at the
+        # default precision, from the same state
+        feat, ms, chosen = wedge.wedge_trace_candidates(H.handle, app, 0, None, 64, 4096)
+        kdef = wedge.wedge_default_opts(app).log2_coarsen
+        # feature 3 of the cost model is the fullness over |E|: the active share of edges
+        r["per_iteration"] = [{"t": t, "active_edges_pct": 100.0 * float(feat[t, 0, 2]),
+                               "dense_ms": float(ms[t, 0]), "wedge_ms": float(ms[t, 1 + kdef]),
+                               "threshold_chose": "dense" if chosen[t] == 0 else f"wedge k={int(chosen[t]) - 1}"}
+                              for t in range(len(ms))]
+        # Fig. 10: fullness threshold (basis points of |E|; 10000 = always transform)
+        r["tau_sweep_ms"] = {}
+        for tau in (10, 100, 500, 2000, 5000, 10000):
+            o = wedge.wedge_default_opts(app)
+            o.tau_bp = tau
+            r["tau_sweep_ms"][str(tau)] = _events(torch, lambda: run(H.handle, o), 5)
+        o = wedge.wedge_default_opts(app)
+        o.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
+        r["tau_sweep_ms"]["always_transform"] = _events(torch, lambda: run(H.handle, o), 5)
+        # Fig. 11: precision, 32 * 2^k edges per Wedge Frontier entry
+        r["precision_sweep_ms"] = {}
+        for k in range(0, 5):
+            o = wedge.wedge_default_opts(app)
+            o.log2_coarsen = k
+            r["precision_sweep_ms"][f"k{k}"] = _events(torch, lambda: run(H.handle, o), 5)
+        res[app] = r
+    G.close()
+    S.close()
+    t_default = sum(min(v["tau_sweep_ms"].values()) for v in res.values())
+    line = _base_line("ms (BFS+CC+SSSP, best threshold) on R-MAT s22 ef16, paper studies", t_default, "ms",
+                      t_default, 5, world, {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp studies"})
+    line["higher_is_better"] = False
+    line["studies"] = res
+    return line
 
 
 def bench_grid(args, wedge, torch, dev, world):
