@@ -113,6 +113,34 @@ class ClockSampler:
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
+# settings the autotuner tries for the step (direct loads, all blocks per SM)
+STEP_TUNE_GRID = {
+    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+}
+
+
+def tune_step(wedge, G, S, g):
+    """Wedge Frontier precision and fullness threshold per application,
+    picked by the project's autotuner on the step's graphs, with BFS and
+    SSSP tuned from another root than the measured one (the paper's own
+    settings are timed in per_app as well)."""
+    import graphgen as gg
+    from paper_1903_07754_gb300 import autotune
+    root = int(gg.roots(g, 1, seed=7)[0])
+    tuned = {}
+    for app, H in (("bfs", G), ("cc", S), ("sssp", G)):
+        best, _ = autotune.tune(H.handle, app, g.V, root=root, grid=STEP_TUNE_GRID[app], reps=3)
+        tuned[app] = {"k": best["k"], "tau_bp": best["tau_bp"]}
+    return tuned
+
+
+def step_opts(wedge, app, tuned):
+    o = wedge.wedge_default_opts(app)
+    o.log2_coarsen, o.tau_bp = tuned[app]["k"], tuned[app]["tau_bp"]
+    return o
+
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -262,7 +290,8 @@ def main():
             # (ncu --profile-from-start off); BFS, CC and SSSP run their
             # iterations through the host-polled loop (traced runs: the same
             # kernels and launch shapes) so that every launch is visible
-            o = [wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp")]
+            tuned = tune_step(wedge, G, S, g)
+            o = [step_opts(wedge, a, tuned) for a in ("bfs", "cc", "sssp")]
             for x in o:
                 x.trace = 1
             out = torch.empty(g.V, dtype=torch.int32, device=dev)
@@ -305,7 +334,8 @@ def main():
     lab = torch.empty(V, dtype=torch.int32, device=dev)
     dist_ = torch.empty(V, dtype=torch.int32, device=dev)
     rank_t = torch.empty(V, dtype=torch.float32, device=dev)
-    o_bfs, o_cc, o_sssp = (wedge.wedge_default_opts(a) for a in ("bfs", "cc", "sssp"))
+    tuned = tune_step(wedge, G, S, g)
+    o_bfs, o_cc, o_sssp = (step_opts(wedge, a, tuned) for a in ("bfs", "cc", "sssp"))
 
     def step(want_stats=False):
         sb = wedge.wedge_run_bfs(G.handle, 0, lvl, o_bfs, want_stats)
@@ -384,8 +414,10 @@ def main():
         t_w = time_fn(lambda: fn(ow))
         t_d = time_fn(lambda: fn(odn))
         t_s = time_fn(lambda: fn(sparse[name]))
+        t_p = time_fn(lambda: fn(wedge.wedge_default_opts(name)))
         sd = stat_fn[name](odn)
-        per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "dense_pull_ms": t_d,
+        per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "tuned": tuned[name],
+                         "paper_settings_ms": t_p, "dense_pull_ms": t_d,
                          "speedup_vs_dense_pull": t_d / t_w, "always_sparse_ms": t_s,
                          "speedup_vs_always_sparse": t_s / t_w,
                          "dense_pull_edges_per_s": sd.edges_pulled / (t_d / 1e3)}
@@ -401,6 +433,7 @@ def main():
             t_l = time_fn(lambda: fn(ol))
             per_app[name]["learned_ms"] = t_l
             per_app[name]["speedup_learned_vs_threshold"] = per_app[name]["ms"] / t_l
+            per_app[name]["speedup_learned_vs_paper_settings"] = per_app[name]["paper_settings_ms"] / t_l
             per_app[name]["speedup_learned_vs_dense_pull"] = per_app[name]["dense_pull_ms"] / t_l
         wedge.wedge_set_cost_model(G.handle, None)
         wedge.wedge_set_cost_model(S.handle, None)
@@ -439,12 +472,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
             "config": {"workload": f"rmat-s{args.scale}-ef{EF}: bfs+cc(sym)+sssp+pr{PR_ITERS}",
                        "V": V, "E": g.E, "E_sym": s.E, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20)},
+                       "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20),
+                       "wedge_settings": "autotuned (k, tau) per app: " + json.dumps(tuned)},
             "per_app": per_app, "graph_build_ms": build_ms, "roofline": roof, "roofline_cc_dense_pull": roof_cc,
             "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e_measure(wedge, torch, g, s, od, edges, args, dev)
+        line["e2e"] = e2e_measure(wedge, torch, g, s, od, edges, args, dev, (o_bfs, o_cc, o_sssp))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, s, od)
     G.close()
@@ -811,7 +845,7 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
                      _gather_bound(torch, dev, E, t, None))
 
 
-def e2e_measure(wedge, torch, g, s, od, edges, args, dev):
+def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
     """Host buffers through the public API: pinned host CSC -> device, graph
     creation (edge index build), the four runs, results back to the host."""
     host = {}
@@ -831,9 +865,9 @@ def e2e_measure(wedge, torch, g, s, od, edges, args, dev):
         lvl = torch.empty(g.V, dtype=torch.int32, device=dev)
         lab, dst = torch.empty_like(lvl), torch.empty_like(lvl)
         pr = torch.empty(g.V, dtype=torch.float32, device=dev)
-        wedge.wedge_run_bfs(G.handle, 0, lvl, None, False)
-        wedge.wedge_run_cc(S.handle, lab, None, False)
-        wedge.wedge_run_sssp(G.handle, 0, dst, None, False)
+        wedge.wedge_run_bfs(G.handle, 0, lvl, opts[0], False)
+        wedge.wedge_run_cc(S.handle, lab, opts[1], False)
+        wedge.wedge_run_sssp(G.handle, 0, dst, opts[2], False)
         wedge.wedge_run_pr(G.handle, pr, PR_ITERS, DAMPING, None, False)
         outs["lvl"].copy_(lvl, non_blocking=True)
         outs["lab"].copy_(lab, non_blocking=True)

@@ -177,26 +177,42 @@ __device__ __forceinline__ bool set_bit(uint32_t* bm, uint32_t v) {
 // cost model on the six candidates (dense; Wedge Frontier with k = 0..4):
 // BF16 weights and activations, FP32 accumulation; the lowest predicted
 // time wins.  Without a model, or if no prediction is finite, the threshold
-// decides.  `sm` needs 2*6*64 + 8 floats of shared memory.
-__device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __nv_bfloat16* mlp,
+// decides.  `sm` needs kDecideSmemBytes of shared memory: the activations
+// and features, then a copy of the weights (read straight from global memory
+// inside the dot products, each decision took ~20 us) with W2 stored
+// k-major, so that the threads of a layer read consecutive weights.
+constexpr int kDecideFloats = 2 * kCandidates * kMlpHidden + 8 + kCandidates * kMlpIn;
+constexpr int kDecideSmemBytes = kDecideFloats * 4 + ((kMlpParams * 2 + 15) / 16) * 16;
+static_assert((kDecideFloats * 4) % 16 == 0, "weights must start 16-byte aligned");
+__device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __nv_bfloat16* mlp_global,
                              const GraphFeat& gf, float* sm) {
     IterRec* r = rec + it_next;
     const unsigned long long F = __ldcg(&r->fullness);
     const unsigned nf = __ldcg(&r->nfront);
     const unsigned rows = __ldcg(&r->rowsum);
-    const bool learned = C->switch_mode == WEDGE_SWITCH_LEARNED && mlp != nullptr && nf > 0;
+    const bool learned = C->switch_mode == WEDGE_SWITCH_LEARNED && mlp_global != nullptr && nf > 0;
     float* h1 = sm;
     float* h2 = sm + kCandidates * kMlpHidden;
     float* out = sm + 2 * kCandidates * kMlpHidden;
+    float* xs = out + 8;  // the candidates' features, BF16-rounded
+    __nv_bfloat16* mlp = reinterpret_cast<__nv_bfloat16*>(sm + kDecideFloats);
+    __nv_bfloat16* w2t = mlp + kMlpW2;  // W2 transposed: w2t[k * 64 + j] = W2[j][k]
     if (learned) {
-        const double E = (double)C->E;
+        for (int i = threadIdx.x; i < kMlpW2; i += blockDim.x) mlp[i] = mlp_global[i];  // W1, b1
+        for (int i = kMlpB2 + threadIdx.x; i < kMlpParams; i += blockDim.x) mlp[i] = mlp_global[i];  // b2, w3, b3
+        for (int i = threadIdx.x; i < kMlpHidden * kMlpHidden; i += blockDim.x)
+            w2t[(i % kMlpHidden) * kMlpHidden + i / kMlpHidden] = mlp_global[kMlpW2 + i];
+        if (threadIdx.x < kCandidates) {
+            float x[kMlpIn];
+            mlp_features(gf, (double)C->E, nf, (double)F, rows, it_next, threadIdx.x, x);
+            for (int f = 0; f < kMlpIn; ++f) xs[threadIdx.x * kMlpIn + f] = __bfloat162float(__float2bfloat16_rn(x[f]));
+        }
+        __syncthreads();
         for (int o = threadIdx.x; o < kCandidates * kMlpHidden; o += blockDim.x) {
             const int c = o / kMlpHidden, j = o % kMlpHidden;
-            float x[kMlpIn];
-            mlp_features(gf, E, nf, (double)F, rows, it_next, c, x);
             float a = __bfloat162float(mlp[kMlpB1 + j]);
             for (int f = 0; f < kMlpIn; ++f)
-                a = fmaf(__bfloat162float(mlp[kMlpW1 + j * kMlpIn + f]), __bfloat162float(__float2bfloat16_rn(x[f])), a);
+                a = fmaf(__bfloat162float(mlp[kMlpW1 + j * kMlpIn + f]), xs[c * kMlpIn + f], a);
             h1[o] = __bfloat162float(__float2bfloat16_rn(fmaxf(a, 0.f)));
         }
         __syncthreads();
@@ -204,7 +220,7 @@ __device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __
             const int c = o / kMlpHidden, j = o % kMlpHidden;
             float a = __bfloat162float(mlp[kMlpB2 + j]);
             for (int k = 0; k < kMlpHidden; ++k)
-                a = fmaf(__bfloat162float(mlp[kMlpW2 + j * kMlpHidden + k]), h1[c * kMlpHidden + k], a);
+                a = fmaf(__bfloat162float(w2t[k * kMlpHidden + j]), h1[c * kMlpHidden + k], a);
             h2[o] = __bfloat162float(__float2bfloat16_rn(fmaxf(a, 0.f)));
         }
         __syncthreads();
@@ -1094,7 +1110,8 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
 __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, const uint32_t* __restrict__ outdeg,
                                  const uint32_t* __restrict__ eidx_off, IterRec* rec, RunCtl* C,
                                  const __nv_bfloat16* mlp, GraphFeat gf) {
-    __shared__ float dsm[2 * kCandidates * kMlpHidden + 8];
+    __shared__ __align__(16) unsigned char dsm_bytes[kDecideSmemBytes];
+    float* dsm = reinterpret_cast<float*>(dsm_bytes);
     __shared__ unsigned long long s_F;
     __shared__ unsigned s_n, s_row, s_last;
     if (threadIdx.x == 0) {
@@ -1810,8 +1827,8 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     int nb = 0;
     for (int a = 0; a < 4; ++a) nb = std::max(nb, std::max(g->pull_blocks_app[a], g->pull_blocks_tma[a]));
     if (nb > kMaxPullBlocks) return set_error(WEDGE_ERR_NOT_SUPPORTED, "too many pull blocks for this device");
-    static_assert((2 * kCandidates * kMlpHidden + 8) * 4 <= pull_records_bytes<kBFS>(),
-                  "the decision's activations live in the pull's record buffer");
+    static_assert(kDecideSmemBytes <= pull_records_bytes<kBFS>(),
+                  "the decision's activations and weights live in the pull's record buffer");
     WEDGE_TRY(dev_alloc(g, (void**)&g->bstat, (uint64_t)nb * sizeof(BlockStat)));
     return WEDGE_OK;
 }

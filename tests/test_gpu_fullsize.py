@@ -1,6 +1,7 @@
 """Parity at the full benchmark size (R-MAT scale 22, edge factor 16), in the
-launch configuration the benchmark times (default options): BFS, CC and SSSP
-bit-exact against the oracle over every vertex, PageRank within L1 1e-6."""
+launch configurations the benchmark times (the paper's settings and the
+precision/threshold pairs its autotuner picks): BFS, CC and SSSP bit-exact
+against the oracle over every vertex, PageRank within L1 1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -18,14 +19,27 @@ def g22():
     return gg.rmat(22, 16).with_weights(255)
 
 
+# the paper's settings, and settings the benchmark's autotuner picks on GB300
+SETTINGS = [None, (0, 500), (0, 2000), (1, 5000)]
+
+
+def _opts(app, st):
+    o = wedge.wedge_default_opts(app)
+    if st is not None:
+        o.log2_coarsen, o.tau_bp = st
+    return o
+
+
 def test_bfs_sssp_pr_scale22(g22):
     G = graph(g22)
     try:
         out = empty_u32(g22.V)
-        wedge.wedge_run_bfs(G.handle, 0, out)
-        np.testing.assert_array_equal(u32(out)[: g22.V], oracle.bfs_push(g22, 0))
-        wedge.wedge_run_sssp(G.handle, 0, out)
-        np.testing.assert_array_equal(u32(out)[: g22.V], oracle.sssp_dijkstra(g22, 0))
+        lv, dist = oracle.bfs_push(g22, 0), oracle.sssp_dijkstra(g22, 0)
+        for st in SETTINGS:
+            wedge.wedge_run_bfs(G.handle, 0, out, _opts("bfs", st))
+            np.testing.assert_array_equal(u32(out)[: g22.V], lv, err_msg=str(st))
+            wedge.wedge_run_sssp(G.handle, 0, out, _opts("sssp", st))
+            np.testing.assert_array_equal(u32(out)[: g22.V], dist, err_msg=str(st))
         rank = torch.empty(g22.V, dtype=torch.float32, device="cuda")
         wedge.wedge_run_pr(G.handle, rank, 20, 0.85)
         l1 = np.abs(rank.cpu().numpy().astype(np.float64) - oracle.pr_pull(g22, 0.85, 20)).sum()
@@ -39,7 +53,9 @@ def test_cc_scale22(g22):
     G = graph(s, with_weights=False)
     try:
         out = empty_u32(s.V)
-        wedge.wedge_run_cc(G.handle, out)
-        np.testing.assert_array_equal(u32(out)[: s.V], oracle.cc_union_find(s))
+        want = oracle.cc_union_find(s)
+        for st in SETTINGS:
+            wedge.wedge_run_cc(G.handle, out, _opts("cc", st))
+            np.testing.assert_array_equal(u32(out)[: s.V], want, err_msg=str(st))
     finally:
         G.close()
