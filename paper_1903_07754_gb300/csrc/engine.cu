@@ -179,13 +179,23 @@ __device__ __forceinline__ bool set_bit(uint32_t* bm, uint32_t v) {
 // time wins.  Without a model, or if no prediction is finite, the threshold
 // decides.  `sm` needs kDecideSmemBytes of shared memory: the activations
 // and features, then a copy of the weights (read straight from global memory
-// inside the dot products, each decision took ~20 us) with W2 stored
-// k-major, so that the threads of a layer read consecutive weights.
+// inside the dot products, each decision took ~20 us).  The device copy
+// stores W2 k-major, so that the threads of a layer read consecutive
+// weights; stage_model() copies it with 16-byte loads (`staged`: done
+// already, overlapped with other loads by the caller).
 constexpr int kDecideFloats = 2 * kCandidates * kMlpHidden + 8 + kCandidates * kMlpIn;
-constexpr int kDecideSmemBytes = kDecideFloats * 4 + ((kMlpParams * 2 + 15) / 16) * 16;
+constexpr int kModelBytes16 = ((kMlpParams * 2 + 15) / 16) * 16;
+constexpr int kDecideSmemBytes = kDecideFloats * 4 + kModelBytes16;
 static_assert((kDecideFloats * 4) % 16 == 0, "weights must start 16-byte aligned");
+
+__device__ __forceinline__ void stage_model(const __nv_bfloat16* mlp_global, float* sm) {
+    uint4* dst = reinterpret_cast<uint4*>(sm + kDecideFloats);
+    const uint4* src = reinterpret_cast<const uint4*>(mlp_global);
+    for (int i = threadIdx.x; i < kModelBytes16 / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 __device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __nv_bfloat16* mlp_global,
-                             const GraphFeat& gf, float* sm) {
+                             const GraphFeat& gf, float* sm, bool staged = false) {
     IterRec* r = rec + it_next;
     const unsigned long long F = __ldcg(&r->fullness);
     const unsigned nf = __ldcg(&r->nfront);
@@ -198,10 +208,7 @@ __device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __
     __nv_bfloat16* mlp = reinterpret_cast<__nv_bfloat16*>(sm + kDecideFloats);
     __nv_bfloat16* w2t = mlp + kMlpW2;  // W2 transposed: w2t[k * 64 + j] = W2[j][k]
     if (learned) {
-        for (int i = threadIdx.x; i < kMlpW2; i += blockDim.x) mlp[i] = mlp_global[i];  // W1, b1
-        for (int i = kMlpB2 + threadIdx.x; i < kMlpParams; i += blockDim.x) mlp[i] = mlp_global[i];  // b2, w3, b3
-        for (int i = threadIdx.x; i < kMlpHidden * kMlpHidden; i += blockDim.x)
-            w2t[(i % kMlpHidden) * kMlpHidden + i / kMlpHidden] = mlp_global[kMlpW2 + i];
+        if (!staged) stage_model(mlp_global, sm);
         if (threadIdx.x < kCandidates) {
             float x[kMlpIn];
             mlp_features(gf, (double)C->E, nf, (double)F, rows, it_next, threadIdx.x, x);
@@ -1208,6 +1215,9 @@ __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nbl
     __shared__ unsigned d_n, d_row;
     IterRec* rec = P.rec;
     RunCtl* C = P.ctl;
+    // the cost model's weights load while the slots are summed
+    const bool stage = C->switch_mode == WEDGE_SWITCH_LEARNED && P.mlp != nullptr;
+    if (stage) stage_model(P.mlp, dsm);
     if (threadIdx.x == 0) {
         d_F = 0;
         d_n = 0;
@@ -1241,7 +1251,7 @@ __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nbl
         if (P.trace) rec[it].t_pull1 = global_timer();
     }
     __syncthreads();
-    decide_block(rec, C, it + 1, P.mlp, P.gf, dsm);
+    decide_block(rec, C, it + 1, P.mlp, P.gf, dsm, stage);
     if (threadIdx.x == 0) {
         const unsigned loops = ++C->loops;
         const bool more = !C->done && loops < C->max_iters + 2;

@@ -186,6 +186,20 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
         out[i] = __float2bfloat16_rn(in[i]);
 }
 
+// The in-loop decision's copy of the model: BF16, with W2 stored k-major
+// (out[W2 + k*64 + j] = W2[j][k]) so that the deciding block's threads read
+// consecutive weights; the rest as laid out in the parameter array.
+__global__ void k_to_bf16_decision(const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += gridDim.x * blockDim.x) {
+        int o = i;
+        if (i >= kMlpW2 && i < kMlpB2) {
+            const int jk = i - kMlpW2;
+            o = kMlpW2 + (jk % kMlpHidden) * kMlpHidden + jk / kMlpHidden;
+        }
+        out[o] = __float2bfloat16_rn(in[i]);
+    }
+}
+
 // Device buffer that holds a caller's parameters (host or device) as FP32.
 static wedge_status params_on_device(const float* params, float** dev, bool* owned) {
     *owned = false;
@@ -275,11 +289,11 @@ wedge_status wedge_set_cost_model(wedge_graph_t g, const float* params) {
         g->has_model = false;
         return WEDGE_OK;
     }
-    if (!g->mlp_bf16) WEDGE_TRY(dev_alloc(g, (void**)&g->mlp_bf16, kMlpParams * sizeof(__nv_bfloat16)));
+    if (!g->mlp_bf16) WEDGE_TRY(dev_alloc(g, (void**)&g->mlp_bf16, kMlpParams * sizeof(__nv_bfloat16) + 16));
     float* dp = nullptr;
     bool owned = false;
     WEDGE_TRY(params_on_device(params, &dp, &owned));
-    k_to_bf16<<<20, 256>>>(dp, reinterpret_cast<__nv_bfloat16*>(g->mlp_bf16), kMlpParams);
+    k_to_bf16_decision<<<20, 256>>>(dp, reinterpret_cast<__nv_bfloat16*>(g->mlp_bf16));
     count_launch();
     cudaError_t e = cudaDeviceSynchronize();
     if (owned) dev_free(dp);
