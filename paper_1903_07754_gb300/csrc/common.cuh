@@ -49,6 +49,14 @@ constexpr int kTileE = kTileC * 32;         // 2048 edges per stage
 constexpr int kStages = 4;
 constexpr int kMetaPad = 2;                 // chunk metadata entries copied past a tile
 constexpr int kSliceShift = 8;              // log2(kSliceE)
+// Segment records a pull warp buffers at a time (a slice makes one per
+// destination segment, up to kSliceE; more take further passes).  The less
+// shared memory the pulls take, the more of the unified L1 caches gathers.
+#ifndef WEDGE_REC_CAP
+#define WEDGE_REC_CAP 64
+#endif
+constexpr int kRecCap = WEDGE_REC_CAP;
+static_assert(kRecCap % 32 == 0 && kRecCap <= kSliceE, "record buffer");
 
 // Per-iteration record (device).  Slot t describes frontier F_t and pull t.
 struct IterRec {

@@ -292,6 +292,11 @@ struct Stats {
 // record is applied with a plain read-modify-write, others with atomics.
 // ------------------------------------------------------------------------
 template <int APP>
+__device__ __forceinline__ void apply_records(const PullParams& P, unsigned it, uint32_t* next, const uint32_t* s_kid,
+                                              const typename Traits<APP>::T* s_val, unsigned base, unsigned end,
+                                              Stats& st, unsigned* s_lcnt, uint32_t* s_list);
+
+template <int APP>
 __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, const uint32_t* cur, uint32_t* next,
                                               const uint32_t (&sv)[kEPL], const uint32_t (&wv)[kEPL], int nvalid,
                                               uint32_t live, unsigned long long c, uint2 meta, unsigned next_head,
@@ -376,23 +381,46 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
         slot += (unsigned)__popc(Bb & below_me) << b;
         total += (unsigned)__popc(Bb) << b;
     }
+    // the buffer holds kRecCap records: more take further passes (a slice
+    // of many short segments), so that little shared memory is taken from L1
+    for (unsigned base = 0; base < total; base += kRecCap) {
+        if (base) __syncwarp();  // the previous pass's records are applied
+        unsigned sl = slot;
 #pragma unroll
-    for (int e = 0; e < kEPL; ++e) {
-        if ((K >> e) & 1u) {
-            const uint32_t kid = meta.y + __popc(heads & ((2u << (o + e)) - 1u) & ~1u);
-            s_kid[slot] = kid | (((X >> e) & 1u) << 31);
-            s_val[slot] = rv[e];
-            ++slot;
+        for (int e = 0; e < kEPL; ++e) {
+            if ((K >> e) & 1u) {
+                if (sl - base < (unsigned)kRecCap) {
+                    const uint32_t kid = meta.y + __popc(heads & ((2u << (o + e)) - 1u) & ~1u);
+                    s_kid[sl - base] = kid | (((X >> e) & 1u) << 31);
+                    s_val[sl - base] = rv[e];
+                }
+                ++sl;
+            }
         }
+        __syncwarp();
+        const unsigned end = total - base < (unsigned)kRecCap ? total : base + kRecCap;
+        apply_records<APP>(P, it, next, s_kid, s_val, base, end, st, s_lcnt, s_list);
     }
     __syncwarp();
-    for (unsigned r0 = 0; r0 < total; r0 += 32) {
+}
+
+// Applies records base .. end-1 of the warp's buffer (entry r - base) with
+// the warp's lanes: exclusive records by plain read-modify-write, others by
+// atomics; activated vertices are added to the frontier sums and staged for
+// the block's frontier list.
+template <int APP>
+__device__ __forceinline__ void apply_records(const PullParams& P, unsigned it, uint32_t* next, const uint32_t* s_kid,
+                                              const typename Traits<APP>::T* s_val, unsigned base, unsigned end,
+                                              Stats& st, unsigned* s_lcnt, uint32_t* s_list) {
+    using T = typename Traits<APP>::T;
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned r0 = base; r0 < end; r0 += 32) {
         const unsigned r = r0 + lane;
         bool act = false;
         uint32_t dv = 0;
-        if (r < total) {
-            const uint32_t kx = s_kid[r];
-            const T m = s_val[r];
+        if (r < end) {
+            const uint32_t kx = s_kid[r - base];
+            const T m = s_val[r - base];
             const bool excl = kx >> 31;
             dv = __ldg(P.vid + (kx & 0x7FFFFFFFu));
             if constexpr (APP == kBFS) {
@@ -458,13 +486,12 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
             if (act && slot < (unsigned)kListCap) s_list[slot] = dv;
         }
     }
-    __syncwarp();
 }
 
 template <int APP>
 constexpr int pull_records_bytes() {
     using T = typename Traits<APP>::T;
-    return kCW * kSliceE * (4 + (int)sizeof(T));
+    return kCW * kRecCap * (4 + (int)sizeof(T));
 }
 
 template <int APP>
@@ -479,6 +506,13 @@ constexpr int pull_stage_bytes() {
 template <int APP>
 constexpr int pull_smem_bytes(bool tma) {
     return pull_records_bytes<APP>() + kListCap * 4 + (tma ? pull_stage_bytes<APP>() : 0);
+}
+
+// ... at least the decision's activations and weights for the applications
+// whose last pull block decides (it reuses the block's buffers)
+template <int APP>
+constexpr int pull_launch_smem(bool tma) {
+    return (APP != kPR && pull_smem_bytes<APP>(tma) < kDecideSmemBytes) ? kDecideSmemBytes : pull_smem_bytes<APP>(tma);
 }
 
 // Which of a lane's edges still have to be pulled: bit i is set if edge
@@ -671,7 +705,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // layout: [records: values, ids][stages: barriers, src, w, metadata]
     T* s_val = reinterpret_cast<T*>(smem);
-    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
+    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kRecCap);
     uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + pull_records_bytes<APP>());
     unsigned char* stage = smem + pull_records_bytes<APP>() + kListCap * 4;
     uint64_t* full = reinterpret_cast<uint64_t*>(stage);
@@ -680,8 +714,8 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     uint32_t* s_w = s_src + kStages * kTileE;
     uint2* s_meta = reinterpret_cast<uint2*>(s_w + (APP == kSSSP ? kStages * kTileE : 0));
     const unsigned wsel = warp < kCW ? warp : 0;
-    uint32_t* my_kid = s_kid + wsel * kSliceE;
-    T* my_val = s_val + wsel * kSliceE;
+    uint32_t* my_kid = s_kid + wsel * kRecCap;
+    T* my_val = s_val + wsel * kRecCap;
     constexpr bool tma = TMA;
     if (threadIdx.x == 0) {
         s_F = 0;
@@ -1498,10 +1532,10 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
     if (C->done) return;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* s_val = reinterpret_cast<T*>(smem);
-    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kSliceE);
+    uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kRecCap);
     uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + pull_records_bytes<kMSBFS>());
-    uint32_t* my_kid = s_kid + warp * kSliceE;
-    T* my_val = s_val + warp * kSliceE;
+    uint32_t* my_kid = s_kid + warp * kRecCap;
+    T* my_val = s_val + warp * kRecCap;
     const unsigned long long gw = (unsigned long long)blockIdx.x * kCW + warp;
     const unsigned long long nw = (unsigned long long)gridDim.x * kCW;
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -1746,9 +1780,9 @@ __global__ void k_standalone_out(const BlockStat* __restrict__ bstat, unsigned n
 template <int APP>
 static void launch_pull(const wedge_graph* g, const PullParams& P, cudaStream_t s) {
     if (P.dense_tma)
-        k_pull<APP, true><<<g->pull_blocks_tma[APP], kPullThreads, pull_smem_bytes<APP>(true), s>>>(P);
+        k_pull<APP, true><<<g->pull_blocks_tma[APP], kPullThreads, pull_launch_smem<APP>(true), s>>>(P);
     else
-        k_pull<APP, false><<<g->pull_blocks_app[APP], kCW * 32, pull_smem_bytes<APP>(false), s>>>(P);
+        k_pull<APP, false><<<g->pull_blocks_app[APP], kCW * 32, pull_launch_smem<APP>(false), s>>>(P);
 }
 
 static void launch_pull_app(const wedge_graph* g, int app, const PullParams& P, cudaStream_t s) {
@@ -1767,7 +1801,7 @@ static void launch_pull_app(const wedge_graph* g, int app, const PullParams& P, 
 template <int APP, bool TMA>
 static wedge_status set_pull_variant(wedge_graph* g, int* blocks) {
     const int threads = TMA ? kPullThreads : kCW * 32;
-    const int bytes = pull_smem_bytes<APP>(TMA);
+    const int bytes = pull_launch_smem<APP>(TMA);
     WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_pull<APP, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     WEDGE_TRY_CUDA(cudaFuncSetAttribute(k_pull<APP, TMA>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared));
@@ -1837,8 +1871,6 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     int nb = 0;
     for (int a = 0; a < 4; ++a) nb = std::max(nb, std::max(g->pull_blocks_app[a], g->pull_blocks_tma[a]));
     if (nb > kMaxPullBlocks) return set_error(WEDGE_ERR_NOT_SUPPORTED, "too many pull blocks for this device");
-    static_assert(kDecideSmemBytes <= pull_records_bytes<kBFS>(),
-                  "the decision's activations and weights live in the pull's record buffer");
     WEDGE_TRY(dev_alloc(g, (void**)&g->bstat, (uint64_t)nb * sizeof(BlockStat)));
     return WEDGE_OK;
 }

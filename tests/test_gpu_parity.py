@@ -333,3 +333,39 @@ def test_invalid_arguments_are_rejected():
         assert e.value.status == 6
     finally:
         G.close()
+
+
+def _short_segments():
+    """Every destination has one or two in-edges, so a 256-edge pull slice
+    holds 170-256 destination segments: more records than a warp buffers at
+    once, applied in several passes."""
+    V = 50_000
+    v = np.arange(V, dtype=np.int64)
+    src = np.concatenate([(v * 7919 + 1) % V, ((v * 31 + 5) % V)[v % 3 == 0]])
+    dst = np.concatenate([v, v[v % 3 == 0]])
+    return gg.from_edges(V, src, dst).with_weights(1000)
+
+
+@pytest.mark.parametrize("switch", [wedge.SWITCH_ALWAYS_DENSE, wedge.SWITCH_ALWAYS_SPARSE, None])
+def test_many_short_segments(switch):
+    g = _short_segments()
+    assert g.src.size > 60_000
+    G = graph(g)
+    try:
+        for root in (0, 12345):
+            got, _ = _run(G, "bfs", root, opts("bfs", switch=switch))
+            np.testing.assert_array_equal(got, oracle.bfs_push(g, root))
+            got, _ = _run(G, "sssp", root, opts("sssp", switch=switch, k=1))
+            np.testing.assert_array_equal(got, oracle.sssp_dijkstra(g, root))
+        rank = torch.empty(g.V, dtype=torch.float32, device="cuda")
+        wedge.wedge_run_pr(G.handle, rank, 20, 0.85)
+        assert np.abs(rank.cpu().numpy() - oracle.pr_pull(g, 0.85, 20)).sum() <= PR_L1_TOL
+    finally:
+        G.close()
+    s = gg.symmetrize(gg.Graph(g.V, g.offsets, g.src))
+    S = graph(s, with_weights=False)
+    try:
+        got, _ = _run(S, "cc", 0, opts("cc", switch=switch))
+        np.testing.assert_array_equal(got, oracle.cc_union_find(s))
+    finally:
+        S.close()
