@@ -503,9 +503,15 @@ constexpr int pull_stage_bytes() {
 
 // Shared memory of a pull: the record buffers and the block's frontier
 // list, plus the stages when dense pulls use bulk copies.
+// (PageRank keeps no frontier list)
+template <int APP>
+constexpr int pull_list_bytes() {
+    return APP == kPR ? 0 : kListCap * 4;
+}
+
 template <int APP>
 constexpr int pull_smem_bytes(bool tma) {
-    return pull_records_bytes<APP>() + kListCap * 4 + (tma ? pull_stage_bytes<APP>() : 0);
+    return pull_records_bytes<APP>() + pull_list_bytes<APP>() + (tma ? pull_stage_bytes<APP>() : 0);
 }
 
 // ... at least the decision's activations and weights for the applications
@@ -707,7 +713,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     T* s_val = reinterpret_cast<T*>(smem);
     uint32_t* s_kid = reinterpret_cast<uint32_t*>(s_val + kCW * kRecCap);
     uint32_t* s_list = reinterpret_cast<uint32_t*>(smem + pull_records_bytes<APP>());
-    unsigned char* stage = smem + pull_records_bytes<APP>() + kListCap * 4;
+    unsigned char* stage = smem + pull_records_bytes<APP>() + pull_list_bytes<APP>();
     uint64_t* full = reinterpret_cast<uint64_t*>(stage);
     uint64_t* empty = full + kStages;
     uint32_t* s_src = reinterpret_cast<uint32_t*>(stage + 2 * kStages * 8);
