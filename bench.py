@@ -625,8 +625,10 @@ def bench_studies(args, wedge, torch, dev, world):
     CC on the symmetrised graph): the split of time between pull and
     transformation (Fig. 8), per-iteration dense vs Wedge times with the
     active share of edges (Fig. 9, from the candidate-timing trace), a
-    sweep of the fullness threshold including "always transform" (Fig. 10)
-    and a sweep of the precision (Fig. 11)."""
+    sweep of the fullness threshold including "always transform" (Fig. 10),
+    a sweep of the precision (Fig. 11), and for CC and SSSP the iterations
+    with in-place updates vs synchronous pulls (Section 5.2's multi-hop
+    propagation)."""
     g, s = make_inputs(args.scale)
     G = wedge.Graph.from_csc(g)
     S = wedge.Graph.from_csc(s, with_weights=False)
@@ -669,6 +671,21 @@ def bench_studies(args, wedge, torch, dev, world):
             o = wedge.wedge_default_opts(app)
             o.log2_coarsen = k
             r["precision_sweep_ms"][f"k{k}"] = _events(torch, lambda: run(H.handle, o), 5)
+        # multi-hop propagation (Section 5.2): iterations with in-place
+        # updates vs every pull reading the previous iteration's values
+        if app != "bfs":
+            r["multi_hop"] = {}
+            for k in (0, 2, 4):
+                row = {}
+                for name, sync in (("in_place", 0), ("synchronous", 1)):
+                    o = wedge.wedge_default_opts(app)
+                    o.log2_coarsen = k
+                    o.synchronous = sync
+                    st = {"cc": lambda: wedge.wedge_run_cc(H.handle, out, o),
+                          "sssp": lambda: wedge.wedge_run_sssp(H.handle, 0, out, o)}[app]()
+                    row[f"{name}_iters"] = st.iters
+                    row[f"{name}_ms"] = _events(torch, lambda: run(H.handle, o), 3)
+                r["multi_hop"][f"k{k}"] = row
         res[app] = r
     G.close()
     S.close()
@@ -718,6 +735,11 @@ def bench_grid(args, wedge, torch, dev, world):
         t = _events(torch, lambda: wedge.wedge_run_sssp(G.handle, 0, out, o, False), 2)
         st = wedge.wedge_run_sssp(G.handle, 0, out, o)
         study[f"k{k}"] = {"ms": t, "iters": st.iters, "edges_pulled": st.edges_pulled}
+        if k in (0, 6):
+            # the same pulls reading only the previous iteration's distances
+            o.synchronous = 1
+            st = wedge.wedge_run_sssp(G.handle, 0, out, o)
+            study[f"k{k}"]["synchronous_iters"] = st.iters
     G.close()
     res["sssp_p0.01_always_sparse_by_precision"] = study
     line = _base_line("GTEPS (BFS+SSSP) on the 4096^2 grid", total_e / (total_ms / 1e3) / 1e9, "GTEPS", total_ms, 2,

@@ -85,7 +85,14 @@ typedef struct {
     uint32_t switch_mode;  /* wedge_switch */
     uint32_t max_iters;    /* 0 = default (2^20) */
     uint32_t trace;        /* nonzero: keep per-iteration records for wedge_get_trace */
-    uint32_t reserved[3];  /* must be zero */
+    uint32_t synchronous;  /* CC/SSSP: nonzero = every pull reads the values of the
+                            * previous iteration (double buffer, host-driven loop)
+                            * instead of the in-place updates that let values
+                            * move several hops per iteration (Section 5.2,
+                            * "Frontier Precision"); iteration counts and traces
+                            * then follow the synchronous definition exactly.
+                            * BFS is level-synchronous either way. */
+    uint32_t reserved[2];  /* must be zero */
 } wedge_opts;
 
 /* Defaults from the paper's tuned settings (Section 5, "Experiments"):

@@ -129,6 +129,7 @@ struct wedge_graph {
     bool eidx_off_owned = false;
     // scratch for runs
     uint32_t* vals = nullptr;      // V values of the current run
+    uint32_t* vals_sync = nullptr; // synchronous CC/SSSP runs: the second value buffer
     uint32_t* bm[2] = {nullptr, nullptr};  // vertex frontier bitmaps
     uint32_t* wb = nullptr;        // Wedge Frontier bitmap, ceil(NC/32) words
     uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries

@@ -61,7 +61,9 @@ struct PullParams {
     const uint32_t* eidx_off;
     unsigned long long E;
     unsigned long long NC;
-    uint32_t* vals;              // BFS levels / CC labels / SSSP distances
+    uint32_t* vals;              // BFS levels / CC labels / SSSP distances (written by the pull)
+    const uint32_t* vread;       // CC/SSSP values the pull gathers: vals, or the previous
+                                 // iteration's buffer in synchronous runs
     uint32_t* bm[2];             // vertex frontier bitmaps indexed by iteration parity
     const uint32_t* clist;       // Wedge Frontier list (sparse pulls)
     uint32_t* wb;                // Wedge Frontier bitmap: consumed words are zeroed
@@ -151,12 +153,12 @@ __device__ __forceinline__ typename Traits<APP>::T candidate(const PullParams& P
     if constexpr (APP == kBFS) {
         return (__ldg(cur + (u >> 5)) >> (u & 31)) & 1u;
     } else if constexpr (APP == kCC) {
-        return P.vals[u];
+        return P.vread[u];
     } else if constexpr (APP == kMSBFS) {
         // written earlier in the same persistent launch: read through L2
         return __ldcg(((it & 1) ? P.fb[1] : P.fb[0]) + u);
     } else if constexpr (APP == kSSSP) {
-        const uint32_t d = P.vals[u];
+        const uint32_t d = P.vread[u];
         if (d == kInf) return kInf;
         const unsigned long long s = (unsigned long long)d + w;
         return s > kSat ? kSat : (uint32_t)s;
@@ -1905,6 +1907,7 @@ static PullParams pull_params(wedge_graph* g, int trace, int app = kCC) {
     P.E = g->E;
     P.NC = g->NC;
     P.vals = g->vals;
+    P.vread = g->vals;
     P.bm[0] = g->bm[0];
     P.bm[1] = g->bm[1];
     P.clist = g->clist;
@@ -2000,8 +2003,7 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
 static wedge_status check_opts(const wedge_opts* o) {
     if (o->log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
     if (o->switch_mode > WEDGE_SWITCH_ALWAYS_SPARSE) return set_error(WEDGE_ERR_INVALID_ARG, "bad switch_mode");
-    if (o->reserved[0] || o->reserved[1] || o->reserved[2])
-        return set_error(WEDGE_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o->reserved[0] || o->reserved[1]) return set_error(WEDGE_ERR_INVALID_ARG, "reserved option fields must be zero");
     return WEDGE_OK;
 }
 
@@ -2053,6 +2055,39 @@ static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, cons
     }
 }
 
+// Synchronous CC/SSSP (the opts' `synchronous`): pull t reads buffer t & 1
+// and writes buffer (t + 1) & 1, which first receives a copy of the values
+// (destinations outside a Wedge Frontier keep theirs).  Launch i of the loop
+// is pull i, or returns at once after the run is done.
+__global__ void k_sync_copy(const RunCtl* C, const uint32_t* __restrict__ from, uint32_t* __restrict__ to,
+                            uint32_t V) {
+    if (C->done) return;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x)
+        to[v] = from[v];
+}
+
+static wedge_status host_loop_sync(wedge_graph* g, int app, const PullParams& P, const XformParams& X,
+                                   uint32_t max_iters, cudaStream_t s) {
+    uint32_t* vb[2] = {g->vals, g->vals_sync};
+    const int batch = 8;
+    uint32_t launched = 0;
+    for (;;) {
+        for (int b = 0; b < batch; ++b, ++launched) {
+            k_sync_copy<<<g->num_sms * 4, 256, 0, s>>>(g->ctl, vb[launched & 1], vb[(launched + 1) & 1], g->V);
+            count_launch();
+            PullParams Q = P;
+            Q.vread = vb[launched & 1];
+            Q.vals = vb[(launched + 1) & 1];
+            launch_pull_app(g, app, Q, s);
+            launch_xform(g, X, s);
+        }
+        WEDGE_TRY_CUDA(cudaGetLastError());
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+        if (g->h_ctl->done || launched > max_iters + 2) return WEDGE_OK;
+    }
+}
+
 static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uint32_t* out,
                                      const wedge_opts* opts_in, wedge_stats* stats, cudaStream_t s) {
     wedge_opts o;
@@ -2073,7 +2108,9 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     init.k = o.log2_coarsen;
     init.E = g->E;
     const uint64_t wb_words = (g->NC + 31) / 32 + 1;
-    if (!trace && !g->loop_exec[app] && !g->loop_failed) {
+    const bool sync = o.synchronous && app != kBFS;
+    if (sync && !g->vals_sync) WEDGE_TRY(dev_alloc(g, (void**)&g->vals_sync, (uint64_t)g->V * 4));
+    if (!trace && !sync && !g->loop_exec[app] && !g->loop_failed) {
         if (build_loop_graph(g, app) != WEDGE_OK) {
             g->loop_failed = true;  // this graph keeps the host-polled loop
             std::fprintf(stderr, "wedge: device loop graph unavailable (%s); using the host-polled loop\n",
@@ -2091,14 +2128,18 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     XformParams X = xform_params(g, trace);
     launch_xform(g, X, s);
     WEDGE_TRY_CUDA(cudaGetLastError());
-    if (!trace && g->loop_exec[app]) {
+    const uint32_t* result = g->vals;
+    if (sync) {
+        WEDGE_TRY(host_loop_sync(g, app, P, X, max_iters, s));
+        if (g->h_ctl->it & 1) result = g->vals_sync;  // pull it - 1 wrote buffer it & 1
+    } else if (!trace && g->loop_exec[app]) {
         WEDGE_TRY_CUDA(cudaGraphLaunch(g->loop_exec[app], s));
     } else {
         WEDGE_TRY(host_loop(g, app, P, X, max_iters, s));
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
-    WEDGE_TRY_CUDA(cudaMemcpyAsync(out, g->vals, (uint64_t)g->V * 4, cudaMemcpyDefault, s));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(out, result, (uint64_t)g->V * 4, cudaMemcpyDefault, s));
     g->last_trace = trace;
     g->last_stream = s;
     return fill_stats(g, s, stats);
@@ -2458,6 +2499,7 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     PullParams P = pull_params(g, 0);
     P.decide = 0;  // one pull: k_standalone_out reduces the block slots
     P.vals = d_values;
+    P.vread = d_values;
     P.bm[iter & 1] = const_cast<uint32_t*>(d_cur_bitmap ? d_cur_bitmap : d_next_bitmap);
     P.bm[(iter + 1) & 1] = d_next_bitmap;
     P.clist = d_chunk_list ? d_chunk_list : g->clist;

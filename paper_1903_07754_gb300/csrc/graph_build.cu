@@ -265,6 +265,7 @@ static void free_graph(wedge_graph* g) {
     if (g->eidx_off_owned) dev_free(g->eidx_off);
     if (g->eidx_owned) dev_free(g->eidx);
     dev_free(g->vals);
+    dev_free(g->vals_sync);
     dev_free(g->bm[0]);
     dev_free(g->bm[1]);
     dev_free(g->wb);

@@ -120,6 +120,38 @@ def test_bfs_trace_matches_oracle(rmat, rmat_dev, tau, k):
             assert rec["nchunks"] == ot[t, 3], t
 
 
+@pytest.mark.parametrize("app", ["cc", "sssp"])
+@pytest.mark.parametrize("policy,tau,k", [("threshold", 2000, 2), ("threshold", 500, 0), ("threshold", 5000, 1),
+                                          ("sparse", 0, 3), ("dense", 0, 0)])
+def test_synchronous_trace_matches_oracle(rmat, rmat_dev, sym, sym_dev, app, policy, tau, k):
+    """Synchronous CC/SSSP (every pull reads the previous iteration's values,
+    as the oracle's Wedge run does): every iteration's frontier size,
+    fullness, decision and Wedge Frontier size agree, and so do the values
+    and the iteration count."""
+    g, G = (sym, sym_dev) if app == "cc" else (rmat, rmat_dev)
+    sw = {"threshold": None, "sparse": wedge.SWITCH_ALWAYS_SPARSE, "dense": wedge.SWITCH_ALWAYS_DENSE}[policy]
+    pol = {"threshold": oracle.POLICY_THRESHOLD, "sparse": oracle.POLICY_ALWAYS_SPARSE,
+           "dense": oracle.POLICY_ALWAYS_DENSE}[policy]
+    o = opts(app, switch=sw, tau=tau, k=k, trace=1)
+    o.synchronous = 1
+    got, st = _run(G, app, 0, o)
+    tr = wedge.wedge_get_trace(G.handle)
+    want, ot = oracle.wedge_run(app, g, 0, pol, tau, 32 << k)
+    np.testing.assert_array_equal(got, want)
+    assert len(tr) == ot.shape[0] == st.iters
+    for t, rec in enumerate(tr):
+        assert rec["nfront"] == ot[t, 0], t
+        assert rec["fullness"] == ot[t, 1], t
+        assert rec["mode"] == ot[t, 2], t
+        if rec["mode"]:
+            assert rec["nchunks"] == ot[t, 3], t
+    # untraced (the loop without records) ends the same way
+    o.trace = 0
+    got2, st2 = _run(G, app, 0, o)
+    np.testing.assert_array_equal(got2, want)
+    assert st2.iters == st.iters
+
+
 @pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse3", "tau50k1"])
 def test_cc_matches_union_find(sym, sym_dev, mode):
     want = oracle.cc_union_find(sym)
