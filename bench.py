@@ -121,6 +121,10 @@ STEP_TUNE_GRID = {
 }
 
 
+# fullness thresholds (basis points of |E|) tried for the push/pull hybrid
+HYBRID_TAUS = (100, 500, 2000, 5000)
+
+
 def tune_step(wedge, G, S, g):
     """Wedge Frontier precision and fullness threshold per application,
     picked by the project's autotuner on the step's graphs, with BFS and
@@ -437,6 +441,41 @@ def main():
             per_app[name]["speedup_learned_vs_dense_pull"] = per_app[name]["dense_pull_ms"] / t_l
         wedge.wedge_set_cost_model(G.handle, None)
         wedge.wedge_set_cost_model(S.handle, None)
+    # the push/pull hybrid (the comparison engine: sparse iterations push
+    # over the frontier's out-edges, dense ones pull), its threshold tuned
+    # from the tuning root like Wedge's settings, timed on the measured root
+    import graphgen as gg
+    troot = int(gg.roots(g, 1, seed=7)[0])
+
+    def run_app(name, o, root):
+        if name == "bfs":
+            return wedge.wedge_run_bfs(G.handle, root, lvl, o, False)
+        if name == "cc":
+            return wedge.wedge_run_cc(S.handle, lab, o, False)
+        return wedge.wedge_run_sssp(G.handle, root, dist_, o, False)
+
+    def hybrid_opts(name, tau, always_push=False):
+        o = wedge.wedge_default_opts(name)
+        o.sparse_push = 1
+        o.tau_bp = tau
+        if always_push:
+            o.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
+        return o
+
+    for name in runs:
+        t_best, tau_best = None, None
+        for tau in HYBRID_TAUS:
+            oh = hybrid_opts(name, tau)
+            t = time_fn(lambda: run_app(name, oh, troot), reps=3)
+            if t_best is None or t < t_best:
+                t_best, tau_best = t, tau
+        oh = hybrid_opts(name, tau_best)
+        t_h = time_fn(lambda: run_app(name, oh, 0))
+        op = hybrid_opts(name, tau_best, always_push=True)
+        t_pp = time_fn(lambda: run_app(name, op, 0))
+        per_app[name].update({"push_pull_hybrid_ms": t_h, "push_pull_hybrid_tau_bp": tau_best,
+                              "speedup_vs_push_pull_hybrid": t_h / per_app[name]["ms"],
+                              "push_every_iteration_ms": t_pp})
     t_pr = time_fn(lambda: wedge.wedge_run_pr(G.handle, rank_t, PR_ITERS, DAMPING, None, False))
     per_app["pr"] = {"ms": t_pr, "gteps": edges["pr"] / (t_pr / 1e3) / 1e9}
     st = step(want_stats=True)

@@ -92,7 +92,16 @@ typedef struct {
                             * "Frontier Precision"); iteration counts and traces
                             * then follow the synchronous definition exactly.
                             * BFS is level-synchronous either way. */
-    uint32_t reserved[2];  /* must be zero */
+    uint32_t sparse_push;  /* nonzero: the push/pull hybrid instead of Wedge - a
+                            * comparison engine, the analogue of the push-based and
+                            * hybrid systems the paper measures against (Sections 1,
+                            * 6): iterations the fullness test finds sparse push
+                            * over the frontier's out-edges (an out-edge CSR is
+                            * built on the graph's first such run, about 8E + 8V
+                            * bytes more), dense ones pull over all edges.
+                            * log2_coarsen is ignored; LEARNED acts as THRESHOLD;
+                            * not with `synchronous`. */
+    uint32_t reserved[1];  /* must be zero */
 } wedge_opts;
 
 /* Defaults from the paper's tuned settings (Section 5, "Experiments"):

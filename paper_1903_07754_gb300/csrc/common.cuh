@@ -11,6 +11,10 @@
 //   eidx_off[V+1], eidx[]    edge index (Sections 3.3, 4): row u lists the
 //                            chunks that hold u's out-edges, once each
 //   npieces_max              sum over u of ceil(|row u| / 32)
+//   csr_off[V+1], csr_dst[E], csr_src[E], csr_w[E], kid_of[V]
+//                            out-edges (CSR) for the push/pull hybrid, built on
+//                            its first run: edge j leaves csr_src[j] for
+//                            csr_dst[j]; kid_of[v] = index of v in vid
 // The head mask plus vid let a warp find the destination of each of its
 // edges from the chunk alone, the role the paper gives to Vector-Sparse
 // (Section 2.2): no search in off[] on the hot path.
@@ -150,6 +154,16 @@ struct wedge_graph {
     // device loop graphs (one per frontier application) and the PageRank graph
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t loop_exec_push[3] = {nullptr, nullptr, nullptr};
+    // push/pull hybrid (the comparison engine): out-edges, built on first use
+    uint32_t* csr_off = nullptr;
+    uint32_t* csr_dst = nullptr;
+    uint32_t* csr_src = nullptr;
+    uint32_t* csr_w = nullptr;
+    uint32_t* kid_of = nullptr;
+    uint2* push_pieces = nullptr;
+    uint64_t npieces_push_max = 0;
+    bool last_push = false;
     bool loop_failed = false;
     cudaGraphExec_t pr_exec = nullptr;
     uint32_t pr_exec_iters = 0;
@@ -195,6 +209,9 @@ namespace wedge {
 wedge_status set_error(wedge_status s, const std::string& msg);
 wedge_status cuda_error(cudaError_t e, const char* what);
 void count_launch(uint64_t n = 1);
+
+// ---- the push/pull hybrid's out-edges, built on its first run (graph_build.cu) ----
+wedge_status build_csr(wedge_graph* g, cudaStream_t s);
 
 #define WEDGE_TRY_CUDA(expr)                                      \
     do {                                                          \

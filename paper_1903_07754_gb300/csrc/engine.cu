@@ -85,7 +85,18 @@ struct PullParams {
     BlockStat* bstat;            // per-block results
     uint32_t* visk;              // BFS runs: visited bit per destination index (nullptr: no skipping)
     int decide;                  // runs: the pull's last block takes the decision for the next pull
+    int hybrid;                  // push/pull hybrid runs: the pull only serves dense iterations
     cudaGraphConditionalHandle cond;  // device loop: the while node's condition (0 outside a graph)
+};
+
+// The push/pull hybrid's out-edges and work pieces (rows of the frontier's
+// out-edges cut into pieces of at most 32 edges by k_xform_scan).
+struct PushParams {
+    const uint32_t* dst;         // CSR: edge j ends at dst[j]
+    const uint32_t* src;         //      and leaves src[j]
+    const uint32_t* w;           //      with weight w[j] (SSSP)
+    const uint32_t* kid_of;      // index of a vertex in vid (BFS visited bits)
+    const uint2* pieces;
 };
 
 struct XformParams {
@@ -279,6 +290,29 @@ struct Stats {
     unsigned int row;
 };
 
+// A vertex activated for the next frontier: its out-degree (fullness), its
+// edge-index row length (a feature of the learned switch) and the count.
+__device__ __forceinline__ void count_active(const PullParams& P, uint32_t v, Stats& st) {
+    st.F += __ldg(P.outdeg + v);
+    st.n += 1;
+    st.row += __ldg(P.eidx_off + v + 1) - __ldg(P.eidx_off + v);
+}
+
+// The block's frontier list (whole warp): one shared-memory reservation per
+// warp and call, none once the block's stage has overflowed.
+__device__ __forceinline__ void stage_list(bool act, uint32_t v, unsigned* s_lcnt, uint32_t* s_list) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned am = __ballot_sync(kFull, act);
+    if (am && *reinterpret_cast<volatile unsigned*>(s_lcnt) <= (unsigned)kListCap) {
+        const unsigned leader = __ffs(am) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(s_lcnt, (unsigned)__popc(am));
+        base = __shfl_sync(kFull, base, leader);
+        const unsigned slot = base + __popc(am & ((1u << lane) - 1u));
+        if (act && slot < (unsigned)kListCap) s_list[slot] = v;
+    }
+}
+
 // ------------------------------------------------------------------------
 // One warp slice of the pull (K1/K4 + K5): kSliceC chunks, kEPL = 8 edges
 // per lane (lane L holds edges 8*(L&3) .. +7 of slice chunk L>>2).
@@ -470,23 +504,9 @@ __device__ __forceinline__ void apply_records(const PullParams& P, unsigned it, 
                 }
                 act = changed && set_bit(next, dv);
             }
-            if (act) {
-                st.F += __ldg(P.outdeg + dv);
-                st.n += 1;
-                st.row += __ldg(P.eidx_off + dv + 1) - __ldg(P.eidx_off + dv);
-            }
+            if (act) count_active(P, dv, st);
         }
-        // the block's frontier list: one reservation per warp and round,
-        // none once the block's stage has overflowed (PageRank has none)
-        const unsigned am = (APP == kPR) ? 0u : __ballot_sync(kFull, act);
-        if (am && *reinterpret_cast<volatile unsigned*>(s_lcnt) <= (unsigned)kListCap) {
-            const unsigned leader = __ffs(am) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(s_lcnt, (unsigned)__popc(am));
-            base = __shfl_sync(kFull, base, leader);
-            const unsigned slot = base + __popc(am & ((1u << lane) - 1u));
-            if (act && slot < (unsigned)kListCap) s_list[slot] = dv;
-        }
+        if constexpr (APP != kPR) stage_list(act, dv, s_lcnt, s_list);
     }
 }
 
@@ -689,6 +709,60 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
 
 __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nblocks, float* dsm);
 
+// End of a pull (or push) block: the warps' frontier sums are added up, the
+// block's sums go to its own slot and its staged frontier list to a range
+// of the next list reserved with one atomic (none if the stage overflowed:
+// the list then stays short of the frontier and the transformation scans
+// the bitmap instead).  With DECIDE, the last block to finish (ticket) sums
+// the slots and takes the decision for the next iteration.
+template <bool DECIDE>
+__device__ __forceinline__ void finish_block(const PullParams& P, unsigned it, Stats st, unsigned long long* s_F,
+                                             unsigned* s_n, unsigned* s_row, unsigned* s_lcnt,
+                                             const uint32_t* s_list, float* dsm) {
+    __shared__ unsigned s_lbase;
+    if constexpr (DECIDE) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            st.F += __shfl_down_sync(kFull, st.F, d);
+            st.n += __shfl_down_sync(kFull, st.n, d);
+            st.row += __shfl_down_sync(kFull, st.row, d);
+        }
+        if ((threadIdx.x & 31) == 0 && st.n) {
+            atomicAdd(s_F, st.F);
+            atomicAdd(s_n, st.n);
+            atomicAdd(s_row, st.row);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        BlockStat b;
+        b.F = *s_F;
+        b.n = *s_n;
+        b.row = *s_row;
+        b.lcnt = *s_lcnt;
+        b.pad_ = 0;
+        P.bstat[blockIdx.x] = b;
+        s_lbase = (*s_lcnt && *s_lcnt <= (unsigned)kListCap) ? atomicAdd(&P.rec[it + 1].nlist, *s_lcnt) : ~0u;
+    }
+    __syncthreads();
+    publish_list(P.flist[(it + 1) & 1], s_list, *s_lcnt, s_lbase);
+    if constexpr (DECIDE) {
+        if (P.decide) {
+            __shared__ unsigned s_last;
+            RunCtl* C = P.ctl;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                decide_after_pull(P, it, gridDim.x, dsm);
+                if (threadIdx.x == 0) C->ticket = 0;
+            }
+        }
+    }
+}
+
 template <int APP, bool TMA>
 __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direct_min_blocks(APP))
     k_pull(const PullParams P) {
@@ -708,6 +782,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     }
     const unsigned it = C->it;
     const unsigned mode = P.rec[it].mode;
+    if (P.hybrid && mode != 0) return;  // the push serves this iteration
     const unsigned k = P.rec[it].k;
     const unsigned nchunks = P.rec[it].nchunks;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -836,51 +911,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
         pull_sparse<APP>(P, it, k, nchunks, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
                          (unsigned long long)gridDim.x * kCW, &s_lcnt, s_list);
 
-    if constexpr (APP != kPR) {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            st.F += __shfl_down_sync(kFull, st.F, d);
-            st.n += __shfl_down_sync(kFull, st.n, d);
-            st.row += __shfl_down_sync(kFull, st.row, d);
-        }
-        if (lane == 0 && st.n) {
-            atomicAdd(&s_F, st.F);
-            atomicAdd(&s_n, st.n);
-            atomicAdd(&s_row, st.row);
-        }
-    }
-    // this block's frontier sums go to its own slot; its staged frontier
-    // list goes to a range of the next list reserved with one atomic (none
-    // if the stage overflowed: the list then stays short of the frontier
-    // and the transformation scans the bitmap instead)
-    __shared__ unsigned s_lbase;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        BlockStat b;
-        b.F = s_F;
-        b.n = s_n;
-        b.row = s_row;
-        b.lcnt = s_lcnt;
-        b.pad_ = 0;
-        P.bstat[blockIdx.x] = b;
-        s_lbase = (s_lcnt && s_lcnt <= (unsigned)kListCap) ? atomicAdd(&P.rec[it + 1].nlist, s_lcnt) : ~0u;
-    }
-    __syncthreads();
-    publish_list(P.flist[(it + 1) & 1], s_list, s_lcnt, s_lbase);
-    if constexpr (APP != kPR) {
-        if (P.decide) {
-            __shared__ unsigned s_last;
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                decide_after_pull(P, it, gridDim.x, reinterpret_cast<float*>(smem));
-                if (threadIdx.x == 0) C->ticket = 0;
-            }
-        }
-    }
+    finish_block<APP != kPR>(P, it, st, &s_F, &s_n, &s_row, &s_lcnt, s_list, reinterpret_cast<float*>(smem));
 }
 
 // ------------------------------------------------------------------------
@@ -1092,6 +1123,21 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
     }
 }
 
+// Before iteration `it` fills the next frontier: the bitmap it fills held
+// F_{it-1}, so clear it (by its list when that list is complete), and zero
+// the record the iteration accumulates into.  Idempotent until then.
+__device__ __forceinline__ void prepare_iteration(const XformParams& X, unsigned it, unsigned long long tid,
+                                                  unsigned long long nth) {
+    if (it > 0) {
+        const IterRec& pr = X.rec[it - 1];
+        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
+        clear_frontier(clr, X.bm_words, ((it + 1) & 1) ? X.flist[1] : X.flist[0], pr.nlist == pr.nfront, pr.nfront,
+                       nullptr, tid, nth);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
+        reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
+}
+
 __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
     RunCtl* C = X.ctl;
     const uint32_t* bm;
@@ -1105,16 +1151,7 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
         if (C->done) return;
         const unsigned it = C->it;
         if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
-        // the bitmap that pull `it` fills held F_{it-1}: clear it (by its list
-        // when that list is complete), and the record pull `it` accumulates into
-        if (it > 0) {
-            const IterRec& pr = X.rec[it - 1];
-            uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
-            clear_frontier(clr, X.bm_words, ((it + 1) & 1) ? X.flist[1] : X.flist[0], pr.nlist == pr.nfront,
-                           pr.nfront, nullptr, tid, nth);
-        }
-        if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
-            reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
+        prepare_iteration(X, it, tid, nth);
         r = X.rec + it;
         if (r->mode == 0) return;
         if (r->nlist == r->nfront) {
@@ -1152,6 +1189,114 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
     }
+}
+
+// ------------------------------------------------------------------------
+// The push/pull hybrid (a comparison engine, not Wedge): iterations the
+// fullness test finds sparse push over the frontier's out-edges instead of
+// pulling over a Wedge Frontier; dense ones are the same pull.  The loop
+// body is k_xform_scan over the out-edge rows (it also clears the bitmap and
+// record the iteration fills), k_push_expand, k_pull: each kernel serves
+// only its own kind of iteration, and the deciding blocks of the push and of
+// the pull advance the iteration.
+// ------------------------------------------------------------------------
+
+// A dense iteration that follows a push in the same loop body: its
+// preparation (k_xform_scan prepared the push's iteration).
+__global__ void __launch_bounds__(kXformThreads) k_hybrid_prepare(const XformParams X) {
+    const RunCtl* C = X.ctl;
+    if (C->done) return;
+    const unsigned it = C->it;
+    if (X.rec[it].mode != 0) return;
+    prepare_iteration(X, it, blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x,
+                      (unsigned long long)gridDim.x * blockDim.x);
+}
+
+// Relaxes destination v over edge j (source Q.src[j]) in place; true if v
+// joins the next frontier (its bit was not yet set).
+template <int APP>
+__device__ __forceinline__ bool push_relax(const PullParams& P, const PushParams& Q, uint32_t j, uint32_t v,
+                                           unsigned it, uint32_t* next) {
+    if constexpr (APP == kBFS) {
+        if (*reinterpret_cast<volatile uint32_t*>(P.vals + v) != kInf) return false;
+        if (atomicCAS(P.vals + v, kInf, it + 1) != kInf) return false;
+        if (P.visk) {
+            const uint32_t kid = __ldg(Q.kid_of + v);
+            atomicOr(P.visk + (kid >> 5), 1u << (kid & 31));
+        }
+        return set_bit(next, v);
+    } else {
+        const uint32_t du = P.vals[__ldg(Q.src + j)];
+        uint32_t c = du;
+        if constexpr (APP == kSSSP) {
+            if (du == kInf) return false;
+            const unsigned long long sum = (unsigned long long)du + __ldg(Q.w + j);
+            c = sum > kSat ? kSat : (uint32_t)sum;
+        }
+        if (c >= *reinterpret_cast<volatile uint32_t*>(P.vals + v)) return false;
+        return c < atomicMin(P.vals + v, c) && set_bit(next, v);
+    }
+}
+
+// One push iteration: the pieces are expanded like the transformation's
+// (a warp task of up to 32 pieces, fewer when there are too few to give
+// every warp a task), one out-edge per lane and round.
+template <int APP>
+__global__ void __launch_bounds__(kXformThreads) k_push_expand(const PullParams P, const PushParams Q) {
+    __shared__ uint32_t s_list[kListCap];
+    __shared__ unsigned long long s_F;
+    __shared__ unsigned s_n, s_row, s_lcnt;
+    RunCtl* C = P.ctl;
+    if (C->done) return;
+    const unsigned it = C->it;
+    if (P.rec[it].mode == 0) return;  // a dense iteration: the pull serves it
+    const unsigned n = P.rec[it].npieces;
+    if (threadIdx.x == 0) {
+        s_F = 0;
+        s_n = 0;
+        s_row = 0;
+        s_lcnt = 0;
+        if (P.trace && blockIdx.x == 0) P.rec[it].t_pull0 = global_timer();
+    }
+    __syncthreads();
+    uint32_t* next = P.bm[(it + 1) & 1];
+    Stats st{0ull, 0u, 0u};
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long per = (unsigned long long)n / nw;
+    const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
+    for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
+        const unsigned long long idx = base + lane;
+        const uint2 pc = (lane < ppt && idx < n) ? __ldcg(Q.pieces + idx) : make_uint2(0u, 0u);
+        unsigned incl = pc.y;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        const unsigned excl = incl - pc.y;
+        for (unsigned e0 = 0; e0 < total; e0 += 32) {
+            const unsigned e = e0 + lane;
+            unsigned jx = 0;
+#pragma unroll
+            for (unsigned stp = 16; stp >= 1; stp >>= 1) {
+                const unsigned cj = jx + stp;
+                if (__shfl_sync(kFull, excl, cj) <= e) jx = cj;
+            }
+            const uint32_t j = __shfl_sync(kFull, pc.x, jx) + (e - __shfl_sync(kFull, excl, jx));
+            bool act = false;
+            uint32_t v = 0;
+            if (e < total) {
+                v = __ldg(Q.dst + j);
+                act = push_relax<APP>(P, Q, j, v, it, next);
+                if (act) count_active(P, v, st);
+            }
+            stage_list(act, v, &s_lcnt, s_list);
+        }
+    }
+    finish_block<true>(P, it, st, &s_F, &s_n, &s_row, &s_lcnt, s_list, reinterpret_cast<float*>(s_list));
 }
 
 // Initial frontier: size, fullness and edge-index work (the transformation
@@ -1876,7 +2021,7 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     WEDGE_TRY(configure_pulls(g));
     g->xform_blocks = g->num_sms * 4;
-    int nb = 0;
+    int nb = g->xform_blocks;  // the hybrid's push blocks write slots too
     for (int a = 0; a < 4; ++a) nb = std::max(nb, std::max(g->pull_blocks_app[a], g->pull_blocks_tma[a]));
     if (nb > kMaxPullBlocks) return set_error(WEDGE_ERR_NOT_SUPPORTED, "too many pull blocks for this device");
     WEDGE_TRY(dev_alloc(g, (void**)&g->bstat, (uint64_t)nb * sizeof(BlockStat)));
@@ -2003,7 +2148,7 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
 static wedge_status check_opts(const wedge_opts* o) {
     if (o->log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
     if (o->switch_mode > WEDGE_SWITCH_ALWAYS_SPARSE) return set_error(WEDGE_ERR_INVALID_ARG, "bad switch_mode");
-    if (o->reserved[0] || o->reserved[1]) return set_error(WEDGE_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o->reserved[0]) return set_error(WEDGE_ERR_INVALID_ARG, "reserved option fields must be zero");
     return WEDGE_OK;
 }
 
@@ -2019,7 +2164,10 @@ static wedge_status fill_stats(wedge_graph* g, cudaStream_t s, wedge_stats* stat
     stats->edges_pulled = 0;
     stats->chunks_listed = 0;
     for (uint32_t t = 0; t < iters; ++t) {
-        if (r[t].mode) {
+        if (r[t].mode && g->last_push) {
+            stats->sparse_iters++;
+            stats->edges_pulled += r[t].fullness;  // the out-edges pushed
+        } else if (r[t].mode) {
             stats->sparse_iters++;
             stats->chunks_listed += r[t].nchunks;
             const uint64_t e = (uint64_t)r[t].nchunks << (5 + r[t].k);
@@ -2037,17 +2185,15 @@ static wedge_status fill_stats(wedge_graph* g, cudaStream_t s, wedge_stats* stat
     return WEDGE_OK;
 }
 
-// Host-polled loop: traced runs, and graphs whose device loop could not be built.
-static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, const XformParams& X, uint32_t max_iters,
-                              cudaStream_t s) {
+// Host-polled loop: traced runs, synchronous runs, and graphs whose device
+// loop could not be built.  body(i) launches loop body i; after the run is
+// done the bodies' kernels return at once.
+template <class Body>
+static wedge_status host_loop(wedge_graph* g, Body body, uint32_t max_iters, cudaStream_t s) {
     const int batch = 8;
     uint32_t launched = 0;
     for (;;) {
-        for (int b = 0; b < batch; ++b) {
-            launch_pull_app(g, app, P, s);
-            launch_xform(g, X, s);
-        }
-        launched += batch;
+        for (int b = 0; b < batch; ++b) body(launched++);
         WEDGE_TRY_CUDA(cudaGetLastError());
         WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
         WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
@@ -2057,8 +2203,8 @@ static wedge_status host_loop(wedge_graph* g, int app, const PullParams& P, cons
 
 // Synchronous CC/SSSP (the opts' `synchronous`): pull t reads buffer t & 1
 // and writes buffer (t + 1) & 1, which first receives a copy of the values
-// (destinations outside a Wedge Frontier keep theirs).  Launch i of the loop
-// is pull i, or returns at once after the run is done.
+// (destinations outside a Wedge Frontier keep theirs).  Body i is pull i,
+// or returns at once after the run is done.
 __global__ void k_sync_copy(const RunCtl* C, const uint32_t* __restrict__ from, uint32_t* __restrict__ to,
                             uint32_t V) {
     if (C->done) return;
@@ -2066,26 +2212,82 @@ __global__ void k_sync_copy(const RunCtl* C, const uint32_t* __restrict__ from, 
         to[v] = from[v];
 }
 
-static wedge_status host_loop_sync(wedge_graph* g, int app, const PullParams& P, const XformParams& X,
-                                   uint32_t max_iters, cudaStream_t s) {
+static void launch_sync_body(wedge_graph* g, int app, const PullParams& P, const XformParams& X, uint32_t i,
+                             cudaStream_t s) {
     uint32_t* vb[2] = {g->vals, g->vals_sync};
-    const int batch = 8;
-    uint32_t launched = 0;
-    for (;;) {
-        for (int b = 0; b < batch; ++b, ++launched) {
-            k_sync_copy<<<g->num_sms * 4, 256, 0, s>>>(g->ctl, vb[launched & 1], vb[(launched + 1) & 1], g->V);
-            count_launch();
-            PullParams Q = P;
-            Q.vread = vb[launched & 1];
-            Q.vals = vb[(launched + 1) & 1];
-            launch_pull_app(g, app, Q, s);
-            launch_xform(g, X, s);
-        }
-        WEDGE_TRY_CUDA(cudaGetLastError());
-        WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
-        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
-        if (g->h_ctl->done || launched > max_iters + 2) return WEDGE_OK;
+    k_sync_copy<<<g->num_sms * 4, 256, 0, s>>>(g->ctl, vb[i & 1], vb[(i + 1) & 1], g->V);
+    count_launch();
+    PullParams Q = P;
+    Q.vread = vb[i & 1];
+    Q.vals = vb[(i + 1) & 1];
+    launch_pull_app(g, app, Q, s);
+    launch_xform(g, X, s);
+}
+
+// The push/pull hybrid's loop body: pieces of the frontier's out-edge rows
+// (X reads the CSR offsets), the push, the preparation of a dense iteration
+// the push may have chosen, the dense pull.
+static void launch_hybrid_body(const wedge_graph* g, int app, const PullParams& P, const XformParams& X,
+                               const PushParams& Q, cudaStream_t s) {
+    k_xform_scan<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+    switch (app) {
+        case kBFS: k_push_expand<kBFS><<<g->xform_blocks, kXformThreads, 0, s>>>(P, Q); break;
+        case kCC: k_push_expand<kCC><<<g->xform_blocks, kXformThreads, 0, s>>>(P, Q); break;
+        default: k_push_expand<kSSSP><<<g->xform_blocks, kXformThreads, 0, s>>>(P, Q); break;
     }
+    k_hybrid_prepare<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+    count_launch(3);
+    launch_pull_app(g, app, P, s);
+}
+
+static PushParams push_params(const wedge_graph* g) {
+    PushParams Q{};
+    Q.dst = g->csr_dst;
+    Q.src = g->csr_src;
+    Q.w = g->csr_w;
+    Q.kid_of = g->kid_of;
+    Q.pieces = g->push_pieces;
+    return Q;
+}
+
+static wedge_status build_hybrid_graph(wedge_graph* g, int app) {
+    cudaGraph_t graph = nullptr;
+    WEDGE_TRY_CUDA(cudaGraphCreate(&graph, 0));
+    struct Destroy {
+        cudaGraph_t g;
+        ~Destroy() {
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{graph};
+    cudaGraphConditionalHandle handle;
+    WEDGE_TRY_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    WEDGE_TRY_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = g->cap_stream;
+    WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    PullParams P = pull_params(g, 0, app);
+    P.cond = handle;
+    P.mlp = nullptr;
+    P.hybrid = 1;
+    XformParams X = xform_params(g, 0);
+    X.eidx_off = g->csr_off;
+    X.pieces = g->push_pieces;
+    launch_hybrid_body(g, app, P, X, push_params(g), cs);
+    cudaError_t le = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) return cuda_error(le, "hybrid loop body launch");
+    if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    WEDGE_TRY_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    g->loop_exec_push[app] = exec;
+    return WEDGE_OK;
 }
 
 static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uint32_t* out,
@@ -2109,8 +2311,20 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     init.E = g->E;
     const uint64_t wb_words = (g->NC + 31) / 32 + 1;
     const bool sync = o.synchronous && app != kBFS;
+    const bool push = o.sparse_push != 0;
+    if (push && o.synchronous) return set_error(WEDGE_ERR_INVALID_ARG, "sparse_push and synchronous exclude each other");
+    if (push && init.switch_mode == WEDGE_SWITCH_LEARNED) init.switch_mode = WEDGE_SWITCH_THRESHOLD;
     if (sync && !g->vals_sync) WEDGE_TRY(dev_alloc(g, (void**)&g->vals_sync, (uint64_t)g->V * 4));
-    if (!trace && !sync && !g->loop_exec[app] && !g->loop_failed) {
+    if (push) WEDGE_TRY(build_csr(g, s));
+    if (push && !trace && !g->loop_exec_push[app] && !g->loop_failed) {
+        if (build_hybrid_graph(g, app) != WEDGE_OK) {
+            g->loop_failed = true;
+            std::fprintf(stderr, "wedge: device loop graph unavailable (%s); using the host-polled loop\n",
+                         wedge_last_error());
+            cudaGetLastError();
+        }
+    }
+    if (!push && !trace && !sync && !g->loop_exec[app] && !g->loop_failed) {
         if (build_loop_graph(g, app) != WEDGE_OK) {
             g->loop_failed = true;  // this graph keeps the host-polled loop
             std::fprintf(stderr, "wedge: device loop graph unavailable (%s); using the host-polled loop\n",
@@ -2122,26 +2336,45 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb, wb_words, g->rec,
                                               g->ctl, init, g->flist[0], g->visk, visk_words(g));
     PullParams P = pull_params(g, trace, app);
+    if (push) {
+        P.mlp = nullptr;
+        P.hybrid = 1;
+    }
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, P.mlp,
                                                     P.gf);
     count_launch(2);
     XformParams X = xform_params(g, trace);
-    launch_xform(g, X, s);
-    WEDGE_TRY_CUDA(cudaGetLastError());
     const uint32_t* result = g->vals;
-    if (sync) {
-        WEDGE_TRY(host_loop_sync(g, app, P, X, max_iters, s));
-        if (g->h_ctl->it & 1) result = g->vals_sync;  // pull it - 1 wrote buffer it & 1
-    } else if (!trace && g->loop_exec[app]) {
-        WEDGE_TRY_CUDA(cudaGraphLaunch(g->loop_exec[app], s));
+    if (push) {
+        X.eidx_off = g->csr_off;
+        X.pieces = g->push_pieces;
+        const PushParams Q = push_params(g);
+        WEDGE_TRY_CUDA(cudaGetLastError());
+        if (!trace && g->loop_exec_push[app])
+            WEDGE_TRY_CUDA(cudaGraphLaunch(g->loop_exec_push[app], s));
+        else
+            WEDGE_TRY(host_loop(g, [&](uint32_t) { launch_hybrid_body(g, app, P, X, Q, s); }, max_iters, s));
     } else {
-        WEDGE_TRY(host_loop(g, app, P, X, max_iters, s));
+        launch_xform(g, X, s);
+        WEDGE_TRY_CUDA(cudaGetLastError());
+        if (sync) {
+            WEDGE_TRY(host_loop(g, [&](uint32_t i) { launch_sync_body(g, app, P, X, i, s); }, max_iters, s));
+            if (g->h_ctl->it & 1) result = g->vals_sync;  // pull it - 1 wrote buffer it & 1
+        } else if (!trace && g->loop_exec[app]) {
+            WEDGE_TRY_CUDA(cudaGraphLaunch(g->loop_exec[app], s));
+        } else {
+            WEDGE_TRY(host_loop(g, [&](uint32_t) {
+                launch_pull_app(g, app, P, s);
+                launch_xform(g, X, s);
+            }, max_iters, s));
+        }
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(out, result, (uint64_t)g->V * 4, cudaMemcpyDefault, s));
     g->last_trace = trace;
     g->last_stream = s;
+    g->last_push = push;
     return fill_stats(g, s, stats);
 }
 
@@ -2438,6 +2671,7 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
     g->last_stream = s;
     g->last_trace = false;
+    g->last_push = false;
     if (!stats) return WEDGE_OK;
     return fill_stats(g, s, stats);
 }

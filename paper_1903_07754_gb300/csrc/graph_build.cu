@@ -224,6 +224,40 @@ __global__ void k_validate(const uint32_t* __restrict__ off, const uint32_t* __r
     if (flag) atomicOr(bad, flag);
 }
 
+// Out-edges of the push/pull hybrid: every in-edge position p (destination
+// from the chunk's head mask and vid, as in the pull) is appended to its
+// source's CSR row; one atomic per distinct source and warp.
+__global__ void k_csr_fill(const uint32_t* __restrict__ src, const uint32_t* __restrict__ w, uint64_t E,
+                           uint64_t NC, const uint2* __restrict__ cmeta, const uint32_t* __restrict__ vid,
+                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ dst_out,
+                           uint32_t* __restrict__ src_out, uint32_t* __restrict__ w_out) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; c < NC; c += nw) {
+        const uint64_t p = c * 32 + lane;
+        const bool valid = p < E;
+        const uint32_t u = valid ? src[p] : 0xFFFFFFFFu;
+        const uint2 meta = cmeta[c];
+        const uint32_t kid = meta.y + __popc(meta.x & ((2u << lane) - 1u) & ~1u);
+        const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, u) & vm;
+        if (!valid) continue;
+        const unsigned leader = __ffs(same) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[u], (unsigned)__popc(same));
+        base = __shfl_sync(same, base, leader);
+        const uint32_t pos = base + __popc(same & ((1u << lane) - 1u));
+        dst_out[pos] = vid[kid];
+        src_out[pos] = u;
+        if (w_out) w_out[pos] = w[p];
+    }
+}
+
+__global__ void k_kid_of(const uint32_t* __restrict__ vid, uint32_t NZ, uint32_t* __restrict__ kid_of) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < NZ; i += (uint64_t)gridDim.x * blockDim.x)
+        kid_of[vid[i]] = (uint32_t)i;
+}
+
 static unsigned grid_for(uint64_t n, int threads, int sms) {
     uint64_t b = (n + threads - 1) / threads;
     uint64_t cap = (uint64_t)sms * 32;
@@ -260,6 +294,12 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->src_own);
     dev_free(g->w_own);
     dev_free(g->outdeg);
+    dev_free(g->csr_off);
+    dev_free(g->csr_dst);
+    dev_free(g->csr_src);
+    dev_free(g->csr_w);
+    dev_free(g->kid_of);
+    dev_free(g->push_pieces);
     dev_free(g->vid);
     dev_free(g->cmeta);
     if (g->eidx_off_owned) dev_free(g->eidx_off);
@@ -292,6 +332,8 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->ms_bar);
     if (g->ms_exec) cudaGraphExecDestroy(g->ms_exec);
     for (auto& e : g->loop_exec)
+        if (e) cudaGraphExecDestroy(e);
+    for (auto& e : g->loop_exec_push)
         if (e) cudaGraphExecDestroy(e);
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -452,6 +494,52 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     dev_free(d_total);
     if (e != cudaSuccess) return cuda_error(e, "edge index build");
     g->npieces_max = total;
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    return WEDGE_OK;
+}
+
+wedge_status build_csr(wedge_graph* g, cudaStream_t s) {
+    if (g->csr_off) return WEDGE_OK;
+    const uint32_t V = g->V;
+    const uint64_t E = g->E;
+    const int sms = g->num_sms;
+    uint32_t* cursor = nullptr;
+    WEDGE_TRY(dev_alloc(nullptr, (void**)&cursor, ((uint64_t)V + 1) * 4));
+    struct Free {
+        uint32_t* p;
+        ~Free() { dev_free(p); }
+    } free_cursor{cursor};
+    uint32_t* off = nullptr;
+    WEDGE_TRY(dev_alloc(g, (void**)&off, ((uint64_t)V + 1) * 4));
+    wedge_status st = exclusive_scan_u32(g->outdeg, off, V, nullptr, s);
+    if (st == WEDGE_OK) st = dev_alloc(g, (void**)&g->csr_dst, (E ? E : 1) * 4);
+    if (st == WEDGE_OK) st = dev_alloc(g, (void**)&g->csr_src, (E ? E : 1) * 4);
+    if (st == WEDGE_OK && g->w) st = dev_alloc(g, (void**)&g->csr_w, (E ? E : 1) * 4);
+    if (st == WEDGE_OK) st = dev_alloc(g, (void**)&g->kid_of, (uint64_t)V * 4);
+    unsigned long long* d_total = nullptr;
+    if (st == WEDGE_OK) st = dev_alloc(nullptr, (void**)&d_total, 8);
+    if (st != WEDGE_OK) {
+        dev_free(off);
+        return st;
+    }
+    g->csr_off = off;  // from here on freed with the graph
+    cudaError_t e = cudaMemcpyAsync(cursor, off, ((uint64_t)V + 1) * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_total, 0, 8, s);
+    if (e == cudaSuccess) {
+        if (g->NC)
+            k_csr_fill<<<grid_for(g->NC * 32, 256, sms), 256, 0, s>>>(g->src, g->w, E, g->NC, g->cmeta, g->vid, cursor,
+                                                                     g->csr_dst, g->csr_src, g->csr_w);
+        if (g->NZ) k_kid_of<<<grid_for(g->NZ, 256, sms), 256, 0, s>>>(g->vid, g->NZ, g->kid_of);
+        k_pieces_total<<<grid_for(V, 256, sms), 256, 0, s>>>(g->outdeg, V, d_total);
+        count_launch(3);
+        unsigned long long total = 0;
+        e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        g->npieces_push_max = total;
+    }
+    dev_free(d_total);
+    if (e != cudaSuccess) return cuda_error(e, "out-edge CSR build");
+    WEDGE_TRY(dev_alloc(g, (void**)&g->push_pieces, (g->npieces_push_max ? g->npieces_push_max : 1) * sizeof(uint2)));
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
 }

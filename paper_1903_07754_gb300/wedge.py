@@ -33,7 +33,7 @@ class wedge_opts(ctypes.Structure):
     _fields_ = [("tau_bp", ctypes.c_uint32), ("log2_coarsen", ctypes.c_uint32),
                 ("switch_mode", ctypes.c_uint32), ("max_iters", ctypes.c_uint32),
                 ("trace", ctypes.c_uint32), ("synchronous", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("sparse_push", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 class wedge_stats(ctypes.Structure):
