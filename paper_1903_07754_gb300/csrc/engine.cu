@@ -2105,10 +2105,12 @@ static void launch_xform(const wedge_graph* g, const XformParams& X, cudaStream_
     count_launch(2);
 }
 
-// Captures the loop body (pull, transformation, loop control) under a
-// conditional while node.  The body reads everything from the library-owned
-// buffers, so one instance serves every run of `app` on g.
-static wedge_status build_loop_graph(wedge_graph* g, int app) {
+// Captures a loop body under a conditional while node: body(cond, stream)
+// launches the body's kernels, whose deciding blocks set the condition.
+// The body reads everything from the library-owned buffers, so one instance
+// serves every run of an application on g.
+template <class Body>
+static wedge_status capture_while_graph(wedge_graph* g, Body body, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     WEDGE_TRY_CUDA(cudaGraphCreate(&graph, 0));
     struct Destroy {
@@ -2126,23 +2128,27 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
     cp.conditional.size = 1;
     cudaGraphNode_t node;
     WEDGE_TRY_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaStream_t cs = g->cap_stream;
-    WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    PullParams P = pull_params(g, 0, app);
-    P.cond = handle;
-    XformParams X = xform_params(g, 0);
-    launch_pull_app(g, app, P, cs);
-    launch_xform(g, X, cs);
+    WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal));
+    body(handle, cs);
     cudaError_t le = cudaGetLastError();
     cudaGraph_t captured = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &captured);
     if (le != cudaSuccess) return cuda_error(le, "loop body launch");
     if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
-    cudaGraphExec_t exec = nullptr;
-    WEDGE_TRY_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    g->loop_exec[app] = exec;
+    WEDGE_TRY_CUDA(cudaGraphInstantiate(out, graph, 0));
     return WEDGE_OK;
+}
+
+// Wedge's loop body: pull (with the decision), transformation.
+static wedge_status build_loop_graph(wedge_graph* g, int app) {
+    return capture_while_graph(g, [&](cudaGraphConditionalHandle cond, cudaStream_t cs) {
+        PullParams P = pull_params(g, 0, app);
+        P.cond = cond;
+        launch_pull_app(g, app, P, cs);
+        launch_xform(g, xform_params(g, 0), cs);
+    }, &g->loop_exec[app]);
 }
 
 static wedge_status check_opts(const wedge_opts* o) {
@@ -2251,43 +2257,16 @@ static PushParams push_params(const wedge_graph* g) {
 }
 
 static wedge_status build_hybrid_graph(wedge_graph* g, int app) {
-    cudaGraph_t graph = nullptr;
-    WEDGE_TRY_CUDA(cudaGraphCreate(&graph, 0));
-    struct Destroy {
-        cudaGraph_t g;
-        ~Destroy() {
-            if (g) cudaGraphDestroy(g);
-        }
-    } guard{graph};
-    cudaGraphConditionalHandle handle;
-    WEDGE_TRY_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    WEDGE_TRY_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaStream_t cs = g->cap_stream;
-    WEDGE_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    PullParams P = pull_params(g, 0, app);
-    P.cond = handle;
-    P.mlp = nullptr;
-    P.hybrid = 1;
-    XformParams X = xform_params(g, 0);
-    X.eidx_off = g->csr_off;
-    X.pieces = g->push_pieces;
-    launch_hybrid_body(g, app, P, X, push_params(g), cs);
-    cudaError_t le = cudaGetLastError();
-    cudaGraph_t captured = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(cs, &captured);
-    if (le != cudaSuccess) return cuda_error(le, "hybrid loop body launch");
-    if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
-    cudaGraphExec_t exec = nullptr;
-    WEDGE_TRY_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-    g->loop_exec_push[app] = exec;
-    return WEDGE_OK;
+    return capture_while_graph(g, [&](cudaGraphConditionalHandle cond, cudaStream_t cs) {
+        PullParams P = pull_params(g, 0, app);
+        P.cond = cond;
+        P.mlp = nullptr;
+        P.hybrid = 1;
+        XformParams X = xform_params(g, 0);
+        X.eidx_off = g->csr_off;
+        X.pieces = g->push_pieces;
+        launch_hybrid_body(g, app, P, X, push_params(g), cs);
+    }, &g->loop_exec_push[app]);
 }
 
 static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uint32_t* out,

@@ -61,3 +61,54 @@ def test_package_exports_c_names():
     for name in ("wedge_graph_create", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
                  "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr"):
         assert callable(getattr(pkg, name))
+
+
+_C_TYPES = {"uint32_t": ("u", 4), "uint64_t": ("u", 8), "int": ("i", 4), "double": ("f", 8), "float": ("f", 4)}
+
+
+def _header_structs():
+    """{name: [(field, kind, size, count)]} for every `typedef struct {...} name;`."""
+    text = "".join(open(h).read() for h in HEADERS)
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            fm = re.fullmatch(r"(\w+)\s+(\w+)(?:\[(\d+)\])?", decl)
+            assert fm, decl
+            kind, size = _C_TYPES[fm.group(1)]
+            fields.append((fm.group(2), kind, size, int(fm.group(3) or 1)))
+        out[m.group(2)] = fields
+    return out
+
+
+def _ctypes_fields(cls):
+    import ctypes
+    res = []
+    for name, t in cls._fields_:
+        count = 1
+        if issubclass(t, ctypes.Array):
+            count, t = t._length_, t._type_
+        kind = "f" if t in (ctypes.c_double, ctypes.c_float) else ("i" if t in (ctypes.c_int, ctypes.c_int32) else "u")
+        res.append((name, kind, ctypes.sizeof(t), count))
+    return res
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors have the header's fields, in order, with the same
+    widths (a drifted struct would shift every later option)."""
+    structs = _header_structs()
+    assert {"wedge_opts", "wedge_stats", "wedge_iter_record", "wedge_tuning", "wedge_graph_info"} <= set(structs)
+    for name, fields in structs.items():
+        cls = getattr(wedge, name)
+        assert _ctypes_fields(cls) == fields, name
+
+
+def test_default_opts_leave_the_extensions_off(lib):
+    for app in ("bfs", "cc", "sssp", "pr"):
+        o = wedge.wedge_default_opts(app)
+        assert (o.synchronous, o.sparse_push, o.trace, o.max_iters) == (0, 0, 0, 0)
+        assert list(o.reserved) == [0]
