@@ -791,18 +791,21 @@ def bench_grid(args, wedge, torch, dev, world):
 # that launch's ncu gpu__time_duration in us, and a digest of the kernel
 # sources they were measured on: reported only while those sources are
 # unchanged.
-TRAFFIC = {"pr": (321036800, 253.184, "e895fd5a9f7e6987"), "cc": (607268096, 507.968, "e895fd5a9f7e6987")}
+TRAFFIC = {"pr": (321036800, 253.184, "f2444b64bef16683"), "cc": (607268096, 507.968, "f2444b64bef16683")}
 
 
 def _kernel_digest():
     """Digest of the kernel sources' code: comments and whitespace are
-    dropped, so that only a change of code invalidates the counters."""
+    dropped, and so is engine.cu's host part (from its "Host side" banner
+    on), so that only a change of device code invalidates the counters."""
     import hashlib
     import re
     h = hashlib.sha256()
     for f in ("engine.cu", "common.cuh", "tma.cuh", "mlp.cuh"):
         with open(os.path.join(ROOT, "paper_1903_07754_gb300", "csrc", f)) as fh:
             src = fh.read()
+        if f == "engine.cu":
+            src = src[:src.index("\n// Host side\n")]
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
         h.update(re.sub(r"\s+", " ", src).strip().encode())
