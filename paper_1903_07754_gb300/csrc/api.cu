@@ -87,6 +87,12 @@ wedge_status dev_alloc(wedge_graph* g, void** p, size_t bytes) {
     return WEDGE_OK;
 }
 
+// Stream-ordered free of scratch whose last use was enqueued on s: no
+// device-wide wait, so work on other streams keeps running.
+void dev_free_async(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 void dev_free(void* p) {
     if (!p) return;
     int dev = 0;

@@ -228,6 +228,7 @@ wedge_status build_csr(wedge_graph* g, cudaStream_t s);
 // Allocation helper that records the bytes owned by g.
 wedge_status dev_alloc(wedge_graph* g, void** p, size_t bytes);
 void dev_free(void* p);
+void dev_free_async(void* p, cudaStream_t s);
 wedge_status trim_pools(int device);
 void* pinned_small_alloc(size_t bytes);  // at most 256 bytes; nullptr on failure
 void pinned_small_free(void* p);
@@ -240,7 +241,7 @@ wedge_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, u
                                 cudaStream_t s);
 
 // Engine (engine.cu)
-wedge_status ensure_run_scratch(wedge_graph* g);
+wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s);
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

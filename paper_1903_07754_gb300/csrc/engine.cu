@@ -1991,7 +1991,7 @@ static wedge_status configure_pulls(wedge_graph* g) {
 
 static uint64_t visk_words(const wedge_graph* g) { return ((uint64_t)g->NZ + 31) / 32 + 1; }
 
-wedge_status ensure_run_scratch(wedge_graph* g) {
+wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     if (g->ctl) return WEDGE_OK;
     const uint64_t V = g->V, NC = g->NC;
     const uint64_t words = (V + 31) / 32;
@@ -1999,7 +1999,7 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->bm[0], words * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->bm[1], words * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->wb, ((NC + 31) / 32 + 1) * 4));
-    WEDGE_TRY_CUDA(cudaMemset(g->wb, 0, ((NC + 31) / 32 + 1) * 4));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, ((NC + 31) / 32 + 1) * 4, s));
     WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
@@ -2008,7 +2008,7 @@ wedge_status ensure_run_scratch(wedge_graph* g) {
     g->rec_cap = kDefaultMaxIters + 2;
     WEDGE_TRY(dev_alloc(g, (void**)&g->rec, (uint64_t)g->rec_cap * sizeof(IterRec)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->ctl, sizeof(RunCtl)));
-    WEDGE_TRY_CUDA(cudaMemset(g->ctl, 0, sizeof(RunCtl)));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(RunCtl), s));
     static_assert(sizeof(RunCtl) <= 256, "control block mirror must fit a pinned block");
     g->h_ctl = static_cast<RunCtl*>(pinned_small_alloc(sizeof(RunCtl)));
     if (!g->h_ctl) return set_error(WEDGE_ERR_OUT_OF_MEMORY, "pinned host memory for the control block");

@@ -99,8 +99,8 @@ static wedge_status scan_rec(const uint32_t* in, uint32_t* out, uint64_t n, cuda
     }
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(s);
-    dev_free(sums);
-    dev_free(offs);
+    dev_free_async(sums, s);
+    dev_free_async(offs, s);
     if (e != cudaSuccess) return cuda_error(e, "scan launch");
     return st;
 }
@@ -357,7 +357,7 @@ static wedge_status validate(wedge_graph* g, cudaStream_t s) {
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    dev_free(d_bad);
+    dev_free_async(d_bad, s);
     if (e != cudaSuccess) return cuda_error(e, "validation");
     if (bad & 1u) return set_error(WEDGE_ERR_INVALID_ARG, "offsets must be non-decreasing");
     if (bad & 2u) return set_error(WEDGE_ERR_INVALID_ARG, "a source id is >= V");
@@ -374,8 +374,9 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     WEDGE_TRY(dev_alloc(nullptr, (void**)&tmp, ((uint64_t)V + 1) * 4));
     struct Free {
         uint32_t* p;
-        ~Free() { dev_free(p); }
-    } free_tmp{tmp};
+        cudaStream_t s;
+        ~Free() { dev_free_async(p, s); }
+    } free_tmp{tmp, s};
 
     WEDGE_TRY(validate(g, s));  // CSC only: no index yet
     WEDGE_TRY(dev_alloc(g, (void**)&g->outdeg, (uint64_t)V * 4));
@@ -390,12 +391,14 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     WEDGE_TRY(dev_alloc(nullptr, (void**)&knz, ((uint64_t)V + 1) * 4));
     struct Free2 {
         uint32_t* p;
-        ~Free2() { dev_free(p); }
-    } free_knz{knz};
+        cudaStream_t s;
+        ~Free2() { dev_free_async(p, s); }
+    } free_knz{knz, s};
     k_nz_flags<<<grid_for(V, 256, sms), 256, 0, s>>>(g->off, V, tmp);
     count_launch();
     WEDGE_TRY(exclusive_scan_u32(tmp, knz, V, nullptr, s));
-    WEDGE_TRY_CUDA(cudaMemcpy(&g->NZ, knz + V, 4, cudaMemcpyDeviceToHost));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(&g->NZ, knz + V, 4, cudaMemcpyDeviceToHost, s));
+    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
 
     WEDGE_TRY(dev_alloc(g, (void**)&g->vid, (uint64_t)(g->NZ ? g->NZ : 1) * 4));
     g->meta_len = (NC + kTileC - 1) / kTileC * kTileC + kTileC + kMetaPad;
@@ -417,10 +420,12 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         } else {
             g->eidx_off_owned = true;
             WEDGE_TRY(dev_alloc(g, (void**)&g->eidx_off, ((uint64_t)V + 1) * 4));
-            WEDGE_TRY_CUDA(cudaMemcpy(g->eidx_off, user_eoff, ((uint64_t)V + 1) * 4, cudaMemcpyHostToDevice));
+            WEDGE_TRY_CUDA(
+                cudaMemcpyAsync(g->eidx_off, user_eoff, ((uint64_t)V + 1) * 4, cudaMemcpyHostToDevice, s));
         }
         uint32_t len = 0;
-        WEDGE_TRY_CUDA(cudaMemcpy(&len, g->eidx_off + V, 4, cudaMemcpyDeviceToHost));
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(&len, g->eidx_off + V, 4, cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
         g->eidx_len = len;
         if (len > E) return set_error(WEDGE_ERR_INVALID_ARG, "edge index longer than E");
         if (len && !user_eidx) return set_error(WEDGE_ERR_INVALID_ARG, "eidx is NULL");
@@ -429,7 +434,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
                 g->eidx = const_cast<uint32_t*>(user_eidx);
             } else {
                 WEDGE_TRY(dev_alloc(g, (void**)&g->eidx, (uint64_t)len * 4));
-                WEDGE_TRY_CUDA(cudaMemcpy(g->eidx, user_eidx, (uint64_t)len * 4, cudaMemcpyHostToDevice));
+                WEDGE_TRY_CUDA(cudaMemcpyAsync(g->eidx, user_eidx, (uint64_t)len * 4, cudaMemcpyHostToDevice, s));
                 g->eidx_owned = true;
             }
         } else {
@@ -458,7 +463,8 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         }
         WEDGE_TRY(exclusive_scan_u32(tmp, g->eidx_off, V, nullptr, s));
         uint32_t len = 0;
-        WEDGE_TRY_CUDA(cudaMemcpy(&len, g->eidx_off + V, 4, cudaMemcpyDeviceToHost));
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(&len, g->eidx_off + V, 4, cudaMemcpyDeviceToHost, s));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
         g->eidx_len = len;
         WEDGE_TRY(dev_alloc(g, (void**)&g->eidx, (uint64_t)(len ? len : 1) * 4));
         // cursor = eidx_off; fill rows
@@ -479,7 +485,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
             e = cudaMemcpyAsync(&g->max_outdeg, d_max, 4, cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        dev_free(d_max);
+        dev_free_async(d_max, s);
         if (e != cudaSuccess) return cuda_error(e, "max out-degree");
     }
     // work pieces bound: sum ceil(|row| / 32)
@@ -491,7 +497,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     unsigned long long total = 0;
     cudaError_t e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    dev_free(d_total);
+    dev_free_async(d_total, s);
     if (e != cudaSuccess) return cuda_error(e, "edge index build");
     g->npieces_max = total;
     WEDGE_TRY_CUDA(cudaGetLastError());
@@ -507,8 +513,9 @@ wedge_status build_csr(wedge_graph* g, cudaStream_t s) {
     WEDGE_TRY(dev_alloc(nullptr, (void**)&cursor, ((uint64_t)V + 1) * 4));
     struct Free {
         uint32_t* p;
-        ~Free() { dev_free(p); }
-    } free_cursor{cursor};
+        cudaStream_t s;
+        ~Free() { dev_free_async(p, s); }
+    } free_cursor{cursor, s};
     uint32_t* off = nullptr;
     WEDGE_TRY(dev_alloc(g, (void**)&off, ((uint64_t)V + 1) * 4));
     wedge_status st = exclusive_scan_u32(g->outdeg, off, V, nullptr, s);
@@ -519,7 +526,7 @@ wedge_status build_csr(wedge_graph* g, cudaStream_t s) {
     unsigned long long* d_total = nullptr;
     if (st == WEDGE_OK) st = dev_alloc(nullptr, (void**)&d_total, 8);
     if (st != WEDGE_OK) {
-        dev_free(off);
+        dev_free_async(off, s);
         return st;
     }
     g->csr_off = off;  // from here on freed with the graph
@@ -537,7 +544,7 @@ wedge_status build_csr(wedge_graph* g, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         g->npieces_push_max = total;
     }
-    dev_free(d_total);
+    dev_free_async(d_total, s);
     if (e != cudaSuccess) return cuda_error(e, "out-edge CSR build");
     WEDGE_TRY(dev_alloc(g, (void**)&g->push_pieces, (g->npieces_push_max ? g->npieces_push_max : 1) * sizeof(uint2)));
     WEDGE_TRY_CUDA(cudaGetLastError());
@@ -590,7 +597,11 @@ wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offset
             st = set_error(WEDGE_ERR_INVALID_ARG, "offsets[0] must be 0 and offsets[V] must be E");
     }
     if (st == WEDGE_OK) st = build(g, d_eidx_off, d_eidx, s);
-    if (st == WEDGE_OK) st = ensure_run_scratch(g);
+    if (st == WEDGE_OK) st = ensure_run_scratch(g, s);
+    if (st == WEDGE_OK) {  // ready for runs on any stream
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(e, "graph creation");
+    }
     if (st != WEDGE_OK) {
         free_graph(g);
         return st;
