@@ -112,8 +112,9 @@ void wedge_default_opts(wedge_app app, wedge_opts* out);
 
 typedef struct {
     uint32_t iters;           /* pull iterations executed */
-    uint32_t sparse_iters;    /* of which pulled over a Wedge Frontier */
-    uint64_t edges_pulled;    /* CSC positions loaded by the pulls */
+    uint32_t sparse_iters;    /* of which pulled over a Wedge Frontier (hybrid: pushed) */
+    uint64_t edges_pulled;    /* CSC positions loaded by the pulls (hybrid: plus the
+                               * out-edges pushed, the fullness of pushed frontiers) */
     uint64_t chunks_listed;   /* Wedge Frontier entries over the run */
     double device_ms;         /* stream time of the run (CUDA events) */
 } wedge_stats;

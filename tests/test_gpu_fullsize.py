@@ -1,7 +1,8 @@
 """Parity at the full benchmark size (R-MAT scale 22, edge factor 16), in the
 launch configurations the benchmark times (the paper's settings and the
-precision/threshold pairs its autotuner picks): BFS, CC and SSSP bit-exact
-against the oracle over every vertex, PageRank within L1 1e-6."""
+precision/threshold pairs its autotuner picks, the push/pull hybrid it
+compares against): BFS, CC and SSSP bit-exact against the oracle over
+every vertex, PageRank within L1 1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -48,6 +49,28 @@ def test_bfs_sssp_pr_scale22(g22):
         G.close()
 
 
+def test_hybrid_and_synchronous_scale22(g22):
+    """The push/pull hybrid and synchronous SSSP at full size, bit-exact."""
+    G = graph(g22)
+    try:
+        out = empty_u32(g22.V)
+        lv, dist = oracle.bfs_push(g22, 0), oracle.sssp_dijkstra(g22, 0)
+        o = wedge.wedge_default_opts("bfs")
+        o.sparse_push, o.tau_bp = 1, 2000
+        wedge.wedge_run_bfs(G.handle, 0, out, o)
+        np.testing.assert_array_equal(u32(out)[: g22.V], lv)
+        o = wedge.wedge_default_opts("sssp")
+        o.sparse_push, o.tau_bp = 1, 2000
+        wedge.wedge_run_sssp(G.handle, 0, out, o)
+        np.testing.assert_array_equal(u32(out)[: g22.V], dist)
+        o = wedge.wedge_default_opts("sssp")
+        o.synchronous = 1
+        wedge.wedge_run_sssp(G.handle, 0, out, o)
+        np.testing.assert_array_equal(u32(out)[: g22.V], dist)
+    finally:
+        G.close()
+
+
 def test_cc_scale22(g22):
     s = gg.symmetrize(gg.Graph(g22.V, g22.offsets, g22.src))
     G = graph(s, with_weights=False)
@@ -57,5 +80,9 @@ def test_cc_scale22(g22):
         for st in SETTINGS:
             wedge.wedge_run_cc(G.handle, out, _opts("cc", st))
             np.testing.assert_array_equal(u32(out)[: s.V], want, err_msg=str(st))
+        o = _opts("cc", (0, 5000))
+        o.sparse_push = 1  # the push/pull hybrid
+        wedge.wedge_run_cc(G.handle, out, o)
+        np.testing.assert_array_equal(u32(out)[: s.V], want)
     finally:
         G.close()
