@@ -826,16 +826,40 @@ def _ncu_gbs(key):
     return val / (us * 1e-6) / 1e9 if val is not None and digest == _kernel_digest() else None
 
 
-def _gather_bound(torch, dev, edges, t, clocks):
+def _gather_bound(torch, dev, edges, t, clocks, probe_t=None):
     """Every edge costs one random gather, and each distinct 128-byte line a
     gather instruction touches is one L1 wavefront; the L1 data pipe retires
-    one wavefront per clock per SM (ncu: l1tex__data_pipe_lsu_wavefronts)."""
+    one wavefront per clock per SM (ncu: l1tex__data_pipe_lsu_wavefronts).
+    probe_t: the time of wedge_gather_probe over the same edges (the same
+    source stream and gathers without the reduction), a measured ceiling."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = sms * mhz * 1e6 / 1e9
     achieved = edges / t / 1e9
-    return {"unit": "G gathers/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-            "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x 1 L1 wavefront/clock"}
+    out = {"unit": "G gathers/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+           "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x 1 L1 wavefront/clock"}
+    if probe_t:
+        out.update({"measured_peak": edges / probe_t / 1e9, "frac_of_measured": probe_t / t,
+                    "measured_peak_basis": "wedge_gather_probe: the pull's 16-byte source stream and one 4-byte "
+                                           "gather per edge, no reduction, same launch shape"})
+    return out
+
+
+def _time_launch(torch, stream, fn, before=None, reps=10, warm=2):
+    """Mean device time (s) of fn() per CUDA-event pair on `stream`."""
+    times = []
+    for r in range(reps + warm):
+        if before:
+            before()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= warm:
+            times.append(e0.elapsed_time(e1))
+    return float(np.mean(times)) / 1e3
 
 
 def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
@@ -862,8 +886,10 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
     # other count takes every gather as one 32-byte sector
     alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 8 * V
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    tp = _time_launch(torch, stream, lambda: wedge.wedge_gather_probe(G.handle, contrib, sink))
     return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "pr", alg, alg_sectors, t, dev,
-                     _gather_bound(torch, dev, E, t, clocks))
+                     _gather_bound(torch, dev, E, t, clocks, tp))
 
 
 def _roofline(kernel, key, alg, alg_sectors, t, dev, gather):
@@ -908,8 +934,11 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     # changed labels written 4*changed, next-frontier bitmap V/8
     alg = 4 * (V + 1) + 4 * E + 4 * V + 4 * V + 4 * nchanged + V / 8
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 4 * V + 4 * nchanged + V / 8
+    fv = torch.rand(V, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    tp = _time_launch(torch, stream, lambda: wedge.wedge_gather_probe(S.handle, fv, sink))
     return _roofline("k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "cc", alg, alg_sectors, t, dev,
-                     _gather_bound(torch, dev, E, t, None))
+                     _gather_bound(torch, dev, E, t, None, tp))
 
 
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):

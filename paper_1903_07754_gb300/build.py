@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libwedge.so")
-SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -69,7 +69,7 @@ EXPORTS = [
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
-    "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
+    "wedge_pr_pull", "wedge_gather_probe", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_pr_pull": (st, [P, P, P, P]),
+        "wedge_gather_probe": (st, [P, P, P, P]),
         "wedge_trim_memory": (st, [i32]),
         "wedge_selftest_timeout": (st, [i32]),
         "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
@@ -251,6 +252,11 @@ def wedge_selftest_timeout(kind):
     """Runs a device wait that cannot be satisfied; returns the library
     status (WEDGE_ERR_TIMEOUT = 4 is the expected outcome)."""
     return int(load().wedge_selftest_timeout(int(kind)))
+
+
+def wedge_gather_probe(handle, vals, sink, stream=None):
+    """vals: V float32 device tensor; sink: 1 float32 device tensor."""
+    _check(load().wedge_gather_probe(handle, _ptr(vals), _ptr(sink), _stream(stream)))
 
 
 def wedge_pr_pull(handle, contrib, sums, stream=None):

@@ -401,3 +401,14 @@ def test_many_short_segments(switch):
         np.testing.assert_array_equal(got, oracle.cc_union_find(s))
     finally:
         S.close()
+
+
+def test_gather_probe_sums_the_gathered_values(rmat, rmat_dev):
+    """The diagnostic gathers vals[src] once per edge: with integer-valued
+    floats the sum is exact (sum over u of vals[u] * outdeg(u))."""
+    vals = torch.from_numpy((np.arange(rmat.V) % 3).astype(np.float32)).cuda()
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    wedge.wedge_gather_probe(rmat_dev.handle, vals, sink)
+    want = float((np.arange(rmat.V) % 3).astype(np.float64) @ oracle.outdeg(rmat).astype(np.float64))
+    assert want < 2 ** 24
+    assert float(sink.item()) == want

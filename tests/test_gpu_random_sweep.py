@@ -49,7 +49,7 @@ def _opts(app, rng):
     return o
 
 
-@pytest.mark.parametrize("seed", range(36))
+@pytest.mark.parametrize("seed", range(96))
 def test_random_graph_and_options(seed):
     g, rng = _case(seed)
     root = int(rng.integers(0, g.V))
