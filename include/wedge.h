@@ -94,8 +94,9 @@ typedef struct {
                             * BFS is level-synchronous either way. */
     uint32_t sparse_push;  /* nonzero: the push/pull hybrid instead of Wedge - a
                             * comparison engine, the analogue of the push-based and
-                            * hybrid systems the paper measures against (Sections 1,
-                            * 6): iterations the fullness test finds sparse push
+                            * hybrid systems the paper measures against (Section
+                            * 5.4; push vs. pull: Section 2.1): iterations the
+                            * fullness test finds sparse push
                             * over the frontier's out-edges (an out-edge CSR is
                             * built on the graph's first such run, about 8E + 8V
                             * bytes more), dense ones pull over all edges.
