@@ -3,8 +3,10 @@
 One step = BFS (root 0), CC (HCC on the symmetrised graph), SSSP (root 0,
 weights in [1,255]) and PageRank (20 iterations, d = 0.85) on R-MAT scale 22,
 edge factor 16 (a=0.57, b=c=0.19, seeded, self-loops and duplicates removed),
-uint32 CSC resident in HBM, through the C ABI with default options (fullness
-threshold 1% / 20%, 256 / 128 edges per Wedge bit).
+uint32 CSC resident in HBM, through the C ABI with the precision and
+fullness threshold the project's autotuner picks per application (the
+paper's settings, 1% / 20% and one 32-edge chunk per Wedge bit, are timed
+beside them).
 
 `value` is whole-job GTEPS over the step: traversed edges of every run
 (BFS, SSSP: sum of out-degrees of reached vertices; CC: |E_sym|; PR: 20*|E|)

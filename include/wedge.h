@@ -105,10 +105,11 @@ typedef struct {
     uint32_t reserved[1];  /* must be zero */
 } wedge_opts;
 
-/* Defaults from the paper's tuned settings (Section 5, "Experiments"):
- * BFS tau = 1% with 8 vectors per bit, CC/SSSP tau = 20% with 4 vectors per
- * bit.  Chunk-size equivalents used here: BFS k = 3 (256 edges), CC/SSSP
- * k = 2 (128 edges). */
+/* Defaults from the paper's tuned settings (Section 5.2, "Frontier Fullness
+ * Threshold" and "Frontier Precision"): BFS tau = 1% with 8 edge vectors per
+ * bit, CC/SSSP tau = 20% with 4 vectors per bit.  A vector holds up to 4
+ * edges of one destination (Section 2.2), so a bit covers up to 32 / 16
+ * edges; the finest entry here is one 32-edge chunk, k = 0, for both. */
 void wedge_default_opts(wedge_app app, wedge_opts* out);
 
 typedef struct {

@@ -182,10 +182,10 @@ void wedge_default_opts(wedge_app app, wedge_opts* out) {
     out->switch_mode = WEDGE_SWITCH_THRESHOLD;
     if (app == WEDGE_BFS) {
         out->tau_bp = 100;     // 1% of edges
-        out->log2_coarsen = 3; // 256 edges per Wedge bit
+        out->log2_coarsen = 0; // 8 edge vectors of <= 4 edges: one 32-edge chunk
     } else {
         out->tau_bp = 2000;    // 20%
-        out->log2_coarsen = 2; // 128 edges per Wedge bit
+        out->log2_coarsen = 0; // 4 vectors (<= 16 edges): the finest entry, one chunk
     }
     out->max_iters = 0;
     out->trace = 0;

@@ -51,9 +51,9 @@ def test_build_targets_sm_103a_only():
 def test_host_only_entry_points(lib):
     assert wedge.wedge_version().startswith("wedge-gb300")
     o = wedge.wedge_default_opts("bfs")
-    assert (o.tau_bp, o.log2_coarsen, o.switch_mode) == (100, 3, wedge.SWITCH_THRESHOLD)
+    assert (o.tau_bp, o.log2_coarsen, o.switch_mode) == (100, 0, wedge.SWITCH_THRESHOLD)
     o = wedge.wedge_default_opts("sssp")
-    assert (o.tau_bp, o.log2_coarsen) == (2000, 2)
+    assert (o.tau_bp, o.log2_coarsen) == (2000, 0)
     assert isinstance(wedge.wedge_kernel_launches(), int)
 
 
