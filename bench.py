@@ -129,16 +129,22 @@ HYBRID_TAUS = (100, 500, 2000, 5000)
 
 def tune_step(wedge, G, S, g):
     """Wedge Frontier precision and fullness threshold per application,
-    picked by the project's autotuner on the step's graphs, with BFS and
-    SSSP tuned from another root than the measured one (the paper's own
-    settings are timed in per_app as well)."""
+    picked by the project's autotuner on the step's graphs: the setting with
+    the least total time over three roots other than the measured one (CC
+    has no root).  The paper's own settings are timed in per_app as well."""
     import graphgen as gg
     from paper_1903_07754_gb300 import autotune
-    root = int(gg.roots(g, 1, seed=7)[0])
+    roots = [int(r) for r in gg.roots(g, 3, seed=7)]
     tuned = {}
     for app, H in (("bfs", G), ("cc", S), ("sssp", G)):
-        best, _ = autotune.tune(H.handle, app, g.V, root=root, grid=STEP_TUNE_GRID[app], reps=3)
-        tuned[app] = {"k": best["k"], "tau_bp": best["tau_bp"]}
+        totals = {}
+        for root in (roots[:1] if app == "cc" else roots):
+            _, table = autotune.tune(H.handle, app, g.V, root=root, grid=STEP_TUNE_GRID[app], reps=3)
+            for row in table:
+                key = (row["k"], row["tau_bp"])
+                totals[key] = totals.get(key, 0.0) + row["ms"]
+        k, tau = min(totals, key=totals.get)
+        tuned[app] = {"k": k, "tau_bp": tau}
     return tuned
 
 
@@ -445,9 +451,9 @@ def main():
         wedge.wedge_set_cost_model(S.handle, None)
     # the push/pull hybrid (the comparison engine: sparse iterations push
     # over the frontier's out-edges, dense ones pull), its threshold tuned
-    # from the tuning root like Wedge's settings, timed on the measured root
+    # on the tuning roots like Wedge's settings, timed on the measured root
     import graphgen as gg
-    troot = int(gg.roots(g, 1, seed=7)[0])
+    troots = [int(r) for r in gg.roots(g, 3, seed=7)]
 
     def run_app(name, o, root):
         if name == "bfs":
@@ -468,7 +474,7 @@ def main():
         t_best, tau_best = None, None
         for tau in HYBRID_TAUS:
             oh = hybrid_opts(name, tau)
-            t = time_fn(lambda: run_app(name, oh, troot), reps=3)
+            t = sum(time_fn(lambda: run_app(name, oh, r), reps=3) for r in (troots[:1] if name == "cc" else troots))
             if t_best is None or t < t_best:
                 t_best, tau_best = t, tau
         by_tau = {}
