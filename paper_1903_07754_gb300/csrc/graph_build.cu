@@ -98,8 +98,7 @@ static wedge_status scan_rec(const uint32_t* in, uint32_t* out, uint64_t n, cuda
         }
     }
     cudaError_t e = cudaGetLastError();
-    cudaStreamSynchronize(s);
-    dev_free_async(sums, s);
+    dev_free_async(sums, s);  // stream-ordered: after the kernels above
     dev_free_async(offs, s);
     if (e != cudaSuccess) return cuda_error(e, "scan launch");
     return st;
