@@ -1195,10 +1195,11 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
 // The push/pull hybrid (a comparison engine, not Wedge): iterations the
 // fullness test finds sparse push over the frontier's out-edges instead of
 // pulling over a Wedge Frontier; dense ones are the same pull.  The loop
-// body is k_xform_scan over the out-edge rows (it also clears the bitmap and
-// record the iteration fills), k_push_expand, k_pull: each kernel serves
-// only its own kind of iteration, and the deciding blocks of the push and of
-// the pull advance the iteration.
+// body is k_xform_scan over the out-edge rows (it also prepares the
+// iteration: clears the bitmap and record it fills), k_push_expand,
+// k_hybrid_prepare (a dense iteration the push chose), k_pull: each kernel
+// serves only its own kind of iteration, and the deciding blocks of the push
+// and of the pull advance the iteration.
 // ------------------------------------------------------------------------
 
 // A dense iteration that follows a push in the same loop body: its
