@@ -143,13 +143,15 @@ __global__ void k_chunk_meta(const uint32_t* __restrict__ off, uint32_t V, const
 
 // One warp per chunk: the sources that appear in the chunk, each counted once
 // (__match_any_sync groups equal sources; the lowest lane of a group keeps it).
-// The counting pass also adds each group's size to the source's out-degree
-// when outdeg is given (one atomic per distinct source and chunk instead of
-// one per edge).
-template <bool FILL>
+// COUNT: one 64-bit atomic per distinct source and chunk adds the row entry
+// (low word) and the group's size, the source's edges in the chunk (high
+// word: its out-degree once summed); row entries stay below NC < 2^32.
+// Otherwise the group's lane appends the chunk to the source's row at the
+// row's cursor.
+template <bool COUNT>
 __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64_t NC,
-                            uint32_t* __restrict__ counter, uint32_t* __restrict__ eidx,
-                            uint32_t* __restrict__ outdeg) {
+                            unsigned long long* __restrict__ counts, uint32_t* __restrict__ cursor,
+                            uint32_t* __restrict__ eidx) {
     const unsigned lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -161,13 +163,22 @@ __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64
         const uint32_t s = src[p];
         const unsigned same = __match_any_sync(vmask, s);
         if ((unsigned)(__ffs(same) - 1) != lane) continue;
-        if (FILL) {
-            const uint32_t pos = atomicAdd(&counter[s], 1u);
-            eidx[pos] = (uint32_t)c;
+        if (COUNT) {
+            atomicAdd(&counts[s], ((unsigned long long)__popc(same) << 32) | 1ull);
         } else {
-            atomicAdd(&counter[s], 1u);
-            if (outdeg) atomicAdd(&outdeg[s], (unsigned)__popc(same));
+            const uint32_t pos = atomicAdd(&cursor[s], 1u);
+            eidx[pos] = (uint32_t)c;
         }
+    }
+}
+
+// Row lengths (low words) and out-degrees (high words) of the count pass.
+__global__ void k_split_counts(const unsigned long long* __restrict__ counts, uint32_t V,
+                               uint32_t* __restrict__ rowlen, uint32_t* __restrict__ outdeg) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long c = counts[v];
+        rowlen[v] = (uint32_t)c;
+        outdeg[v] = (uint32_t)(c >> 32);
     }
 }
 
@@ -457,8 +468,17 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         WEDGE_TRY_CUDA(cudaMemsetAsync(tmp, 0, ((uint64_t)V + 1) * 4, s));
         const unsigned eg = grid_for(NC * 32, 256, sms);
         if (NC) {
-            k_eidx_pass<false><<<eg, 256, 0, s>>>(g->src, E, NC, tmp, nullptr, g->outdeg);
-            count_launch();
+            unsigned long long* counts = nullptr;
+            WEDGE_TRY(dev_alloc(nullptr, (void**)&counts, (uint64_t)V * 8));
+            cudaError_t e = cudaMemsetAsync(counts, 0, (uint64_t)V * 8, s);
+            if (e == cudaSuccess) {
+                k_eidx_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, counts, nullptr, nullptr);
+                k_split_counts<<<grid_for(V, 256, sms), 256, 0, s>>>(counts, V, tmp, g->outdeg);
+                count_launch(2);
+                e = cudaGetLastError();
+            }
+            dev_free_async(counts, s);
+            if (e != cudaSuccess) return cuda_error(e, "edge index count");
         }
         WEDGE_TRY(exclusive_scan_u32(tmp, g->eidx_off, V, nullptr, s));
         uint32_t len = 0;
@@ -469,7 +489,7 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         // cursor = eidx_off; fill rows
         WEDGE_TRY_CUDA(cudaMemcpyAsync(knz, g->eidx_off, ((uint64_t)V + 1) * 4, cudaMemcpyDeviceToDevice, s));
         if (NC) {
-            k_eidx_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, knz, g->eidx, nullptr);
+            k_eidx_pass<false><<<eg, 256, 0, s>>>(g->src, E, NC, nullptr, knz, g->eidx);
             count_launch();
         }
     }
