@@ -963,9 +963,10 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
     """Host buffers through the public API: pinned host CSC -> device, graph
     creation (edge index build), the four runs, results back to the host.
-    Two streams: the R-MAT graph's copies, creation and BFS/SSSP/PageRank
-    runs on one; the symmetrised graph's copies (queued behind the R-MAT
-    copies), creation and CC run on the other, overlapping the first."""
+    Three streams: the R-MAT graph's CSC copy, creation and BFS/SSSP/
+    PageRank runs on one; its weights' copy on another, beside the creation
+    (SSSP waits for it); the symmetrised graph's copies (queued behind the
+    weights), creation and CC on a third, overlapping the first."""
     host = {}
     for name, arr in (("off", g.offsets), ("src", g.src), ("w", g.w), ("soff", s.offsets), ("ssrc", s.src)):
         t = torch.from_numpy(np.ascontiguousarray(arr).view(np.int32)).pin_memory()
@@ -975,17 +976,25 @@ def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
     outs["pr"] = torch.empty(g.V, dtype=torch.float32).pin_memory()
     d2h = sum(t.numel() * 4 for t in outs.values())
     stream = torch.cuda.current_stream()
-    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    sa, sb, sw = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
     def one():
-        sa.wait_stream(stream)
-        sb.wait_stream(stream)
+        for st in (sa, sb, sw):
+            st.wait_stream(stream)
+        # the host link carries one copy at a time at full rate: the R-MAT
+        # CSC first, then its weights (creation does not read them), then
+        # the symmetrised CSC
         with torch.cuda.stream(sa):
-            dg = {n: host[n].to(dev, non_blocking=True) for n in ("off", "src", "w")}
-            copied = torch.cuda.Event()
-            copied.record(sa)
+            dg = {n: host[n].to(dev, non_blocking=True) for n in ("off", "src")}
+            csc_copied = torch.cuda.Event()
+            csc_copied.record(sa)
+        with torch.cuda.stream(sw):
+            sw.wait_event(csc_copied)
+            dg["w"] = host["w"].to(dev, non_blocking=True)
+            w_copied = torch.cuda.Event()
+            w_copied.record(sw)
         with torch.cuda.stream(sb):
-            sb.wait_event(copied)
+            sb.wait_event(w_copied)
             ds = {n: host[n].to(dev, non_blocking=True) for n in ("soff", "ssrc")}
         with torch.cuda.stream(sa):
             G = wedge.Graph(wedge.wedge_graph_create(g.V, g.E, dg["off"], dg["src"], dg["w"]), keep=list(dg.values()))
@@ -993,6 +1002,7 @@ def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
             dst = torch.empty_like(lvl)
             pr = torch.empty(g.V, dtype=torch.float32, device=dev)
             wedge.wedge_run_bfs(G.handle, 0, lvl, opts[0], False)
+            sa.wait_event(w_copied)  # SSSP reads the weights
             wedge.wedge_run_sssp(G.handle, 0, dst, opts[2], False)
             wedge.wedge_run_pr(G.handle, pr, PR_ITERS, DAMPING, None, False)
             outs["lvl"].copy_(lvl, non_blocking=True)
@@ -1003,8 +1013,8 @@ def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
             lab = torch.empty(s.V, dtype=torch.int32, device=dev)
             wedge.wedge_run_cc(S.handle, lab, opts[1], False)
             outs["lab"].copy_(lab, non_blocking=True)
-        stream.wait_stream(sa)
-        stream.wait_stream(sb)
+        for st in (sa, sb, sw):
+            stream.wait_stream(st)
         torch.cuda.synchronize()
         G.close()
         S.close()
@@ -1022,7 +1032,8 @@ def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):
     return {"value": sum(edges.values()) / (ms / 1e3) / 1e9, "unit": "GTEPS", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "includes": "H2D of both CSCs, two wedge_graph_create (edge index build), 4 runs, D2H of results; "
-                        "the symmetrised graph's copies, creation and CC on a second stream"}
+                        "the weights' copy beside the R-MAT graph's creation, the symmetrised graph's copies, "
+                        "creation and CC on other streams"}
 
 
 def cpu_baseline(g, s, od):

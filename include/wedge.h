@@ -145,6 +145,9 @@ typedef struct {
  *  A caller's index is checked for non-decreasing offsets and entries
  *  < NC; rows that list the wrong chunks give wrong results, not faults.
  *  chunk_edges must be 32.
+ *  The weights are not read here: device weights only have to be in place
+ *  (stream-ordered) before the first SSSP run and the first run with
+ *  `sparse_push`, so their upload may overlap the graph's construction.
  *  Synchronises `stream` before returning.  Errors: INVALID_ARG (sizes,
  *  NULL arrays, unaligned device src/w, chunk_edges != 32), OUT_OF_MEMORY,
  *  CUDA. */
