@@ -4,7 +4,7 @@
  * Wedge (Grossman & Kozyrakis, "A New Frontier for Pull-Based Graph
  * Processing", arXiv 1903.07754) is a pull-only graph engine.  Each
  * iteration pulls values along in-edges and produces the traditional
- * source-oriented vertex frontier (Section 3.2, Requirement 1).  When that
+ * source-oriented vertex frontier (Section 3.1, Requirement 1).  When that
  * frontier is sparse enough (the fullness threshold, Section 3.4) it is
  * transformed into the Wedge Frontier: the set of edge groups ("chunks") of
  * the destination-sorted in-edge array that hold an edge from an active
@@ -98,8 +98,9 @@ typedef struct {
                             * 5.4; push vs. pull: Section 2.1): iterations the
                             * fullness test finds sparse push
                             * over the frontier's out-edges (an out-edge CSR is
-                            * built on the graph's first such run, about 8E + 8V
-                            * bytes more), dense ones pull over all edges.
+                            * built on the graph's first such run: about 8E + 16V
+                            * bytes more, 12E + 16V with weights), dense ones
+                            * pull over all edges.
                             * log2_coarsen is ignored; LEARNED acts as THRESHOLD;
                             * not with `synchronous`. */
     uint32_t reserved[1];  /* must be zero */

@@ -91,7 +91,7 @@ def test_edge_index_rows_are_sorted_unique_and_complete():
 @pytest.mark.parametrize("app", ["bfs", "cc", "sssp"])
 def test_wedge_runs_reach_the_plain_result(app):
     """The Wedge Frontier carries the same information as the vertex frontier
-    (Section 3.2) and coarser groups never break correctness (Section 3.4):
+    (Section 3.3) and coarser groups never break correctness (Section 3.4):
     every policy and precision reaches the definition's result."""
     base = gg.rmat(11, 16)
     if app == "cc":
