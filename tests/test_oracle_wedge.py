@@ -134,3 +134,54 @@ def test_bfs_trace_follows_levels():
         assert trace[t, 2] == int(trace[t, 1] * 10000 < tau * g.E)
         if trace[t, 2]:
             assert trace[t, 3] == oracle.wedge_groups_scan(g, members, 64).size
+
+
+def _jacobi_frontiers(app, g, root):
+    """Synchronous iteration written with NumPy, independently of the oracle:
+    x_{t+1}[v] = min(x_t[v], min over in-edges (u, v) with u in F_t of
+    x_t[u] (+ w)), F_{t+1} = {v : x_{t+1}[v] < x_t[v]}; returns the frontiers.
+    Sources outside F_t offer nothing new (their value was offered before)."""
+    V = g.V
+    dst = g.dst().astype(np.int64)
+    src = g.src.astype(np.int64)
+    inf = np.iinfo(np.int64).max
+    if app == "cc":
+        x = np.arange(V, dtype=np.int64)
+        front = np.ones(V, dtype=bool)
+    else:
+        x = np.full(V, inf, dtype=np.int64)
+        x[root] = 0
+        front = np.zeros(V, dtype=bool)
+        front[root] = True
+    w = g.w.astype(np.int64) if app == "sssp" else np.zeros(src.size, dtype=np.int64)
+    fronts = []
+    while front.any():
+        fronts.append(front.copy())
+        act = front[src]
+        cand = np.full(V, inf, dtype=np.int64)
+        vals = np.minimum(x[src[act]] + w[act], 0xFFFFFFFE) if app == "sssp" else x[src[act]]
+        np.minimum.at(cand, dst[act], vals)
+        nx = np.minimum(x, cand)
+        front = nx < x
+        x = nx
+    return fronts
+
+
+@pytest.mark.parametrize("app", ["cc", "sssp"])
+def test_synchronous_cc_sssp_traces_follow_jacobi(app):
+    """The oracle's Wedge run is synchronous for CC and SSSP: its frontier
+    sizes, fullness and decisions per iteration equal those of the plain
+    Jacobi iteration (the reference the GPU's synchronous mode is held to)."""
+    base = gg.rmat(11, 16)
+    g = gg.symmetrize(base) if app == "cc" else base.with_weights(255)
+    od = oracle.outdeg(g)
+    tau = 2000
+    fronts = _jacobi_frontiers(app, g, 0)
+    _, trace = oracle.wedge_run(app, g, 0, oracle.POLICY_THRESHOLD, tau, 32)
+    assert trace.shape[0] == len(fronts)
+    for t, f in enumerate(fronts):
+        assert trace[t, 0] == f.sum()
+        assert trace[t, 1] == od[f].sum()
+        assert trace[t, 2] == int(trace[t, 1] * 10000 < tau * g.E)
+        if trace[t, 2]:
+            assert trace[t, 3] == oracle.wedge_groups_scan(g, f, 32).size
