@@ -1,0 +1,82 @@
+"""Host-side arithmetic of bench.py (no GPU): credited edges, the
+gather-rate bound, the measured-peak file, and the digest that ties the
+committed ncu counters to the device code they were taken on."""
+import os
+import shutil
+import types
+
+import numpy as np
+
+import bench
+import graphgen as gg
+import oracle
+
+
+def test_credited_edges_is_the_out_degree_sum_of_reached_vertices():
+    g = gg.rmat(10, 8)
+    lvl = oracle.bfs_push(g, 0)
+    reached = lvl != oracle.INF
+    od = oracle.outdeg(g)
+    # Graph500 style: every edge leaving a reached vertex, counted once
+    want = int(g.src.size) - int(od[~reached].sum())
+    assert bench.credited_edges(od, reached) == want
+    assert bench.credited_edges(od, np.zeros(g.V, dtype=bool)) == 0
+
+
+def test_gather_bound_arithmetic(monkeypatch):
+    props = types.SimpleNamespace(multi_processor_count=152)
+    import torch
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: props)
+    edges, t, probe_t = 65_000_000, 0.25e-3, 0.2e-3
+    b = bench._gather_bound(torch, 0, edges, t, {"sm_mhz": 2000.0}, probe_t)
+    assert abs(b["peak"] - 152 * 2.0) < 1e-9
+    assert abs(b["achieved"] - edges / t / 1e9) < 1e-9
+    assert abs(b["frac"] - b["achieved"] / b["peak"]) < 1e-12
+    assert abs(b["measured_peak"] - edges / probe_t / 1e9) < 1e-9
+    assert abs(b["frac_of_measured"] - probe_t / t) < 1e-12
+    assert "measured_peak" not in bench._gather_bound(torch, 0, edges, t, None)
+
+
+def test_measured_peaks_are_used_when_present():
+    peak, kind = bench.peaks()
+    if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured" and peak > 1000
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
+
+
+def _digest_of(tmp_path, monkeypatch, edit=None):
+    csrc = tmp_path / "paper_1903_07754_gb300" / "csrc"
+    if not csrc.exists():
+        shutil.copytree(os.path.join(bench.ROOT, "paper_1903_07754_gb300", "csrc"), csrc)
+    if edit:
+        name, old, new = edit
+        p = csrc / name
+        text = p.read_text()
+        assert old in text
+        p.write_text(text.replace(old, new, 1))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return bench._kernel_digest()
+
+
+def test_digest_follows_device_code_only(tmp_path, monkeypatch):
+    base = _digest_of(tmp_path, monkeypatch)
+    # comments and the host part do not count
+    assert _digest_of(tmp_path, monkeypatch, ("engine.cu", "\n// Host side\n", "\n// Host side\n// a note\n")) == base
+    host = open(os.path.join(bench.ROOT, "paper_1903_07754_gb300", "csrc", "engine.cu")).read()
+    tail = host[host.index("\n// Host side\n"):]
+    assert "static PullParams pull_params(" in tail
+    assert _digest_of(tmp_path, monkeypatch,
+                      ("engine.cu", "static PullParams pull_params(", "static PullParams  pull_params(")) == base
+    assert _digest_of(tmp_path, monkeypatch, ("common.cuh", "struct wedge_graph {",
+                                              "struct wedge_graph {\n    int unused_host_field = 0;")) == base
+    # device code does
+    assert _digest_of(tmp_path, monkeypatch, ("engine.cu", "constexpr unsigned kFull = 0xFFFFFFFFu;",
+                                              "constexpr unsigned kFull = 0xFFFFFFFFu + 0u;")) != base
+
+
+def test_committed_ncu_counters_belong_to_the_current_device_code():
+    """TRAFFIC's digest is the current one, so bench.py reports the counters
+    (a change of device code must come with a new capture)."""
+    for key in bench.TRAFFIC:
+        assert bench._traffic(key) is not None, key
