@@ -137,14 +137,8 @@ def tune_step(wedge, G, S, g):
     roots = [int(r) for r in gg.roots(g, 3, seed=7)]
     tuned = {}
     for app, H in (("bfs", G), ("cc", S), ("sssp", G)):
-        totals = {}
-        for root in (roots[:1] if app == "cc" else roots):
-            _, table = autotune.tune(H.handle, app, g.V, root=root, grid=STEP_TUNE_GRID[app], reps=3)
-            for row in table:
-                key = (row["k"], row["tau_bp"])
-                totals[key] = totals.get(key, 0.0) + row["ms"]
-        k, tau = min(totals, key=totals.get)
-        tuned[app] = {"k": k, "tau_bp": tau}
+        best, _ = autotune.tune(H.handle, app, g.V, root=roots, grid=STEP_TUNE_GRID[app], reps=3)
+        tuned[app] = {"k": best["k"], "tau_bp": best["tau_bp"]}
     return tuned
 
 

@@ -18,9 +18,9 @@ import os
 from . import wedge
 
 DEFAULT_GRID = {
-    "bfs": {"k": (1, 2, 3, 4), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "cc": {"k": (1, 2, 3), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
-    "sssp": {"k": (1, 2, 3), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
+    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
+    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
     "bfs_batch": {"k": (0, 1, 2, 3, 4), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,),
                   "blocks_per_sm": (0,)},
 }
@@ -41,11 +41,15 @@ def _time(fn, reps):
 
 def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
     """Times every setting of `grid` for `app` ('bfs', 'cc', 'sssp' or
-    'bfs_batch') on graph `handle`; returns (best setting, table)."""
+    'bfs_batch') on graph `handle`; returns (best setting, table).  `root`
+    may be a list: BFS and SSSP settings are then ranked by their total time
+    over those roots (a single root can favour a setting that suits only
+    it); CC has no root; `roots` are the batched queries' roots."""
     import torch
     grid = dict(DEFAULT_GRID[app], **(grid or {}))
     out = torch.empty(V * (nqueries if app == "bfs_batch" else 1), dtype=torch.int32, device="cuda")
     base_app = "bfs" if app == "bfs_batch" else app
+    tune_roots = [int(r) for r in root] if hasattr(root, "__len__") else [int(root)]
     before = wedge.wedge_graph_get_tuning(handle)
     table = []
     try:
@@ -55,15 +59,15 @@ def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
             o = wedge.wedge_default_opts(base_app)
             o.log2_coarsen, o.tau_bp = k, tau
             if app == "bfs":
-                fn = lambda: wedge.wedge_run_bfs(handle, root, out, o, False)  # noqa: E731
+                fns = [lambda r=r: wedge.wedge_run_bfs(handle, r, out, o, False) for r in tune_roots]
             elif app == "cc":
-                fn = lambda: wedge.wedge_run_cc(handle, out, o, False)  # noqa: E731
+                fns = [lambda: wedge.wedge_run_cc(handle, out, o, False)]
             elif app == "sssp":
-                fn = lambda: wedge.wedge_run_sssp(handle, root, out, o, False)  # noqa: E731
+                fns = [lambda r=r: wedge.wedge_run_sssp(handle, r, out, o, False) for r in tune_roots]
             else:
-                fn = lambda: wedge.wedge_run_bfs_batch(handle, roots, None, nqueries, out, o, False)  # noqa: E731
+                fns = [lambda: wedge.wedge_run_bfs_batch(handle, roots, None, nqueries, out, o, False)]
             table.append({"k": k, "tau_bp": tau, "dense_loader": loader, "blocks_per_sm": bps,
-                          "ms": _time(fn, reps)})
+                          "ms": sum(_time(fn, reps) for fn in fns)})
     finally:
         wedge.wedge_graph_set_tuning(handle, before["dense_loader"], before["blocks_per_sm"])
     best = min(table, key=lambda r: r["ms"])

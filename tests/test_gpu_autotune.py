@@ -26,6 +26,10 @@ def test_settings_are_bit_exact_and_best_is_fastest():
             wedge.wedge_graph_set_tuning(G.handle, r["dense_loader"], r["blocks_per_sm"])
             wedge.wedge_run_bfs(G.handle, 0, out, autotune.opts_for("bfs", r))
             np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), want)
+        # several roots: settings ranked by their total time over the roots
+        mbest, mtable = autotune.tune(G.handle, "bfs", g.V, [0, 7, 123], grid={"k": (0, 2), "tau_bp": (100,)},
+                                      reps=1)
+        assert len(mtable) == 2 and mbest["ms"] == min(r["ms"] for r in mtable)
         roots = gg.roots(g, 16, seed=8)
         bbest, btable = autotune.tune(G.handle, "bfs_batch", g.V, roots=roots, nqueries=16,
                                       grid={"k": (0, 3), "tau_bp": (100, 5000), "blocks_per_sm": (0, 1)}, reps=1)
