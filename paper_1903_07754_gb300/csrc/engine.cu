@@ -4,9 +4,11 @@
 //   its last block (Sections 3.2, 3.4, Fig. 5), the frontier transformation
 //   (Sections 3.3, 4), PageRank, the run drivers for BFS, CC, SSSP and
 //   PageRank (Section 5), and -- beyond the paper -- the learned switch's
-//   in-loop inference, batched BFS/SSSP in one persistent launch and a
+//   in-loop inference, batched BFS/SSSP in one persistent launch, the
+//   push/pull hybrid the paper compares against, synchronous CC/SSSP and a
 //   self-test of the bounded waits.  The iteration loop runs on the device
-//   inside a CUDA graph with a conditional while node.
+//   inside a CUDA graph with a conditional while node (traced and
+//   synchronous runs drive it from the host).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
