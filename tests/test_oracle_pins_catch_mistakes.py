@@ -123,3 +123,34 @@ def test_pagerank_pins_reject_planted_mistakes():
     assert not pr_ok(g, _pr_numpy(g, dangling=False))
     assert not pr_ok(g, _pr_numpy(g, teleport_over_v=False))
     assert not pr_ok(g, _pr_numpy(g, divide=False))
+
+
+def test_wedge_frontier_fixture_rejects_planted_mistakes():
+    """The worked example's Wedge Frontiers (one and two edges per group)
+    single out the definition: groups of the active sources' out-edges.
+    Destination-oriented groups, an off-by-one group index or the sources'
+    in-edges all miss them."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _golden import edges, read
+    ex = read("paper_example_fig4.txt")
+    s, d = edges(ex["edges"])
+    g = gg.from_edges(int(ex["V"][0]), s, d)
+    front = [int(x) for x in ex["frontier"]]
+    src, dst = g.src.astype(np.int64), g.dst().astype(np.int64)
+    pos = np.arange(g.E)
+
+    def groups(active, size, shift=0):
+        return sorted(set(((pos[active] + shift) // size).tolist()))
+
+    for size, key in ((1, "wedge_group1"), (2, "wedge_group2")):
+        want = [int(x) for x in ex[key]]
+        assert groups(np.isin(src, front), size) == want                   # the definition
+        assert groups(np.isin(dst, front), size) != want                   # destination-oriented
+        assert groups(np.isin(src, front), size, shift=1) != want          # off by one position
+        assert oracle.wedge_groups_scan(g, front, size).tolist() == want
+    active_dst = sorted(set(dst[np.isin(src, front)].tolist()))
+    assert active_dst == [int(x) for x in ex["active_destinations"]]
+    # in-edges of the frontier instead of its out-edges
+    assert sorted(set(src[np.isin(dst, front)].tolist())) != active_dst
