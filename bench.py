@@ -245,7 +245,7 @@ def main():
     ap.add_argument("--ref-pr-iters", type=int, default=PR_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced"],
+    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced", "xform"],
                     help="run only one small case for a profiler (no JSON line)")
     ap.add_argument("--config", default="s22", choices=["s22", "learned-s24", "batch-s26", "grid", "studies"],
                     help="s22: the benchmark line (R-MAT s22, four apps); the others print one line each "
@@ -315,6 +315,8 @@ def main():
                 one()
             torch.cuda.synchronize()
             torch.cuda.cudart().cudaProfilerStop()
+        elif args.profile_case == "xform":
+            print(json.dumps(transform_case(wedge, torch, G, g, od, stream, dev)))
         elif args.profile_case == "pr":
             r = torch.empty(g.V, dtype=torch.float32, device=dev)
             for _ in range(2):
@@ -915,6 +917,33 @@ def _roofline(kernel, key, alg, alg_sectors, t, dev, gather):
             "gathers_counted": f"once per vertex (V*4 <= L2 = {l2 >> 20} MB)",
             "alg_bytes_gather_sectors": alg_sectors, "achieved_gather_sectors": alg_sectors / t / 1e9,
             "ncu_dram_gbs": _ncu_gbs(key), "gather_bound": gather}
+
+
+def transform_case(wedge, torch, G, g, od, stream, dev, frac=0.10, seed=5):
+    """One frontier transformation (wedge_frontier_transform, k = 0) of a
+    seeded random frontier holding `frac` of the vertices: its time and its
+    algorithmic bytes -- the frontier bitmap V/8, two row offsets per active
+    vertex, the rows' entries, the Wedge bitmap NC/8 and the list."""
+    rng = np.random.default_rng(seed)
+    mask = rng.random(g.V) < frac
+    packed = np.packbits(mask, bitorder="little")
+    packed = np.concatenate([packed, np.zeros((-packed.size) % 4, dtype=np.uint8)])
+    bm = torch.from_numpy(packed.view(np.int32).copy()).to(dev)
+    nc = (g.E + 31) // 32
+    clist = torch.empty(nc, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    t = _time_launch(torch, stream, lambda: wedge.wedge_frontier_transform(G.handle, bm, 0, clist, cnt), reps=10)
+    eo = np.empty(g.V + 1, dtype=np.uint32)
+    d_eo = torch.empty(g.V + 1, dtype=torch.int32, device=dev)
+    info = wedge.wedge_graph_get_info(G.handle)
+    d_ei = torch.empty(max(info["eidx_len"], 1), dtype=torch.int32, device=dev)
+    wedge.wedge_graph_copy_edge_index(G.handle, d_eo, d_ei)
+    eo[:] = d_eo.cpu().numpy().view(np.uint32)
+    rows = int((eo[1:].astype(np.int64) - eo[:-1])[mask].sum())
+    entries = int(cnt.item())
+    alg = g.V / 8 + 8 * int(mask.sum()) + 4 * rows + nc / 8 + 4 * entries
+    return {"frontier": int(mask.sum()), "row_entries": rows, "list_entries": entries, "ms": t * 1e3,
+            "alg_bytes": alg, "alg_gbs": alg / t / 1e9, "entries_per_s": rows / t}
 
 
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
