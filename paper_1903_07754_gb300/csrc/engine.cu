@@ -1057,9 +1057,26 @@ __device__ __forceinline__ void clear_frontier(uint32_t* bm, unsigned long long 
 // A warp task is up to 32 pieces, fewer when there are too few pieces to
 // give every warp a task (one hub's row): a task's entries are walked 32 at
 // a time, so its length is the latency that matters.
+// Fresh list entries staged by a warp are appended with one reservation on
+// the list's counter per kAppendStage entries (appending every round put up
+// to one atomic per 32 entries on that single address).
+constexpr unsigned kAppendStage = 256;
+
+__device__ __forceinline__ void flush_staged(uint32_t* list, unsigned* count, const uint32_t* stage, unsigned n) {
+    const unsigned lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(count, n);
+    base = __shfl_sync(kFull, base, 0);
+    for (unsigned i = lane; i < n; i += 32) list[base + i] = stage[i];
+    __syncwarp();
+}
+
 __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
-                                                    unsigned* count, unsigned long long gw, unsigned long long nw) {
+                                                    unsigned* count, unsigned long long gw, unsigned long long nw,
+                                                    uint32_t* stage = nullptr) {
+    unsigned staged = 0;  // warp-uniform
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned long long per = (unsigned long long)n / nw;
@@ -1114,7 +1131,15 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
             const unsigned same = __match_any_sync(kFull, b) & run;
             const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
             const unsigned m = __ballot_sync(kFull, fresh);
-            if (m) {
+            if (m && stage) {
+                const unsigned nm = __popc(m);
+                if (staged + nm > kAppendStage) {
+                    flush_staged(list, count, stage, staged);
+                    staged = 0;
+                }
+                if (fresh) stage[staged + __popc(m & lt_mask)] = b;
+                staged += nm;
+            } else if (m) {
                 const unsigned leader = __ffs(m) - 1;
                 unsigned slot = 0;
                 if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
@@ -1123,6 +1148,7 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
             }
         }
     }
+    if (stage && staged) flush_staged(list, count, stage, staged);
 }
 
 // Before iteration `it` fills the next frontier: the bitmap it fills held
@@ -1184,9 +1210,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
         k = r->k;
         count = &X.rec[it].nchunks;
     }
+    __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw);
+    xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
