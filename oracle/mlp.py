@@ -4,8 +4,11 @@ The model is a plain two-hidden-layer perceptron, 12 -> 64 (ReLU) -> 64
 (ReLU) -> 1, trained on the mean squared error.  Parameters are one flat
 array laid out W1[64][12] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3.
 This module is the definition written out in NumPy (forward, the analytic
-gradient, and a BF16-rounding forward for the inference path); the tests pin
-the gradient against central finite differences of the forward.
+gradient, a BF16-rounding forward for the inference path, and one Adam
+update); the tests pin the gradient against central finite differences of
+the forward, the BF16 forward against a hand-set network whose rounded and
+unrounded outputs differ by a hand-derived amount, and the Adam update
+against the closed forms of its moving averages.
 """
 import numpy as np
 
@@ -75,3 +78,23 @@ def forward_bf16(p, X):
     h1 = bf16(np.maximum(x @ w1.T + b1, 0.0)).astype(np.float64)
     h2 = bf16(np.maximum(h1 @ w2.T + b2, 0.0)).astype(np.float64)
     return h2 @ w3 + b3
+
+
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def adam_step(p, g, m, v, t, lr, b1=ADAM_B1, b2=ADAM_B2, eps=ADAM_EPS):
+    """One Adam update (Kingma & Ba, "Adam: A Method for Stochastic
+    Optimization", Algorithm 1), in FP64, for step number t >= 1:
+    the first and second moment estimates are exponential moving averages of
+    the gradient and of its square, each divided by (1 - beta^t) to undo
+    their bias towards the zero start, and the parameters move by
+    lr * m_hat / (sqrt(v_hat) + eps).  Returns (p, m, v) after the step."""
+    assert t >= 1
+    g = np.asarray(g, dtype=np.float64)
+    m = b1 * np.asarray(m, dtype=np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, dtype=np.float64) + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    p = np.asarray(p, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return p, m, v
