@@ -837,13 +837,16 @@ def _ncu_gbs(key):
     return val / (us * 1e-6) / 1e9 if val is not None and digest == _kernel_digest() else None
 
 
-def _gather_bound(torch, dev, edges, t, clocks, probe_t=None):
+def _gather_bound(torch, dev, edges, t, clocks, probe_t=None, lib_t=None):
     """Every edge costs one random gather, and each distinct 128-byte line a
     gather instruction touches is one L1 wavefront; the L1 data pipe retires
     one wavefront per clock per SM (ncu: l1tex__data_pipe_lsu_wavefronts).
-    probe_t: the shortest time of wedge_gather_probe over the same edges
-    (the same source stream and gathers without the reduction), a measured
-    ceiling."""
+    probe_t: the shortest time of the probe (libwedge_probe.so) over the same
+    edges (the same source stream and gathers without the reduction), a
+    measured ceiling of this access pattern.  lib_t: the shortest time of a
+    library gather of the same values by the same sources
+    (torch.index_select with the int32 source array as index), a ceiling
+    measured with code and a launch shape that are not this project's."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = sms * mhz * 1e6 / 1e9
@@ -852,9 +855,32 @@ def _gather_bound(torch, dev, edges, t, clocks, probe_t=None):
            "peak_basis": f"{sms} SMs x {mhz:.0f} MHz x 1 L1 wavefront/clock"}
     if probe_t:
         out.update({"measured_peak": edges / probe_t / 1e9, "frac_of_measured": probe_t / t,
-                    "measured_peak_basis": "wedge_gather_probe: the pull's 16-byte source stream and one 4-byte "
+                    "measured_peak_basis": "wedge_probe_gather: the pull's 16-byte source stream and one 4-byte "
                                            "gather per edge, no reduction, same launch shape"})
+    if lib_t:
+        out.update({"library_gather": edges / lib_t / 1e9, "frac_of_library_gather": lib_t / t,
+                    "library_gather_basis": "torch.index_select(values, 0, int32 sources, out=...): reads the "
+                                            "sources, gathers one 4-byte value per edge and writes it out; "
+                                            "best of 20"})
     return out
+
+
+def gather_ceilings(torch, stream, src, E, vals):
+    """Shortest times (s) over 20 launches of the probe and of the library
+    gather, both over `src` (int32 device tensor of E sources) into `vals`."""
+    from paper_1903_07754_gb300 import probe
+    sink = torch.zeros(1, dtype=torch.float32, device=vals.device)
+    tp = _time_launch(torch, stream, lambda: probe.wedge_probe_gather(src, E, vals, sink, stream=stream), reps=20,
+                      warm=3, best=True)
+    buf = torch.empty(E, dtype=torch.float32, device=vals.device)
+    idx = src[:E]
+
+    def lib():
+        with torch.cuda.stream(stream):
+            torch.index_select(vals, 0, idx, out=buf)
+
+    tl = _time_launch(torch, stream, lib, reps=20, warm=3, best=True)
+    return tp, tl
 
 
 def _time_launch(torch, stream, fn, before=None, reps=10, warm=2, best=False):
@@ -899,11 +925,9 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
     # other count takes every gather as one 32-byte sector
     alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 8 * V
-    sink = torch.zeros(1, dtype=torch.float32, device=dev)
-    tp = _time_launch(torch, stream, lambda: wedge.wedge_gather_probe(G.handle, contrib, sink), reps=20, warm=3,
-                      best=True)
+    tp, tl = gather_ceilings(torch, stream, G.device_src, E, contrib)
     return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "pr", alg, alg_sectors, t, dev,
-                     _gather_bound(torch, dev, E, t, clocks, tp))
+                     _gather_bound(torch, dev, E, t, clocks, tp, tl))
 
 
 def _roofline(kernel, key, alg, alg_sectors, t, dev, gather):
@@ -976,11 +1000,9 @@ def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):
     alg = 4 * (V + 1) + 4 * E + 4 * V + 4 * V + 4 * nchanged + V / 8
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 4 * V + 4 * nchanged + V / 8
     fv = torch.rand(V, dtype=torch.float32, device=dev)
-    sink = torch.zeros(1, dtype=torch.float32, device=dev)
-    tp = _time_launch(torch, stream, lambda: wedge.wedge_gather_probe(S.handle, fv, sink), reps=20, warm=3,
-                      best=True)
+    tp, tl = gather_ceilings(torch, stream, S.device_src, E, fv)
     return _roofline("k_pull<CC> dense (first CC iteration, R-MAT s22 sym)", "cc", alg, alg_sectors, t, dev,
-                     _gather_bound(torch, dev, E, t, None, tp))
+                     _gather_bound(torch, dev, E, t, None, tp, tl))
 
 
 def e2e_measure(wedge, torch, g, s, od, edges, args, dev, opts):

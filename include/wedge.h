@@ -280,17 +280,6 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
  * d_sums: V uint64 (device), must hold zeros on entry; vertices without
  * in-edges keep 0.  Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
 wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums, wedge_stream_t stream);
-/* Diagnostic (not a step of the method): streams g's in-edge source array
- * the way a dense pull does (warp slices of 256 edges, lane = 8 consecutive
- * sources in two 16-byte loads, the next slice in flight) and gathers
- * d_vals[src] for every edge, adding the values into *d_sink (one float,
- * atomically; only the loads matter).  Timed, it measures how fast this GPU
- * streams this edge order with one random 4-byte gather per edge: the
- * ceiling of a dense pull over it, without the per-destination reduction.
- * d_vals: V floats (device); d_sink: 1 float (device).  Asynchronous on
- * stream.  Errors: INVALID_ARG, CUDA. */
-wedge_status wedge_gather_probe(wedge_graph_t g, const float* d_vals, float* d_sink, wedge_stream_t stream);
-
 /* ---- Learned switch (not in the paper) --------------------------------
  * A cost model replaces the fixed fullness threshold and the fixed
  * precision of Section 3.4: before each pull it predicts ln(milliseconds)

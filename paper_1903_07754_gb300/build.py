@@ -13,7 +13,11 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libwedge.so")
-SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu", "probe.cu"]
+SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu"]
+# A measurement tool for the benchmark, linked into a library of its own
+# (include/wedge_probe.h), not into the engine's.
+PROBE_SOURCES = ["probe.cu"]
+PROBE_LIB_PATH = os.path.join(HERE, "libwedge_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -25,7 +29,7 @@ def _nvcc() -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files = [os.path.join(CSRC, s) for s in SOURCES + PROBE_SOURCES]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
@@ -33,14 +37,15 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+    if not (os.path.exists(LIB_PATH) and os.path.exists(PROBE_LIB_PATH)):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = min(os.path.getmtime(LIB_PATH), os.path.getmtime(PROBE_LIB_PATH))
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every CUDA source for sm_103a and link libwedge.so."""
+    """Compile every CUDA source for sm_103a and link libwedge.so and
+    libwedge_probe.so."""
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(BUILD_DIR, exist_ok=True)
@@ -48,10 +53,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                     "--expt-relaxed-constexpr"] + list(extra_flags or [])
     procs = []
-    objs = []
-    for src in SOURCES:
+    objs, probe_objs = [], []
+    for src in SOURCES + PROBE_SOURCES:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        objs.append(obj)
+        (probe_objs if src in PROBE_SOURCES else objs).append(obj)
         cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -65,12 +70,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB_PATH)
+    for path, parts in ((LIB_PATH, objs), (PROBE_LIB_PATH, probe_objs)):
+        tmp = path + f".tmp{os.getpid()}"
+        cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + parts
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        os.replace(tmp, path)
     return LIB_PATH
 
 

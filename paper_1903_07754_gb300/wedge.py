@@ -69,7 +69,7 @@ EXPORTS = [
     "wedge_last_error", "wedge_version", "wedge_graph_set_tuning", "wedge_graph_get_tuning",
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
-    "wedge_pr_pull", "wedge_gather_probe", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
+    "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -100,7 +100,6 @@ def load(path: str = LIB_PATH):
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_pr_pull": (st, [P, P, P, P]),
-        "wedge_gather_probe": (st, [P, P, P, P]),
         "wedge_trim_memory": (st, [i32]),
         "wedge_selftest_timeout": (st, [i32]),
         "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
@@ -254,11 +253,6 @@ def wedge_selftest_timeout(kind):
     return int(load().wedge_selftest_timeout(int(kind)))
 
 
-def wedge_gather_probe(handle, vals, sink, stream=None):
-    """vals: V float32 device tensor; sink: 1 float32 device tensor."""
-    _check(load().wedge_gather_probe(handle, _ptr(vals), _ptr(sink), _stream(stream)))
-
-
 def wedge_pr_pull(handle, contrib, sums, stream=None):
     """One PageRank in-edge pass: sums (int64 view of uint64, zeroed by the
     caller) = exact 2^-62 fixed-point in-edge sums of contrib (float32)."""
@@ -376,6 +370,12 @@ class Graph:
             w = torch.from_numpy(np.ascontiguousarray(g.w, dtype=np.uint32).view(np.int32)).to(device)
         h = wedge_graph_create(g.V, src.numel(), off, src, w, stream=stream)
         return cls(h, keep=(off, src, w))
+
+    @property
+    def device_src(self):
+        """The device tensor of the in-edge sources (int32 view), or None
+        when the graph was created from a raw handle."""
+        return self._keep[1] if len(self._keep) > 1 else None
 
     @property
     def V(self):

@@ -1,5 +1,6 @@
 """The C ABI library builds for sm_103a, loads, and exports every function
-that include/wedge.h declares (no device calls: runs without a GPU)."""
+that include/wedge.h declares; the benchmark's probe library does the same
+for include/wedge_probe.h (no device calls: runs without a GPU)."""
 import os
 import re
 import subprocess
@@ -11,12 +12,13 @@ from paper_1903_07754_gb300 import build as wbuild
 from paper_1903_07754_gb300 import wedge
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+HEADER = os.path.join(ROOT, "include", "wedge.h")
+PROBE_HEADER = os.path.join(ROOT, "include", "wedge_probe.h")
 
 
-def _declared():
+def _declared(headers=(HEADER,)):
     names = set()
-    for h in HEADERS:
+    for h in headers:
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(wedge_\w+)\s*\(", text, flags=re.M):
@@ -30,13 +32,30 @@ def lib():
     return wedge.load()
 
 
+def _exported(path):
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    return {line.split()[-1] for line in out.splitlines() if " T " in line}
+
+
+def test_headers_are_the_engine_and_the_probe():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == \
+        ["wedge.h", "wedge_probe.h"]
+
+
+def test_probe_library_is_separate(lib):
+    from paper_1903_07754_gb300 import probe
+    declared = _declared((PROBE_HEADER,))
+    assert declared == set(probe.EXPORTS) == {"wedge_probe_gather"}
+    assert declared <= _exported(wbuild.PROBE_LIB_PATH)
+    assert not (declared & _exported(wbuild.LIB_PATH)), "the engine library must not carry the probe"
+    assert hasattr(probe.load(), "wedge_probe_gather")
+
+
 def test_every_declared_symbol_is_exported(lib):
     declared = _declared()
     assert {"wedge_graph_create", "wedge_frontier_transform", "wedge_pull_iterate", "wedge_run_bfs",
             "wedge_run_cc", "wedge_run_sssp", "wedge_run_pr"} <= declared
-    out = subprocess.run(["nm", "-D", "--defined-only", wbuild.LIB_PATH], capture_output=True, text=True,
-                         check=True).stdout
-    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    exported = _exported(wbuild.LIB_PATH)
     missing = declared - exported
     assert not missing, f"declared but not exported: {sorted(missing)}"
     for name in declared:
@@ -68,7 +87,7 @@ _C_TYPES = {"uint32_t": ("u", 4), "uint64_t": ("u", 8), "int": ("i", 4), "double
 
 def _header_structs():
     """{name: [(field, kind, size, count)]} for every `typedef struct {...} name;`."""
-    text = "".join(open(h).read() for h in HEADERS)
+    text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     out = {}
     for m in re.finditer(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):

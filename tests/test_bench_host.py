@@ -35,6 +35,10 @@ def test_gather_bound_arithmetic(monkeypatch):
     assert abs(b["measured_peak"] - edges / probe_t / 1e9) < 1e-9
     assert abs(b["frac_of_measured"] - probe_t / t) < 1e-12
     assert "measured_peak" not in bench._gather_bound(torch, 0, edges, t, None)
+    lib_t = 0.3e-3
+    b = bench._gather_bound(torch, 0, edges, t, None, probe_t, lib_t)
+    assert abs(b["library_gather"] - edges / lib_t / 1e9) < 1e-9
+    assert abs(b["frac_of_library_gather"] - lib_t / t) < 1e-12
 
 
 def test_measured_peaks_are_used_when_present():

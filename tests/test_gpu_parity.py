@@ -403,12 +403,17 @@ def test_many_short_segments(switch):
         S.close()
 
 
-def test_gather_probe_sums_the_gathered_values(rmat, rmat_dev):
-    """The diagnostic gathers vals[src] once per edge: with integer-valued
-    floats the sum is exact (sum over u of vals[u] * outdeg(u))."""
+@pytest.mark.parametrize("cut", [0, 5, 301])
+def test_gather_probe_sums_the_gathered_values(rmat, cut):
+    """The benchmark's probe (libwedge_probe.so) gathers vals[src] once per
+    edge: with integer-valued floats the sum is exact, sum over the edges'
+    sources of vals[u] (a ragged tail when `cut` edges are left off)."""
+    from paper_1903_07754_gb300 import probe
+    E = rmat.E - cut
+    src = dev_u32(rmat.src[:E])
     vals = torch.from_numpy((np.arange(rmat.V) % 3).astype(np.float32)).cuda()
     sink = torch.zeros(1, dtype=torch.float32, device="cuda")
-    wedge.wedge_gather_probe(rmat_dev.handle, vals, sink)
-    want = float((np.arange(rmat.V) % 3).astype(np.float64) @ oracle.outdeg(rmat).astype(np.float64))
+    probe.wedge_probe_gather(src, E, vals, sink)
+    want = float((rmat.src[:E].astype(np.int64) % 3).sum())
     assert want < 2 ** 24
     assert float(sink.item()) == want
