@@ -9,8 +9,10 @@ unreached vertices (and additions past the saturation value) at
 0xFFFFFFFF / 0xFFFFFFFE as the engine defines them.  Checking every vertex's
 equation therefore checks the whole output exactly.
 Workloads: R-MAT scale 24 with the learned switch (BFS, SSSP), the rewired
-4096^2 grid (BFS, SSSP) and R-MAT scale 26 batched BFS and SSSP (64 roots;
-two queries of each checked)."""
+4096^2 grid (BFS, SSSP), R-MAT scale 26 batched BFS and SSSP (64 roots, two
+queries of each checked; and three of the sixteen 64-root waves of the
+1024-root run with the benchmark's autotuned settings, two queries of each),
+and the uneven batch of 256 R-MAT graphs of scales 12-20 (every query)."""
 import numpy as np
 import pytest
 import torch
@@ -34,12 +36,14 @@ def _edges(g):
 
 
 def _bellman(dst, src, w, V, root, d):
-    """Asserts d (int64 CUDA, INF = unreached) solves Bellman's equations."""
+    """Asserts d (int64 CUDA, INF = unreached) solves Bellman's equations;
+    `root` is one vertex or an array of them (a query with several roots:
+    the distance to the nearest)."""
     du = d[src]
     cand = torch.where(du == INF, torch.full_like(du, INF), torch.clamp(du + w, max=SAT))
     best = torch.full((V,), INF, dtype=torch.int64, device="cuda").scatter_reduce(
         0, dst, cand, reduce="amin", include_self=True)
-    best[root] = 0
+    best[torch.as_tensor(np.asarray(root, dtype=np.int64), device="cuda")] = 0
     bad = int((best != d).sum().item())
     assert bad == 0, f"{bad} vertices violate the equations"
     assert int((d != INF).sum().item()) > 1
@@ -85,8 +89,13 @@ def test_rewired_grid_4096():
         G.close()
 
 
-def test_batched_bfs_and_sssp_scale26():
-    g = gg.rmat(26, 16).with_weights(255)
+@pytest.fixture(scope="module")
+def g26():
+    return gg.rmat(26, 16).with_weights(255)
+
+
+def test_batched_bfs_and_sssp_scale26(g26):
+    g = g26
     roots = gg.roots(g, 64, seed=3)
     G = graph(g)
     try:
@@ -101,6 +110,61 @@ def test_batched_bfs_and_sssp_scale26():
         w = torch.from_numpy(g.w.astype(np.int64)).cuda()
         for q in (5, 63):
             _bellman(dst, src, w, g.V, int(roots[q]), _u32(lv.view(g.V, 64)[:, q].contiguous()))
+    finally:
+        G.close()
+
+
+def test_batched_1024_roots_scale26_waves(g26):
+    """The 1024-root run as the benchmark times it: the batched-BFS settings
+    its autotuner picks on the first 64 roots, then 16 waves of 64 roots;
+    waves 0, 7 and 15 are checked (two queries each), for BFS and SSSP."""
+    from paper_1903_07754_gb300 import autotune
+    g = g26
+    roots = gg.roots(g, 1024, seed=3)
+    G = graph(g)
+    try:
+        best, _ = autotune.tune(G.handle, "bfs_batch", g.V, roots=roots[:64], nqueries=64,
+                                grid={"k": (1, 2, 3), "tau_bp": (500, 2000, 5000)}, reps=1)
+        autotune.apply(G.handle, best)
+        o = autotune.opts_for("bfs_batch", best)
+        lv = torch.empty(g.V * 64, dtype=torch.int32, device="cuda")
+        dst, src = _edges(g)
+        one = torch.ones(1, dtype=torch.int64, device="cuda").expand(src.numel())
+        w = torch.from_numpy(g.w.astype(np.int64)).cuda()
+        for wave in (0, 7, 15):
+            r = roots[64 * wave:64 * (wave + 1)]
+            wedge.wedge_run_bfs_batch(G.handle, r, None, 64, lv, o, False)
+            for q in (wave % 64, (13 * wave + 5) % 64):
+                _bellman(dst, src, one, g.V, int(r[q]), _u32(lv.view(g.V, 64)[:, q].contiguous()))
+            wedge.wedge_run_sssp_batch(G.handle, r, None, 64, lv, None, False)
+            for q in ((wave + 31) % 64, (7 * wave + 2) % 64):
+                _bellman(dst, src, w, g.V, int(r[q]), _u32(lv.view(g.V, 64)[:, q].contiguous()))
+    finally:
+        G.close()
+
+
+def test_uneven_batch_of_256_graphs_full_size():
+    """The benchmark's uneven batch: 256 R-MAT graphs of scales 12 + (i mod 9)
+    concatenated block-diagonally, graph i's vertex 0 a root of query
+    i mod 64 (four graphs per query).  Every query's levels and distances
+    solve Bellman's equations with its four roots."""
+    graphs = [gg.rmat(12 + (i % 9), 16, seed=1000 + i).with_weights(255) for i in range(256)]
+    big, base = gg.block_diagonal(graphs)
+    del graphs
+    rq = (np.arange(256) % 64).astype(np.uint32)
+    roots = base[:256].astype(np.uint32)
+    G = graph(big)
+    try:
+        lv = torch.empty(big.V * 64, dtype=torch.int32, device="cuda")
+        dst, src = _edges(big)
+        one = torch.ones(1, dtype=torch.int64, device="cuda").expand(src.numel())
+        w = torch.from_numpy(big.w.astype(np.int64)).cuda()
+        wedge.wedge_run_bfs_batch(G.handle, roots, rq, 64, lv, None, False)
+        for q in range(64):
+            _bellman(dst, src, one, big.V, roots[rq == q], _u32(lv.view(big.V, 64)[:, q].contiguous()))
+        wedge.wedge_run_sssp_batch(G.handle, roots, rq, 64, lv, None, False)
+        for q in range(64):
+            _bellman(dst, src, w, big.V, roots[rq == q], _u32(lv.view(big.V, 64)[:, q].contiguous()))
     finally:
         G.close()
 

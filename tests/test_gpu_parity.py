@@ -90,6 +90,33 @@ def test_transform_matches_definition(rmat, rmat_dev, frac):
         np.testing.assert_array_equal(np.sort(got), want)
 
 
+def test_transform_flushes_several_times_per_warp():
+    """A frontier large enough that each transformation warp stages more than
+    one batch of fresh entries (R-MAT s20, 30% of the vertices, k = 0: about
+    5 M edge-index entries over the warps), so the mid-task flushes of the
+    staged list are compared with the Wedge Frontier's definition too."""
+    g = gg.rmat(20, 16)
+    r = np.array([gg.rand(78, i) for i in range(g.V)], dtype=np.uint64)
+    front = (r % np.uint64(100)) < np.uint64(30)
+    G = graph(g, with_weights=False)
+    try:
+        bm = dev_u32(bitmap(G.V, front))
+        nc = G.info["nchunks"]
+        for k in (0, 1):
+            cap = (nc + (1 << k) - 1) >> k
+            lst = empty_u32(cap)
+            cnt = zeros_u32(1)
+            wedge.wedge_frontier_transform(G.handle, bm, k, lst, cnt)
+            n = int(u32(cnt)[0])
+            got = np.sort(u32(lst)[:n].astype(np.uint64))
+            want = oracle.wedge_groups_scan(g, front, 32 << k)
+            assert n == want.size
+            assert np.unique(got).size == n
+            np.testing.assert_array_equal(got, want)
+    finally:
+        G.close()
+
+
 @pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse2", "sparse5", "tau20k1"])
 def test_bfs_matches_oracle(rmat, rmat_dev, mode):
     want = oracle.bfs_push(rmat, 0)
