@@ -51,9 +51,9 @@ def test_gradient_matches_oracle(n):
 def test_adam_matches_oracle_elementwise():
     """wedge_mlp_adam against the FP64 Adam step after 1, 2 and 50 steps of
     the same seeded gradients.  Scales: the moving averages of |g| and g^2
-    (FP32 keeps ~1e-7 of them per step) and the sum of the oracle's step
-    sizes (the update's FP32 arithmetic, including the host's beta^t, keeps
-    ~1e-5 of each step)."""
+    (FP32 keeps ~1e-7 of them per step, plus the FP32 rounding of the
+    betas) and the sum of the oracle's step sizes (the update's FP32
+    arithmetic, including the host's beta^t, keeps ~1e-5 of each step)."""
     rng = np.random.default_rng(17)
     n, lr = omlp.NPARAMS, 2e-3
     G = rng.normal(0, 1, (50, n)).astype(np.float32)
@@ -71,7 +71,9 @@ def test_adam_matches_oracle_elementwise():
         if t in (1, 2, 50):
             gp, gm, gv = (x.cpu().numpy().astype(np.float64) for x in (dp, dm, dv))
             assert np.all(np.abs(gm - om) <= 1e-5 * abs_m), f"m, step {t}"
-            assert np.all(np.abs(gv - ov) <= 1e-5 * ov), f"v, step {t}"
+            # v: (1 - beta2) in FP32 is 1 - 0.999f = 0.00099998713, 1.3e-5
+            # below 0.001, so every FP32 second moment sits ~1.3e-5 low
+            assert np.all(np.abs(gv - ov) <= 3e-5 * ov), f"v, step {t}"
             tol = 1e-4 * moved + 2 * t * 2.0 ** -24 * np.abs(op)
             bad = np.flatnonzero(np.abs((gp - p0) - (op - p0)) > tol)
             assert bad.size == 0, (t, bad[:10], gp[bad[:10]], op[bad[:10]])
