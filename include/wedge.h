@@ -206,6 +206,33 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
                                       uint32_t log2_coarsen, uint32_t* d_chunk_list,
                                       uint32_t* d_chunk_count, wedge_stream_t stream);
 
+/* Load balance of the frontier transformation (Section 4, "Parallelization";
+ * Section 5.3 and Fig. 13, which measure the time threads spend idle at the
+ * transformation's barrier).  Runs the transformation of
+ * wedge_frontier_transform (same arguments and output) under one of two
+ * schedules and records, for every warp of the launch and each kernel, the
+ * warp's start and end on the device's global timer and its busy SM cycles:
+ *  schedule 0: the library's (wedge_frontier_transform): kernel 0 cuts the
+ *              active vertices' edge-index rows into pieces of at most 32
+ *              entries, kernel 1 expands them with the pieces balanced over
+ *              the warps;
+ *  schedule 1: the paper's: the vertex frontier is cut into equal pieces of
+ *              256 vertices, each taken by the next free warp, which walks
+ *              every row of its piece's active vertices (kernel 0 only;
+ *              kernel 1's records stay zero).
+ * d_warp_stats (device): 8 uint64 per warp w, {start ns, end ns, busy SM
+ * cycles, SM id} of kernel 0 at [8w .. 8w+3] and of kernel 1 at
+ * [8w+4 .. 8w+7].  A warp is busy from its start to the end of its last
+ * piece and idle from then to the end of the kernel (the barrier).
+ * *n_warps (host) = the launch's warps; with d_warp_stats = NULL only
+ * *n_warps is set.  cap_warps: warps d_warp_stats holds (>= *n_warps).
+ * Errors: INVALID_ARG (NULL, schedule > 1, cap_warps too small,
+ * log2_coarsen > 7), CUDA. */
+wedge_status wedge_frontier_transform_profile(wedge_graph_t g, const uint32_t* d_vertex_bitmap,
+                                              uint32_t log2_coarsen, uint32_t schedule, uint32_t* d_chunk_list,
+                                              uint32_t* d_chunk_count, uint64_t* d_warp_stats, uint32_t cap_warps,
+                                              uint32_t* n_warps, wedge_stream_t stream);
+
 /* The frontier transformation without any memory allocation.  The paper has
  * no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (a framework that owns all device memory through its own pool,

@@ -197,6 +197,7 @@ struct wedge_graph {
     int pull_blocks_tma[4] = {0, 0, 0, 0};     // bulk-copy staged dense pulls
     wedge_tuning tuning{};
     int xform_blocks = 0;
+    unsigned* slice_ctr = nullptr;  // load-balance study: the paper's schedule's slice counter
     uint32_t last_iters = 0;
     bool last_trace = false;
     cudaStream_t last_stream = nullptr;

@@ -117,6 +117,10 @@ struct XformParams {
     unsigned int* count_out;     // standalone mode: list count (else rec[it].nchunks)
     int standalone_k;            // >= 0: standalone transformation at this coarsening
     int trace;
+    // load-balance accounting of a standalone transformation (nullptr: off):
+    // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
+    unsigned long long* wstat;
+    unsigned* slice_ctr;         // the paper's schedule: next frontier slice
 };
 
 // ------------------------------------------------------------------------
@@ -1166,15 +1170,46 @@ __device__ __forceinline__ void prepare_iteration(const XformParams& X, unsigned
         reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
 }
 
+// Load-balance accounting (standalone transformations only): warp `gw`'s
+// record {start ns, end ns, busy cycles, SM} in slot `kernel` (0: scan or
+// the paper's schedule, 1: expansion).
+struct WarpStamp {
+    unsigned long long t0 = 0, c0 = 0;
+    __device__ __forceinline__ void start(const XformParams& X) {
+        if (X.wstat) {
+            t0 = global_timer();
+            c0 = clock64();
+        }
+    }
+    __device__ __forceinline__ void stop(const XformParams& X, unsigned long long gw, int kernel) {
+        if (!X.wstat) return;
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            unsigned long long* w = X.wstat + gw * 8 + kernel * 4;
+            w[0] = t0;
+            w[1] = global_timer();
+            w[2] = clock64() - c0;
+            w[3] = smid;
+        }
+    }
+};
+
 __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
     RunCtl* C = X.ctl;
     const uint32_t* bm;
     IterRec* r;
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    WarpStamp ws;
+    ws.start(X);
     if (X.standalone_k >= 0) {
         bm = X.bm_in;
         r = X.rec;
+        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+        ws.stop(X, tid >> 5, 0);
+        return;
     } else {
         if (C->done) return;
         const unsigned it = C->it;
@@ -1213,11 +1248,67 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    WarpStamp ws;
+    ws.start(X);
     xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+    if (X.standalone_k >= 0) ws.stop(X, gw, 1);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
     }
+}
+
+// The transformation as the paper's implementation schedules it (Section 4,
+// "Parallelization"), for the load-balance study of Section 5.3 (Fig. 13):
+// the vertex frontier is sliced into equal pieces of kStaticSliceWords
+// bitmap words, each taken by the next free warp, which walks the whole
+// edge-index row of every active vertex in its piece, 32 entries at a time
+// (neither the pieces' bit counts nor the rows' lengths are considered).
+// Every Wedge bitmap bit is set with an atomicOr; the one that finds it
+// clear appends its entry to the list.  Standalone transformations only.
+constexpr unsigned kStaticSliceWords = 8;  // 256 vertices per piece
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_static(const XformParams X) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned k = (unsigned)X.standalone_k;
+    const unsigned long long nslices = (X.bm_words + kStaticSliceWords - 1) / kStaticSliceWords;
+    WarpStamp ws;
+    ws.start(X);
+    for (;;) {
+        unsigned long long sl = 0;
+        if (lane == 0) sl = atomicAdd(X.slice_ctr, 1u);
+        sl = __shfl_sync(kFull, sl, 0);
+        if (sl >= nslices) break;
+        for (unsigned long long wi = sl * kStaticSliceWords; wi < (sl + 1) * kStaticSliceWords && wi < X.bm_words;
+             ++wi) {
+            uint32_t word = __ldg(X.bm_in + wi);
+            if (wi == X.bm_words - 1 && (X.V & 31)) word &= (1u << (X.V & 31)) - 1u;
+            for (; word; word &= word - 1) {
+                const uint32_t u = (uint32_t)(wi * 32 + __ffs(word) - 1);
+                const uint32_t rb = __ldg(X.eidx_off + u), re = __ldg(X.eidx_off + u + 1);
+                for (uint32_t e0 = rb; e0 < re; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    bool fresh = false;
+                    uint32_t b = 0;
+                    if (e < re) {
+                        b = __ldg(X.eidx + e) >> k;
+                        const uint32_t bit = 1u << (b & 31);
+                        fresh = (atomicOr(X.wb + (b >> 5), bit) & bit) == 0;
+                    }
+                    const unsigned m = __ballot_sync(kFull, fresh);
+                    if (m) {
+                        const unsigned leader = __ffs(m) - 1;
+                        unsigned slot = 0;
+                        if (lane == leader) slot = atomicAdd(X.count_out, (unsigned)__popc(m));
+                        slot = __shfl_sync(kFull, slot, leader);
+                        if (fresh) X.clist[slot + __popc(m & ((1u << lane) - 1u))] = b;
+                    }
+                }
+            }
+        }
+    }
+    ws.stop(X, gw, 0);
 }
 
 // ------------------------------------------------------------------------
@@ -2121,6 +2212,8 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.count_out = nullptr;
     X.standalone_k = -1;
     X.trace = trace;
+    X.wstat = nullptr;
+    X.slice_ctr = nullptr;
     return X;
 }
 
@@ -2715,6 +2808,44 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
     X.count_out = d_chunk_count;
     X.standalone_k = (int)log2_coarsen;
     launch_xform(g, X, s);
+    k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
+    count_launch();
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    return WEDGE_OK;
+}
+
+wedge_status wedge_frontier_transform_profile(wedge_graph_t g, const uint32_t* d_vertex_bitmap,
+                                              uint32_t log2_coarsen, uint32_t schedule, uint32_t* d_chunk_list,
+                                              uint32_t* d_chunk_count, uint64_t* d_warp_stats, uint32_t cap_warps,
+                                              uint32_t* n_warps, wedge_stream_t stream) {
+    if (!g || !n_warps) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (schedule > 1) return set_error(WEDGE_ERR_INVALID_ARG, "schedule must be 0 or 1");
+    const uint32_t nw = (uint32_t)((uint64_t)g->xform_blocks * kXformThreads / 32);
+    *n_warps = nw;
+    if (!d_warp_stats) return WEDGE_OK;
+    if (!d_vertex_bitmap || !d_chunk_list || !d_chunk_count) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (cap_warps < nw) return set_error(WEDGE_ERR_INVALID_ARG, "d_warp_stats holds fewer warps than the launch");
+    if (log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->slice_ctr) WEDGE_TRY(dev_alloc(g, (void**)&g->slice_ctr, 16));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, sizeof(IterRec), s));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(d_chunk_count, 0, 4, s));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->slice_ctr, 0, 4, s));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(d_warp_stats, 0, (size_t)nw * 8 * sizeof(uint64_t), s));
+    XformParams X = xform_params(g, 0);
+    X.bm_in = d_vertex_bitmap;
+    X.clist = d_chunk_list;
+    X.count_out = d_chunk_count;
+    X.standalone_k = (int)log2_coarsen;
+    X.wstat = reinterpret_cast<unsigned long long*>(d_warp_stats);
+    X.slice_ctr = g->slice_ctr;
+    if (schedule == 0) {
+        launch_xform(g, X, s);
+    } else {
+        k_xform_static<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
+        count_launch();
+    }
     k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
     count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());

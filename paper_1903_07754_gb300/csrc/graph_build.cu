@@ -346,6 +346,7 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->ms_seen);
     dev_free(g->ms_roots);
     dev_free(g->ms_bar);
+    dev_free(g->slice_ctr);
     if (g->ms_exec) cudaGraphExecDestroy(g->ms_exec);
     for (auto& e : g->loop_exec)
         if (e) cudaGraphExecDestroy(e);

@@ -70,6 +70,7 @@ EXPORTS = [
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
+    "wedge_frontier_transform_profile",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
         "wedge_graph_copy_edge_index": (st, [P, P, P, P]),
         "wedge_frontier_transform": (st, [P, P, u32, P, P, P]),
         "wedge_frontier_transform_noalloc": (st, [u32, u64, P, P, P, u32, P, P, P]),
+        "wedge_frontier_transform_profile": (st, [P, P, u32, u32, P, P, P, u32, ctypes.POINTER(u32), P]),
         "wedge_pull_iterate": (st, [P, i32, P, u32, P, P, P, u32, P, P, P, P]),
         "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
@@ -200,6 +202,21 @@ def wedge_frontier_transform_noalloc(V, E, eidx_off, eidx, vertex_bitmap, log2_c
     _check(load().wedge_frontier_transform_noalloc(int(V), int(E), _ptr(eidx_off), _ptr(eidx), _ptr(vertex_bitmap),
                                                    int(log2_coarsen), _ptr(chunk_list), _ptr(chunk_count),
                                                    _stream(stream)))
+
+
+def wedge_frontier_transform_profile(handle, bitmap, k, schedule, chunk_list, chunk_count, stream=None):
+    """Runs one transformation under `schedule` (0 library, 1 the paper's)
+    and returns the per-warp records as an (n_warps, 2, 4) uint64 array:
+    [warp, kernel, {start ns, end ns, busy cycles, SM}]."""
+    import torch
+    n = ctypes.c_uint32(0)
+    _check(load().wedge_frontier_transform_profile(handle, None, int(k), int(schedule), None, None, None, 0,
+                                                   ctypes.byref(n), _stream(stream)))
+    stats = torch.zeros(n.value * 8, dtype=torch.int64, device=chunk_list.device)
+    _check(load().wedge_frontier_transform_profile(handle, _ptr(bitmap), int(k), int(schedule), _ptr(chunk_list),
+                                                   _ptr(chunk_count), _ptr(stats), n.value, ctypes.byref(n),
+                                                   _stream(stream)))
+    return stats.cpu().numpy().view(np.uint64).reshape(n.value, 2, 4)
 
 
 def wedge_pull_iterate(handle, app, values, it, cur_bitmap, chunk_list, chunk_count, log2_coarsen, next_bitmap,

@@ -117,6 +117,41 @@ def test_transform_flushes_several_times_per_warp():
         G.close()
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_transform_profile_schedules_match_definition(rmat, rmat_dev, schedule):
+    """The load-balance study's transformation (the library's schedule and
+    the paper's static slices) produces the Wedge Frontier's definition, and
+    every warp's records are well formed: start <= end within the kernel's
+    span, busy cycles > 0, an SM id below the SM count."""
+    G = rmat_dev
+    r = np.array([gg.rand(79, i) for i in range(G.V)], dtype=np.uint64)
+    front = (r % np.uint64(100)) < np.uint64(20)
+    front[0] = True          # the hub: one long row
+    bm = dev_u32(bitmap(G.V, front))
+    nc = G.info["nchunks"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for k in (0, 2):
+        cap = (nc + (1 << k) - 1) >> k
+        lst = empty_u32(cap)
+        cnt = zeros_u32(1)
+        rec = wedge.wedge_frontier_transform_profile(G.handle, bm, k, schedule, lst, cnt)
+        n = int(u32(cnt)[0])
+        got = np.sort(u32(lst)[:n].astype(np.uint64))
+        np.testing.assert_array_equal(got, oracle.wedge_groups_scan(rmat, front, 32 << k))
+        kernels = (0, 1) if schedule == 0 else (0,)
+        for kk in kernels:
+            st, en, cyc, sm = (rec[:, kk, i] for i in range(4))
+            assert np.all(st > 0) and np.all(en >= st)
+            assert np.all(cyc > 0) and np.all(sm < sms)
+        if schedule == 1:
+            assert np.all(rec[:, 1, :] == 0)
+        # the library's transformation afterwards still matches (Wedge bitmap left clear)
+        cnt2 = zeros_u32(1)
+        wedge.wedge_frontier_transform(G.handle, bm, k, lst, cnt2)
+        n2 = int(u32(cnt2)[0])
+        np.testing.assert_array_equal(np.sort(u32(lst)[:n2].astype(np.uint64)), got)
+
+
 @pytest.mark.parametrize("mode", ["default", "dense", "sparse0", "sparse2", "sparse5", "tau20k1"])
 def test_bfs_matches_oracle(rmat, rmat_dev, mode):
     want = oracle.bfs_push(rmat, 0)
