@@ -799,26 +799,28 @@ def bench_grid(args, wedge, torch, dev, world):
 
 
 # DRAM traffic of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum),
-# that launch's ncu gpu__time_duration in us, and a digest of the kernel
-# sources they were measured on: reported only while those sources are
-# unchanged.
-TRAFFIC = {"pr": (321036800, 253.184, "19e411d6848f961c"), "cc": (607268096, 507.968, "19e411d6848f961c")}
+# that launch's ncu gpu__time_duration in us, and a digest of the device code
+# of the captured kernel (KERNEL_FILES): reported only while that code is
+# unchanged.  (None, None, None): no capture on the current code yet.
+TRAFFIC = {"pr": (None, None, None), "cc": (None, None, None)}
+# The sources each captured kernel is built from.
+KERNEL_FILES = {"pr": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
+                "cc": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
+                "xform": ("xform.cuh", "common.cuh")}
 
 
-def _kernel_digest():
-    """Digest of the kernel sources' code: comments and whitespace are
-    dropped, and so are the host parts (engine.cu from its "Host side"
-    banner on, common.cuh from the host-side graph object on), so that only
-    a change of device code invalidates the counters."""
+def _kernel_digest(key="pr"):
+    """Digest of the device code the kernel `key` is built from: comments and
+    whitespace are dropped, and so is common.cuh's host part (from the
+    host-side graph object on), so that only a change of that device code
+    invalidates its counters."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("engine.cu", "common.cuh", "tma.cuh", "mlp.cuh"):
+    for f in KERNEL_FILES[key]:
         with open(os.path.join(ROOT, "paper_1903_07754_gb300", "csrc", f)) as fh:
             src = fh.read()
-        if f == "engine.cu":
-            src = src[:src.index("\n// Host side\n")]
-        elif f == "common.cuh":
+        if f == "common.cuh":
             src = src[:src.index("\nstruct wedge_graph {")]
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -828,13 +830,13 @@ def _kernel_digest():
 
 def _traffic(key):
     val, _, digest = TRAFFIC[key]
-    return val if val is not None and digest == _kernel_digest() else None
+    return val if val is not None and digest == _kernel_digest(key) else None
 
 
 def _ncu_gbs(key):
     """DRAM bytes over the launch's duration, both from the ncu capture."""
     val, us, digest = TRAFFIC[key]
-    return val / (us * 1e-6) / 1e9 if val is not None and digest == _kernel_digest() else None
+    return val / (us * 1e-6) / 1e9 if val is not None and digest == _kernel_digest(key) else None
 
 
 def _gather_bound(torch, dev, edges, t, clocks, probe_t=None, lib_t=None):

@@ -31,6 +31,7 @@
 
 namespace wedge {
 
+constexpr unsigned kFull = 0xFFFFFFFFu;  // all lanes of a warp
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kSat = 0xFFFFFFFEu;
 constexpr uint32_t kChunk = 32;

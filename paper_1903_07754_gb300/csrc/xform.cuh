@@ -1,0 +1,424 @@
+// The frontier transformation (Sections 3.3, 4; K2 and the compaction K3):
+// its parameter block, the library's load-balanced scan and expansion, and
+// the paper's static schedule with per-warp load-balance accounting
+// (Section 5.3, Fig. 13).  Included by engine.cu after pull.cuh.
+#pragma once
+
+#include "common.cuh"
+
+namespace wedge {
+
+struct XformParams {
+    const uint32_t* eidx;
+    const uint32_t* eidx_off;
+    uint2* pieces;
+    uint32_t* wb;
+    uint32_t* clist;
+    IterRec* rec;
+    RunCtl* ctl;
+    uint32_t* bm[2];             // run mode: frontier bitmaps by parity
+    uint32_t* flist[2];          // run mode: frontier lists by parity
+    const uint32_t* bm_in;       // standalone mode: the caller's frontier bitmap
+    uint32_t V;
+    unsigned long long bm_words;
+    unsigned int* count_out;     // standalone mode: list count (else rec[it].nchunks)
+    int standalone_k;            // >= 0: standalone transformation at this coarsening
+    int trace;
+    // load-balance accounting of a standalone transformation (nullptr: off):
+    // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
+    unsigned long long* wstat;
+    unsigned* slice_ctr;         // the paper's schedule: next frontier slice
+};
+
+// ------------------------------------------------------------------------
+// Transformation (K2), two kernels.
+//   A (k_xform_scan): walk the vertex frontier bitmap; every active vertex's
+//     edge-index row is cut into pieces of at most 32 entries; one
+//     reservation per warp.  In run mode it also clears the bitmap the next
+//     pull fills and the record that pull accumulates into.
+//   B (k_xform_expand): expand the pieces with the warp's lanes balanced over
+//     up to 32 pieces at a time, set the Wedge Frontier bits (bit b = list
+//     entry b at coarsening k) and append every newly set bit to the list:
+//     the bitmap removes duplicates (Section 4).
+// ------------------------------------------------------------------------
+// The warp's rows (lane L: row start rb, length rl, np pieces, exclusive
+// piece offset excl among the warp's pieces) written as pieces of at most 32
+// entries to pieces[slot0 ...] by all 32 lanes: piece i goes to the lane
+// whose range holds it (binary search over the lanes' offsets), so one long
+// row (a hub's) is written by the whole warp.
+__device__ __forceinline__ void write_pieces(uint2* pieces, unsigned slot0, unsigned total, uint32_t rb, uint32_t rl,
+                                             unsigned excl) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned i0 = 0; i0 < total; i0 += 32) {
+        const unsigned i = i0 + lane;
+        unsigned jx = 0;
+#pragma unroll
+        for (unsigned stp = 16; stp >= 1; stp >>= 1) {
+            const unsigned ex = __shfl_sync(kFull, excl, jx + stp);
+            if (ex <= i) jx += stp;
+        }
+        const uint32_t b = __shfl_sync(kFull, rb, jx);
+        const uint32_t l = __shfl_sync(kFull, rl, jx);
+        const unsigned q = (i - __shfl_sync(kFull, excl, jx)) * 32u;
+        if (i < total) pieces[slot0 + i] = make_uint2(b + q, min(32u, l - q));
+    }
+}
+
+// Warp-level scan of bitmap words [gw*32, ...) step nw*32: pieces of the
+// active vertices' edge-index rows, one reservation per warp on *npieces.
+__device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V, unsigned long long words,
+                                                 const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                 unsigned* npieces, unsigned long long gw, unsigned long long nw) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned long long base = gw * 32; base < words; base += nw * 32) {
+        const unsigned long long wi = base + lane;
+        uint32_t word = wi < words ? __ldcg(bm + wi) : 0u;
+        if (wi == words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
+        unsigned np = 0;
+        for (uint32_t w = word; w; w &= w - 1) {
+            const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
+            np += (__ldg(eidx_off + u + 1) - __ldg(eidx_off + u) + 31u) >> 5;
+        }
+        unsigned incl = np;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (!total) continue;
+        unsigned slot = 0;
+        if (lane == 31) slot = atomicAdd(npieces, total);
+        slot = __shfl_sync(kFull, slot, 31);
+        // one vertex per lane and round: every round's rows go out together
+        unsigned rem = word, done = 0;
+        while (__any_sync(kFull, rem != 0)) {
+            uint32_t rb = 0, rl = 0;
+            if (rem) {
+                const uint32_t u = (uint32_t)(wi * 32 + __ffs(rem) - 1);
+                rem &= rem - 1;
+                rb = __ldg(eidx_off + u);
+                rl = __ldg(eidx_off + u + 1) - rb;
+            }
+            const unsigned p = (rl + 31u) >> 5;
+            unsigned pi = p;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(kFull, pi, d);
+                if (lane >= (unsigned)d) pi += y;
+            }
+            const unsigned rt = __shfl_sync(kFull, pi, 31);
+            write_pieces(pieces, slot + done, rt, rb, rl, pi - p);
+            done += rt;
+        }
+    }
+}
+
+// Same as xform_scan_words over an explicit list of n frontier vertices.
+__device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n,
+                                                const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                unsigned* npieces, unsigned long long gw, unsigned long long nw) {
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        uint32_t rb = 0, rl = 0;
+        if (i < n) {
+            const uint32_t u = __ldcg(list + i);
+            rb = __ldg(eidx_off + u);
+            rl = __ldg(eidx_off + u + 1) - rb;
+        }
+        const unsigned np = (rl + 31u) >> 5;
+        unsigned incl = np;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (!total) continue;
+        unsigned slot = 0;
+        if (lane == 31) slot = atomicAdd(npieces, total);
+        slot = __shfl_sync(kFull, slot, 31);
+        write_pieces(pieces, slot, total, rb, rl, incl - np);
+    }
+}
+
+// Zeroes the bitmap words of a frontier: by its list when complete,
+// otherwise every word.  Optionally zeroes the vertices' query masks too.
+__device__ __forceinline__ void clear_frontier(uint32_t* bm, unsigned long long words, const uint32_t* list,
+                                               bool complete, unsigned n, unsigned long long* masks,
+                                               unsigned long long tid, unsigned long long nth) {
+    if (complete) {
+        for (unsigned long long i = tid; i < n; i += nth) {
+            const uint32_t v = __ldcg(list + i);
+            bm[v >> 5] = 0u;
+            if (masks) masks[v] = 0ull;
+        }
+    } else if (masks) {
+        for (unsigned long long wi = tid; wi < words; wi += nth) {
+            uint32_t w = __ldcg(bm + wi);
+            if (!w) continue;
+            bm[wi] = 0u;
+            for (; w; w &= w - 1) masks[wi * 32 + __ffs(w) - 1] = 0ull;
+        }
+    } else {
+        for (unsigned long long wi = tid; wi < words; wi += nth) bm[wi] = 0u;
+    }
+}
+
+// Warp-level expansion of n pieces: Wedge bitmap bits (entry = chunk >> k),
+// fresh bits appended to list with a warp-aggregated reservation on *count.
+// A warp task is up to 32 pieces, fewer when there are too few pieces to
+// give every warp a task (one hub's row): a task's entries are walked 32 at
+// a time, so its length is the latency that matters.
+// Fresh list entries staged by a warp are appended with one reservation on
+// the list's counter per kAppendStage entries (appending every round put up
+// to one atomic per 32 entries on that single address).
+constexpr unsigned kAppendStage = 256;
+
+__device__ __forceinline__ void flush_staged(uint32_t* list, unsigned* count, const uint32_t* stage, unsigned n) {
+    const unsigned lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(count, n);
+    base = __shfl_sync(kFull, base, 0);
+    for (unsigned i = lane; i < n; i += 32) list[base + i] = stage[i];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigned n, unsigned k,
+                                                    const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
+                                                    unsigned* count, unsigned long long gw, unsigned long long nw,
+                                                    uint32_t* stage = nullptr) {
+    unsigned staged = 0;  // warp-uniform
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned long long per = (unsigned long long)n / nw;
+    const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
+    for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
+        const unsigned long long idx = base + lane;
+        const uint2 pc = (lane < ppt && idx < n) ? __ldcg(pieces + idx) : make_uint2(0u, 0u);
+        unsigned incl = pc.y;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        const unsigned excl = incl - pc.y;
+        for (unsigned e0 = 0; e0 < total; e0 += 32) {
+            const unsigned e = e0 + lane;
+            const bool act = e < total;
+            unsigned jx = 0;
+#pragma unroll
+            for (unsigned stp = 16; stp >= 1; stp >>= 1) {
+                const unsigned cj = jx + stp;
+                const unsigned ex = __shfl_sync(kFull, excl, cj);
+                if (ex <= e) jx = cj;
+            }
+            const unsigned st = __shfl_sync(kFull, pc.x, jx);
+            const unsigned ex = __shfl_sync(kFull, excl, jx);
+            // Lanes are runs of consecutive rows' entries, so neighbouring
+            // lanes often hit the same bitmap word (always for a hub's row
+            // at coarse precision).  Each run of lanes on one word sets its
+            // bits with one atomicOr by the run's last lane; within the
+            // run, the first lane holding an entry owns it, and it is fresh
+            // if the word did not have its bit before.
+            const uint32_t b = act ? __ldg(eidx + st + (e - ex)) >> k : 0xFFFFFFFFu;
+            const uint32_t word = b >> 5;
+            const uint32_t bit = act ? 1u << (b & 31) : 0u;
+            const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
+            const unsigned starts = __ballot_sync(kFull, lane == 0 || word != wprev);
+            const unsigned rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
+            const unsigned above = starts & ~(lt_mask | (1u << lane));
+            const unsigned re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
+            uint32_t bits = bit;
+#pragma unroll
+            for (unsigned d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, bits, d);
+                if (lane >= rs + d) bits |= y;
+            }
+            uint32_t old = 0;
+            if (lane == re && act) old = atomicOr(wb + word, bits);
+            old = __shfl_sync(kFull, old, re);
+            const unsigned run = (re == 31 ? kFull : ((2u << re) - 1u)) & ~((1u << rs) - 1u);
+            const unsigned same = __match_any_sync(kFull, b) & run;
+            const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
+            const unsigned m = __ballot_sync(kFull, fresh);
+            if (m && stage) {
+                const unsigned nm = __popc(m);
+                if (staged + nm > kAppendStage) {
+                    flush_staged(list, count, stage, staged);
+                    staged = 0;
+                }
+                if (fresh) stage[staged + __popc(m & lt_mask)] = b;
+                staged += nm;
+            } else if (m) {
+                const unsigned leader = __ffs(m) - 1;
+                unsigned slot = 0;
+                if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
+                slot = __shfl_sync(kFull, slot, leader);
+                if (fresh) list[slot + __popc(m & lt_mask)] = b;
+            }
+        }
+    }
+    if (stage && staged) flush_staged(list, count, stage, staged);
+}
+
+// Before iteration `it` fills the next frontier: the bitmap it fills held
+// F_{it-1}, so clear it (by its list when that list is complete), and zero
+// the record the iteration accumulates into.  Idempotent until then.
+__device__ __forceinline__ void prepare_iteration(const XformParams& X, unsigned it, unsigned long long tid,
+                                                  unsigned long long nth) {
+    if (it > 0) {
+        const IterRec& pr = X.rec[it - 1];
+        uint32_t* clr = ((it + 1) & 1) ? X.bm[1] : X.bm[0];
+        clear_frontier(clr, X.bm_words, ((it + 1) & 1) ? X.flist[1] : X.flist[0], pr.nlist == pr.nfront, pr.nfront,
+                       nullptr, tid, nth);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(IterRec) / 4)
+        reinterpret_cast<unsigned*>(X.rec + it + 1)[threadIdx.x] = 0u;
+}
+
+// Load-balance accounting (standalone transformations only): warp `gw`'s
+// record {start ns, end ns, busy cycles, SM} in slot `kernel` (0: scan or
+// the paper's schedule, 1: expansion).
+struct WarpStamp {
+    unsigned long long t0 = 0, c0 = 0;
+    __device__ __forceinline__ void start(const XformParams& X) {
+        if (X.wstat) {
+            t0 = global_timer();
+            c0 = clock64();
+        }
+    }
+    __device__ __forceinline__ void stop(const XformParams& X, unsigned long long gw, int kernel) {
+        if (!X.wstat) return;
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            unsigned long long* w = X.wstat + gw * 8 + kernel * 4;
+            w[0] = t0;
+            w[1] = global_timer();
+            w[2] = clock64() - c0;
+            w[3] = smid;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
+    RunCtl* C = X.ctl;
+    const uint32_t* bm;
+    IterRec* r;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    WarpStamp ws;
+    ws.start(X);
+    if (X.standalone_k >= 0) {
+        bm = X.bm_in;
+        r = X.rec;
+        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+        ws.stop(X, tid >> 5, 0);
+        return;
+    } else {
+        if (C->done) return;
+        const unsigned it = C->it;
+        if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
+        prepare_iteration(X, it, tid, nth);
+        r = X.rec + it;
+        if (r->mode == 0) return;
+        if (r->nlist == r->nfront) {
+            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, X.pieces, &r->npieces,
+                            tid >> 5, nth >> 5);
+            return;
+        }
+        bm = (it & 1) ? X.bm[1] : X.bm[0];
+    }
+    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+}
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
+    RunCtl* C = X.ctl;
+    unsigned n, k;
+    unsigned* count;
+    unsigned it = 0;
+    if (X.standalone_k >= 0) {
+        n = __ldcg(&X.rec[0].npieces);
+        k = (unsigned)X.standalone_k;
+        count = X.count_out;
+    } else {
+        if (C->done) return;
+        it = C->it;
+        const IterRec* r = X.rec + it;
+        if (r->mode == 0) return;
+        n = r->npieces;
+        k = r->k;
+        count = &X.rec[it].nchunks;
+    }
+    __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    WarpStamp ws;
+    ws.start(X);
+    xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+    if (X.standalone_k >= 0) ws.stop(X, gw, 1);
+    if (X.trace && X.standalone_k < 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
+    }
+}
+
+// The transformation as the paper's implementation schedules it (Section 4,
+// "Parallelization"), for the load-balance study of Section 5.3 (Fig. 13):
+// the vertex frontier is sliced into equal pieces of kStaticSliceWords
+// bitmap words, each taken by the next free warp, which walks the whole
+// edge-index row of every active vertex in its piece, 32 entries at a time
+// (neither the pieces' bit counts nor the rows' lengths are considered).
+// Every Wedge bitmap bit is set with an atomicOr; the one that finds it
+// clear appends its entry to the list.  Standalone transformations only.
+constexpr unsigned kStaticSliceWords = 8;  // 256 vertices per piece
+
+__global__ void __launch_bounds__(kXformThreads) k_xform_static(const XformParams X) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned k = (unsigned)X.standalone_k;
+    const unsigned long long nslices = (X.bm_words + kStaticSliceWords - 1) / kStaticSliceWords;
+    WarpStamp ws;
+    ws.start(X);
+    for (;;) {
+        unsigned long long sl = 0;
+        if (lane == 0) sl = atomicAdd(X.slice_ctr, 1u);
+        sl = __shfl_sync(kFull, sl, 0);
+        if (sl >= nslices) break;
+        for (unsigned long long wi = sl * kStaticSliceWords; wi < (sl + 1) * kStaticSliceWords && wi < X.bm_words;
+             ++wi) {
+            uint32_t word = __ldg(X.bm_in + wi);
+            if (wi == X.bm_words - 1 && (X.V & 31)) word &= (1u << (X.V & 31)) - 1u;
+            for (; word; word &= word - 1) {
+                const uint32_t u = (uint32_t)(wi * 32 + __ffs(word) - 1);
+                const uint32_t rb = __ldg(X.eidx_off + u), re = __ldg(X.eidx_off + u + 1);
+                for (uint32_t e0 = rb; e0 < re; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    bool fresh = false;
+                    uint32_t b = 0;
+                    if (e < re) {
+                        b = __ldg(X.eidx + e) >> k;
+                        const uint32_t bit = 1u << (b & 31);
+                        fresh = (atomicOr(X.wb + (b >> 5), bit) & bit) == 0;
+                    }
+                    const unsigned m = __ballot_sync(kFull, fresh);
+                    if (m) {
+                        const unsigned leader = __ffs(m) - 1;
+                        unsigned slot = 0;
+                        if (lane == leader) slot = atomicAdd(X.count_out, (unsigned)__popc(m));
+                        slot = __shfl_sync(kFull, slot, leader);
+                        if (fresh) X.clist[slot + __popc(m & ((1u << lane) - 1u))] = b;
+                    }
+                }
+            }
+        }
+    }
+    ws.stop(X, gw, 0);
+}
+
+}  // namespace wedge

@@ -65,22 +65,29 @@ def _digest_of(tmp_path, monkeypatch, edit=None):
 
 def test_digest_follows_device_code_only(tmp_path, monkeypatch):
     base = _digest_of(tmp_path, monkeypatch)
-    # comments and the host part do not count
-    assert _digest_of(tmp_path, monkeypatch, ("engine.cu", "\n// Host side\n", "\n// Host side\n// a note\n")) == base
-    host = open(os.path.join(bench.ROOT, "paper_1903_07754_gb300", "csrc", "engine.cu")).read()
-    tail = host[host.index("\n// Host side\n"):]
-    assert "static PullParams pull_params(" in tail
-    assert _digest_of(tmp_path, monkeypatch,
-                      ("engine.cu", "static PullParams pull_params(", "static PullParams  pull_params(")) == base
+    # comments and the host part of common.cuh do not count
+    assert _digest_of(tmp_path, monkeypatch, ("pull.cuh", "namespace wedge {", "namespace wedge {\n// a note")) == base
     assert _digest_of(tmp_path, monkeypatch, ("common.cuh", "struct wedge_graph {",
                                               "struct wedge_graph {\n    int unused_host_field = 0;")) == base
-    # device code does
-    assert _digest_of(tmp_path, monkeypatch, ("engine.cu", "constexpr unsigned kFull = 0xFFFFFFFFu;",
+    # nor does code of other kernels or of the host side
+    assert _digest_of(tmp_path, monkeypatch, ("xform.cuh", "constexpr unsigned kAppendStage = 256;",
+                                              "constexpr unsigned kAppendStage = 128;")) == base
+    assert _digest_of(tmp_path, monkeypatch, ("engine.cu", "static PullParams pull_params(",
+                                              "static PullParams  pull_params(")) == base
+    assert _digest_of(tmp_path, monkeypatch, ("pull.cuh", "constexpr unsigned long long kSkipVisitedMinChunks",
+                                              "constexpr unsigned long long  kSkipVisitedMinChunks")) == base
+    # the pull's device code does (edits accumulate on the copy: this one last)
+    assert _digest_of(tmp_path, monkeypatch, ("common.cuh", "constexpr unsigned kFull = 0xFFFFFFFFu;",
                                               "constexpr unsigned kFull = 0xFFFFFFFFu + 0u;")) != base
 
 
 def test_committed_ncu_counters_belong_to_the_current_device_code():
-    """TRAFFIC's digest is the current one, so bench.py reports the counters
-    (a change of device code must come with a new capture)."""
-    for key in bench.TRAFFIC:
-        assert bench._traffic(key) is not None, key
+    """Every committed capture's digest is the current one (a change of a
+    kernel's device code must come with a new capture, or its counters go
+    back to pending), so bench.py never reports stale counters."""
+    for key, (val, us, digest) in bench.TRAFFIC.items():
+        if val is None:
+            assert us is None and digest is None, key
+        else:
+            assert digest == bench._kernel_digest(key), key
+            assert bench._traffic(key) == val
