@@ -516,6 +516,7 @@ def main():
     roof = roofline_pr_pull(wedge, torch, G, g, stream, dev, clk.summary())
     roof["share_of_step"] = PR_ITERS * roof["ms"] / ms_per_step
     roof_cc = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
+    balance = transform_balance(wedge, torch, G, g, stream, dev)
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -525,6 +526,7 @@ def main():
                        "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20),
                        "wedge_settings": "autotuned (k, tau) per app: " + json.dumps(tuned)},
             "per_app": per_app, "graph_build_ms": build_ms, "roofline": roof, "roofline_cc_dense_pull": roof_cc,
+            "transform_balance": balance,
             "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
@@ -970,6 +972,65 @@ def transform_case(wedge, torch, G, g, od, stream, dev, frac=0.10, seed=5):
     alg = g.V / 8 + 8 * int(mask.sum()) + 4 * rows + nc / 8 + 4 * entries
     return {"frontier": int(mask.sum()), "row_entries": rows, "list_entries": entries, "ms": t * 1e3,
             "alg_bytes": alg, "alg_gbs": alg / t / 1e9, "entries_per_s": rows / t}
+
+
+def balance_summary(rec, kernel):
+    """Busy and idle shares of one transformation kernel's warps (Fig. 13's
+    division of thread time): a warp is busy from its start to the end of its
+    last piece, idle from then to the kernel's last end; the span runs from
+    the first start to the last end."""
+    r = rec[:, kernel, :].astype(np.float64)
+    start, end, cyc = r[:, 0], r[:, 1], r[:, 2]
+    span = end.max() - start.min()
+    busy = end - start
+    return {"span_us": span / 1e3, "busy_mean_us": busy.mean() / 1e3, "busy_max_us": busy.max() / 1e3,
+            "idle_frac": float(1.0 - busy.sum() / (r.shape[0] * span)) if span > 0 else 0.0,
+            "busy_max_over_mean": float(busy.max() / busy.mean()) if busy.mean() > 0 else 1.0,
+            "cycles_max_over_mean": float(cyc.max() / cyc.mean()) if cyc.mean() > 0 else 1.0}
+
+
+def transform_balance(wedge, torch, G, g, stream, dev):
+    """Load balance of the frontier transformation (Section 5.3, Fig. 13) on
+    two frontiers of the benchmark graph: a seeded random 10% of the vertices
+    and SSSP's frontier after four dense pulls from vertex 0; under the
+    library's schedule (rows cut into 32-entry pieces, balanced expansion)
+    and the paper's (equal slices of the vertex frontier, whole rows per
+    warp).  Per schedule: the call's device time and each kernel's idle
+    share of warp time."""
+    V = g.V
+    words = (V + 31) // 32
+    rng = np.random.default_rng(5)
+    packed = np.packbits(rng.random(V) < 0.10, bitorder="little")
+    packed = np.concatenate([packed, np.zeros((-packed.size) % 4, dtype=np.uint8)])
+    fronts = {"random10": torch.from_numpy(packed.view(np.int32).copy()).to(dev)}
+    vals = torch.full((V,), -1, dtype=torch.int32, device=dev)
+    vals[0] = 0
+    nxt = torch.zeros(words, dtype=torch.int32, device=dev)
+    full = torch.zeros(1, dtype=torch.int64, device=dev)
+    nf = torch.zeros(1, dtype=torch.int32, device=dev)
+    for t in range(4):
+        nxt.zero_()
+        wedge.wedge_pull_iterate(G.handle, "sssp", vals, t, None, None, None, 0, nxt, full, nf)
+    fronts["sssp_iter4"] = nxt.clone()
+    nc = (g.E + 31) // 32
+    clist = torch.empty(nc, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+    for name, bm in fronts.items():
+        res = {"frontier": int(np.unpackbits(bm.cpu().numpy().view(np.uint8)).sum())}
+        for sched in (0, 1):
+            rec = None
+            for _ in range(3):
+                rec = wedge.wedge_frontier_transform_profile(G.handle, bm, 0, sched, clist, cnt)
+            t = _time_launch(torch, stream, lambda: wedge.wedge_frontier_transform_profile(
+                G.handle, bm, 0, sched, clist, cnt), reps=5)
+            kern = {"scan": balance_summary(rec, 0), "expand": balance_summary(rec, 1)} if sched == 0 else \
+                {"slices": balance_summary(rec, 0)}
+            res["library" if sched == 0 else "paper_static_slices"] = {"ms": t * 1e3, "kernels": kern}
+            res["list_entries"] = int(cnt.item())
+        res["speedup_library_vs_paper"] = res["paper_static_slices"]["ms"] / res["library"]["ms"]
+        out[name] = res
+    return out
 
 
 def roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev):

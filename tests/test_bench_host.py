@@ -91,3 +91,16 @@ def test_committed_ncu_counters_belong_to_the_current_device_code():
         else:
             assert digest == bench._kernel_digest(key), key
             assert bench._traffic(key) == val
+
+
+def test_balance_summary_arithmetic():
+    # three warps over a 100 ns span: busy 100, 50 and 10 ns -> idle 1 - 160/300
+    rec = np.zeros((3, 2, 4), dtype=np.uint64)
+    rec[:, 0, 0] = [1000, 1000, 1050]
+    rec[:, 0, 1] = [1100, 1050, 1060]
+    rec[:, 0, 2] = [200, 100, 20]
+    b = bench.balance_summary(rec, 0)
+    assert abs(b["span_us"] - 0.1) < 1e-12
+    assert abs(b["idle_frac"] - (1 - 160 / 300)) < 1e-12
+    assert abs(b["busy_max_over_mean"] - 100 / (160 / 3)) < 1e-12
+    assert abs(b["cycles_max_over_mean"] - 200 / (320 / 3)) < 1e-12
