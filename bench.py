@@ -517,6 +517,7 @@ def main():
     roof["share_of_step"] = PR_ITERS * roof["ms"] / ms_per_step
     roof_cc = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
     balance = transform_balance(wedge, torch, G, g, stream, dev)
+    zindex = compressed_index(wedge, torch, G, g, od, stream, dev, o_sssp)
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -526,7 +527,7 @@ def main():
                        "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20),
                        "wedge_settings": "autotuned (k, tau) per app: " + json.dumps(tuned)},
             "per_app": per_app, "graph_build_ms": build_ms, "roofline": roof, "roofline_cc_dense_pull": roof_cc,
-            "transform_balance": balance,
+            "transform_balance": balance, "compressed_edge_index": zindex,
             "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
@@ -972,6 +973,33 @@ def transform_case(wedge, torch, G, g, od, stream, dev, frac=0.10, seed=5):
     alg = g.V / 8 + 8 * int(mask.sum()) + 4 * rows + nc / 8 + 4 * entries
     return {"frontier": int(mask.sum()), "row_entries": rows, "list_entries": entries, "ms": t * 1e3,
             "alg_bytes": alg, "alg_gbs": alg / t / 1e9, "entries_per_s": rows / t}
+
+
+def compressed_index(wedge, torch, G, g, od, stream, dev, sssp_opts):
+    """The compressed edge index on the benchmark graph: its size against the
+    plain index, its build time, and the 10% transformation and the SSSP run
+    with each index (the transformation's algorithmic bytes count the index
+    entries it reads: 4 per entry plain; header + packed words compressed)."""
+    info0 = wedge.wedge_graph_get_info(G.handle)
+    plain = transform_case(wedge, torch, G, g, od, stream, dev)
+    dist = torch.empty(g.V, dtype=torch.int32, device=dev)
+    t_sssp = _time_launch(torch, stream, lambda: wedge.wedge_run_sssp(G.handle, 0, dist, sssp_opts, False), reps=10)
+    before = wedge.wedge_graph_get_tuning(G.handle)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wedge.wedge_graph_set_tuning(G.handle, before["dense_loader"], before["blocks_per_sm"], 1)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    info1 = wedge.wedge_graph_get_info(G.handle)
+    comp = transform_case(wedge, torch, G, g, od, stream, dev)
+    t_sssp_z = _time_launch(torch, stream, lambda: wedge.wedge_run_sssp(G.handle, 0, dist, sssp_opts, False),
+                            reps=10)
+    wedge.wedge_graph_set_tuning(G.handle, before["dense_loader"], before["blocks_per_sm"], before["edge_index"])
+    ratio = info1["eidx_z_bytes"] / info0["eidx_bytes"]
+    return {"plain_bytes": info0["eidx_bytes"], "compressed_bytes": info1["eidx_z_bytes"], "ratio": ratio,
+            "build_ms": build_ms, "transform10_ms": {"plain": plain["ms"], "compressed": comp["ms"]},
+            "transform10_index_bytes": {"plain": 4 * plain["row_entries"],
+                                        "compressed_est": ratio * 4 * plain["row_entries"]},
+            "sssp_ms": {"plain": t_sssp * 1e3, "compressed": t_sssp_z * 1e3}}
 
 
 def balance_summary(rec, kernel):

@@ -166,11 +166,25 @@ wedge_status wedge_graph_create(uint32_t V, uint64_t E, const uint32_t* d_offset
  *                shared memory with 1D bulk copies (TMA) through a 4-stage
  *                mbarrier pipeline.
  *  blocks_per_sm: pull blocks per SM, 0 = as many as fit.
+ *  edge_index:   0 = the transformation reads the plain edge index (4
+ *                bytes per entry);
+ *                1 = it reads the compressed edge index (Section 4 names
+ *                in-memory compression of the index as a way to cut the
+ *                transformation's memory traffic): each row in ascending
+ *                order, cut into blocks of up to 32 entries that store the
+ *                first entry and the differences between consecutive
+ *                entries at the block's fewest bits.  Built on the device
+ *                the first time it is asked for (synchronously; about
+ *                8 bytes per block of 32 entries plus the packed bits, see
+ *                wedge_graph_info.eidx_z_bytes); needs ceil(E/32) < 2^27.
+ *                Batched runs, the push/pull hybrid and the paper's
+ *                transformation schedule keep the plain index.
  * Changing it drops the graph's cached device-loop graphs. */
 typedef struct {
     uint32_t dense_loader;
     uint32_t blocks_per_sm;
-    uint32_t reserved[6]; /* must be zero */
+    uint32_t edge_index;
+    uint32_t reserved[5]; /* must be zero */
 } wedge_tuning;
 
 wedge_status wedge_graph_set_tuning(wedge_graph_t g, const wedge_tuning* t);
@@ -187,6 +201,10 @@ typedef struct {
     uint64_t eidx_len;    /* edge-index entries */
     uint64_t device_bytes;/* device memory owned by the object */
     int device;
+    uint64_t eidx_bytes;  /* the plain edge index: 4(V+1) + 4 * eidx_len */
+    uint64_t eidx_z_bytes;/* the compressed edge index (block headers, packed
+                           * differences, first block of each row); 0 until
+                           * built (wedge_tuning.edge_index) */
 } wedge_graph_info;
 
 wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out);

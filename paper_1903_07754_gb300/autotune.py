@@ -2,8 +2,9 @@
 
 For one graph and application it times a grid of settings -- Wedge Frontier
 precision k (chunk of 32*2^k edges), fullness threshold tau, dense loader
-(direct streaming loads or bulk-copy staging) and pull blocks per SM -- with
-CUDA events, and returns the fastest.  Every setting computes the same
+(direct streaming loads or bulk-copy staging), pull blocks per SM and the
+edge index the transformation reads (plain or compressed) -- with CUDA
+events, and returns the fastest.  Every setting computes the same
 result (the schedule never changes the fixed point; BFS is level-exact), so
 tuning is safe; `tests/test_gpu_autotune.py` checks that the chosen and
 rejected settings agree bit for bit.  Results can be cached in a JSON file
@@ -18,11 +19,14 @@ import os
 from . import wedge
 
 DEFAULT_GRID = {
-    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
-    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0, 1), "blocks_per_sm": (0,)},
+    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,),
+            "edge_index": (0,)},
+    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
+           "edge_index": (0,)},
+    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
+             "edge_index": (0,)},
     "bfs_batch": {"k": (0, 1, 2, 3, 4), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,),
-                  "blocks_per_sm": (0,)},
+                  "blocks_per_sm": (0,), "edge_index": (0,)},
 }
 
 
@@ -53,9 +57,9 @@ def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
     before = wedge.wedge_graph_get_tuning(handle)
     table = []
     try:
-        for k, tau, loader, bps in itertools.product(grid["k"], grid["tau_bp"], grid["dense_loader"],
-                                                     grid["blocks_per_sm"]):
-            wedge.wedge_graph_set_tuning(handle, loader, bps)
+        for k, tau, loader, bps, ei in itertools.product(grid["k"], grid["tau_bp"], grid["dense_loader"],
+                                                         grid["blocks_per_sm"], grid["edge_index"]):
+            wedge.wedge_graph_set_tuning(handle, loader, bps, ei)
             o = wedge.wedge_default_opts(base_app)
             o.log2_coarsen, o.tau_bp = k, tau
             if app == "bfs":
@@ -66,10 +70,10 @@ def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
                 fns = [lambda r=r: wedge.wedge_run_sssp(handle, r, out, o, False) for r in tune_roots]
             else:
                 fns = [lambda: wedge.wedge_run_bfs_batch(handle, roots, None, nqueries, out, o, False)]
-            table.append({"k": k, "tau_bp": tau, "dense_loader": loader, "blocks_per_sm": bps,
+            table.append({"k": k, "tau_bp": tau, "dense_loader": loader, "blocks_per_sm": bps, "edge_index": ei,
                           "ms": sum(_time(fn, reps) for fn in fns)})
     finally:
-        wedge.wedge_graph_set_tuning(handle, before["dense_loader"], before["blocks_per_sm"])
+        wedge.wedge_graph_set_tuning(handle, before["dense_loader"], before["blocks_per_sm"], before["edge_index"])
     best = min(table, key=lambda r: r["ms"])
     return best, table
 
@@ -77,7 +81,7 @@ def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
 def apply(handle, best):
     """Installs the best setting's tuning on the graph and returns matching
     options for its application."""
-    wedge.wedge_graph_set_tuning(handle, best["dense_loader"], best["blocks_per_sm"])
+    wedge.wedge_graph_set_tuning(handle, best["dense_loader"], best["blocks_per_sm"], best.get("edge_index", 0))
     return best
 
 

@@ -197,6 +197,12 @@ struct wedge_graph {
     int pull_blocks_app[4] = {0, 0, 0, 0};     // direct-load pulls
     int pull_blocks_tma[4] = {0, 0, 0, 0};     // bulk-copy staged dense pulls
     wedge_tuning tuning{};
+    // compressed edge index (built when the tuning asks for it; eidx_z.cu)
+    uint2* zhdr = nullptr;          // per block: {first entry | width << 27, first word}
+    uint32_t* zwords = nullptr;     // packed differences
+    uint32_t* zbo = nullptr;        // V+1: first block of each row
+    uint4* zpieces = nullptr;       // the transformation's pieces in compressed mode
+    uint64_t zblocks = 0, zwords_len = 0, z_bytes = 0;
     int xform_blocks = 0;
     unsigned* slice_ctr = nullptr;  // load-balance study: the paper's schedule's slice counter
     uint32_t last_iters = 0;
@@ -244,6 +250,9 @@ wedge_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, u
 
 // Engine (engine.cu)
 wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s);
+
+// The compressed edge index (eidx_z.cu), built once on request.
+wedge_status build_eidx_z(wedge_graph* g, cudaStream_t s);
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

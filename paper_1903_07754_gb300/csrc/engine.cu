@@ -544,14 +544,14 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
             reinterpret_cast<unsigned*>(P.rec + nit + 1)[threadIdx.x] = 0u;
         if (sparse) {
             if (__ldcg(&P.rec[nit].nlist) == nf)
-                xform_scan_list((nit & 1) ? P.flist[1] : P.flist[0], nf, X.eidx_off, X.pieces, &P.rec[nit].npieces,
+                xform_scan_list((nit & 1) ? P.flist[1] : P.flist[0], nf, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr}, &P.rec[nit].npieces,
                                 gw, nw);
             else
-                xform_scan_words(next, X.V, words, X.eidx_off, X.pieces, &P.rec[nit].npieces, gw, nw);
+                xform_scan_words(next, X.V, words, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr}, &P.rec[nit].npieces, gw, nw);
         }
         if (!grid_sync(bar, &C->status)) break;
         if (sparse)
-            xform_expand_pieces(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
+            xform_expand_pieces<false>(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
                                 &P.rec[nit].nchunks, gw, nw);
         if (!grid_sync(bar, &C->status)) break;
         it = nit;
@@ -873,6 +873,11 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.trace = trace;
     X.wstat = nullptr;
     X.slice_ctr = nullptr;
+    const bool z = g->tuning.edge_index == 1 && g->zpieces;
+    X.zhdr = z ? g->zhdr : nullptr;
+    X.zwords = z ? g->zwords : nullptr;
+    X.zbo = z ? g->zbo : nullptr;
+    X.zpieces = z ? g->zpieces : nullptr;
     return X;
 }
 
@@ -1047,6 +1052,7 @@ static wedge_status build_hybrid_graph(wedge_graph* g, int app) {
         XformParams X = xform_params(g, 0);
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed
         launch_hybrid_body(g, app, P, X, push_params(g), cs);
     }, &g->loop_exec_push[app]);
 }
@@ -1109,6 +1115,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     if (push) {
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed
         const PushParams Q = push_params(g);
         WEDGE_TRY_CUDA(cudaGetLastError());
         if (!trace && g->loop_exec_push[app])
@@ -1158,6 +1165,7 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     P.levels = levels;
     P.Q = Q;
     XformParams X = xform_params(g, 0);
+    X.zhdr = nullptr;  // batched runs read the plain edge index
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);
     launch_xform(g, X, s);
@@ -1548,10 +1556,15 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
 wedge_status wedge_graph_set_tuning(wedge_graph_t g, const wedge_tuning* t) {
     if (!g || !t) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
     if (t->dense_loader > 1) return set_error(WEDGE_ERR_INVALID_ARG, "dense_loader must be 0 or 1");
+    if (t->edge_index > 1) return set_error(WEDGE_ERR_INVALID_ARG, "edge_index must be 0 or 1");
     for (uint32_t r : t->reserved)
         if (r) return set_error(WEDGE_ERR_INVALID_ARG, "reserved tuning fields must be zero");
     DeviceGuard dg(g->device);
     WEDGE_TRY_CUDA(cudaDeviceSynchronize());
+    if (t->edge_index == 1) {
+        WEDGE_TRY(build_eidx_z(g, g->cap_stream));
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(g->cap_stream));
+    }
     g->tuning = *t;
     for (auto& e : g->loop_exec)
         if (e) {

@@ -347,6 +347,10 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->ms_roots);
     dev_free(g->ms_bar);
     dev_free(g->slice_ctr);
+    dev_free(g->zhdr);
+    dev_free(g->zwords);
+    dev_free(g->zbo);
+    dev_free(g->zpieces);
     if (g->ms_exec) cudaGraphExecDestroy(g->ms_exec);
     for (auto& e : g->loop_exec)
         if (e) cudaGraphExecDestroy(e);
@@ -651,6 +655,8 @@ wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out) {
     out->eidx_len = g->eidx_len;
     out->device_bytes = g->device_bytes;
     out->device = g->device;
+    out->eidx_bytes = ((uint64_t)g->V + 1) * 4 + g->eidx_len * 4;
+    out->eidx_z_bytes = g->zpieces ? g->z_bytes : 0;
     return WEDGE_OK;
 }
 

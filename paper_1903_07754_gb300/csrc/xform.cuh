@@ -28,7 +28,13 @@ struct XformParams {
     // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
     unsigned long long* wstat;
     unsigned* slice_ctr;         // the paper's schedule: next frontier slice
+    // compressed edge index (zhdr == nullptr: the plain index)
+    const uint2* zhdr;
+    const uint32_t* zwords;
+    const uint32_t* zbo;
+    uint4* zpieces;
 };
+
 
 // ------------------------------------------------------------------------
 // Transformation (K2), two kernels.
@@ -46,8 +52,26 @@ struct XformParams {
 // entries to pieces[slot0 ...] by all 32 lanes: piece i goes to the lane
 // whose range holds it (binary search over the lanes' offsets), so one long
 // row (a hub's) is written by the whole warp.
-__device__ __forceinline__ void write_pieces(uint2* pieces, unsigned slot0, unsigned total, uint32_t rb, uint32_t rl,
-                                             unsigned excl) {
+// Where the scan writes the pieces: plain pieces {first entry, length}, or,
+// with the compressed edge index, {block header .x, .y, length, 0}.
+struct PieceOut {
+    uint2* pieces;
+    uint4* zpieces;         // non-null: compressed edge index
+    const uint32_t* zbo;    // first block of each row
+    const uint2* zhdr;      // block headers
+};
+
+__device__ __forceinline__ PieceOut piece_out(const XformParams& X) {
+    PieceOut po;
+    po.pieces = X.pieces;
+    po.zpieces = X.zhdr ? X.zpieces : nullptr;
+    po.zbo = X.zbo;
+    po.zhdr = X.zhdr;
+    return po;
+}
+
+__device__ __forceinline__ void write_pieces(const PieceOut& po, unsigned slot0, unsigned total, uint32_t rb,
+                                             uint32_t rl, uint32_t zb, unsigned excl) {
     const unsigned lane = threadIdx.x & 31;
     for (unsigned i0 = 0; i0 < total; i0 += 32) {
         const unsigned i = i0 + lane;
@@ -59,15 +83,24 @@ __device__ __forceinline__ void write_pieces(uint2* pieces, unsigned slot0, unsi
         }
         const uint32_t b = __shfl_sync(kFull, rb, jx);
         const uint32_t l = __shfl_sync(kFull, rl, jx);
-        const unsigned q = (i - __shfl_sync(kFull, excl, jx)) * 32u;
-        if (i < total) pieces[slot0 + i] = make_uint2(b + q, min(32u, l - q));
+        const uint32_t z = __shfl_sync(kFull, zb, jx);
+        const unsigned qi = i - __shfl_sync(kFull, excl, jx);
+        const unsigned q = qi * 32u;
+        if (i < total) {
+            if (po.zpieces) {
+                const uint2 h = __ldg(po.zhdr + z + qi);
+                po.zpieces[slot0 + i] = make_uint4(h.x, h.y, min(32u, l - q), 0u);
+            } else {
+                po.pieces[slot0 + i] = make_uint2(b + q, min(32u, l - q));
+            }
+        }
     }
 }
 
 // Warp-level scan of bitmap words [gw*32, ...) step nw*32: pieces of the
 // active vertices' edge-index rows, one reservation per warp on *npieces.
 __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V, unsigned long long words,
-                                                 const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                 const uint32_t* __restrict__ eidx_off, const PieceOut& po,
                                                  unsigned* npieces, unsigned long long gw, unsigned long long nw) {
     const unsigned lane = threadIdx.x & 31;
     for (unsigned long long base = gw * 32; base < words; base += nw * 32) {
@@ -93,12 +126,13 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
         // one vertex per lane and round: every round's rows go out together
         unsigned rem = word, done = 0;
         while (__any_sync(kFull, rem != 0)) {
-            uint32_t rb = 0, rl = 0;
+            uint32_t rb = 0, rl = 0, zb = 0;
             if (rem) {
                 const uint32_t u = (uint32_t)(wi * 32 + __ffs(rem) - 1);
                 rem &= rem - 1;
                 rb = __ldg(eidx_off + u);
                 rl = __ldg(eidx_off + u + 1) - rb;
+                if (po.zpieces) zb = __ldg(po.zbo + u);
             }
             const unsigned p = (rl + 31u) >> 5;
             unsigned pi = p;
@@ -108,7 +142,7 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
                 if (lane >= (unsigned)d) pi += y;
             }
             const unsigned rt = __shfl_sync(kFull, pi, 31);
-            write_pieces(pieces, slot + done, rt, rb, rl, pi - p);
+            write_pieces(po, slot + done, rt, rb, rl, zb, pi - p);
             done += rt;
         }
     }
@@ -116,16 +150,17 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
 
 // Same as xform_scan_words over an explicit list of n frontier vertices.
 __device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n,
-                                                const uint32_t* __restrict__ eidx_off, uint2* pieces,
+                                                const uint32_t* __restrict__ eidx_off, const PieceOut& po,
                                                 unsigned* npieces, unsigned long long gw, unsigned long long nw) {
     const unsigned lane = threadIdx.x & 31;
     for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
         const unsigned long long i = base + lane;
-        uint32_t rb = 0, rl = 0;
+        uint32_t rb = 0, rl = 0, zb = 0;
         if (i < n) {
             const uint32_t u = __ldcg(list + i);
             rb = __ldg(eidx_off + u);
             rl = __ldg(eidx_off + u + 1) - rb;
+            if (po.zpieces) zb = __ldg(po.zbo + u);
         }
         const unsigned np = (rl + 31u) >> 5;
         unsigned incl = np;
@@ -139,7 +174,7 @@ __device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n
         unsigned slot = 0;
         if (lane == 31) slot = atomicAdd(npieces, total);
         slot = __shfl_sync(kFull, slot, 31);
-        write_pieces(pieces, slot, total, rb, rl, incl - np);
+        write_pieces(po, slot, total, rb, rl, zb, incl - np);
     }
 }
 
@@ -186,7 +221,12 @@ __device__ __forceinline__ void flush_staged(uint32_t* list, unsigned* count, co
     __syncwarp();
 }
 
-__device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigned n, unsigned k,
+// With Z, the pieces are compressed blocks {header .x, .y, length, 0} and
+// each lane decodes its entry: the block's first entry plus the prefix sum
+// of the packed differences over the lanes of its block (a block cut by a
+// round boundary carries its last decoded entry into the next round).
+template <bool Z>
+__device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw,
                                                     uint32_t* stage = nullptr) {
@@ -197,15 +237,26 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
     const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
     for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
         const unsigned long long idx = base + lane;
-        const uint2 pc = (lane < ppt && idx < n) ? __ldcg(pieces + idx) : make_uint2(0u, 0u);
-        unsigned incl = pc.y;
+        const bool have = lane < ppt && idx < n;
+        uint2 pc;        // plain: {first entry, length}; Z: {header .x, header .y}
+        unsigned plen;   // piece length
+        if constexpr (Z) {
+            const uint4 z = have ? __ldcg(static_cast<const uint4*>(pieces_v) + idx) : make_uint4(0u, 0u, 0u, 0u);
+            pc = make_uint2(z.x, z.y);
+            plen = z.z;
+        } else {
+            pc = have ? __ldcg(static_cast<const uint2*>(pieces_v) + idx) : make_uint2(0u, 0u);
+            plen = pc.y;
+        }
+        unsigned incl = plen;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const unsigned y = __shfl_up_sync(kFull, incl, d);
             if (lane >= (unsigned)d) incl += y;
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
-        const unsigned excl = incl - pc.y;
+        const unsigned excl = incl - plen;
+        uint32_t carry = 0;  // Z: last decoded entry of the previous round
         for (unsigned e0 = 0; e0 < total; e0 += 32) {
             const unsigned e = e0 + lane;
             const bool act = e < total;
@@ -224,7 +275,37 @@ __device__ __forceinline__ void xform_expand_pieces(const uint2* pieces, unsigne
             // bits with one atomicOr by the run's last lane; within the
             // run, the first lane holding an entry owns it, and it is fresh
             // if the word did not have its bit before.
-            const uint32_t b = act ? __ldg(eidx + st + (e - ex)) >> k : 0xFFFFFFFFu;
+            uint32_t b;
+            if constexpr (Z) {
+                // st = header .x (first entry | width << 27), .y = first word
+                const unsigned i = e - ex;
+                const unsigned w = st >> 27;
+                const unsigned hy = __shfl_sync(kFull, pc.y, jx);
+                uint32_t x = 0;
+                if (act) {
+                    if (i == 0) {
+                        x = st & 0x7FFFFFFu;
+                    } else if (w) {
+                        const unsigned bit = (i - 1) * w, j = bit >> 5, r = bit & 31u;
+                        unsigned long long two = __ldg(static_cast<const uint32_t*>(eidx) + hy + j);
+                        if (r + w > 32u) two |= (unsigned long long)__ldg(static_cast<const uint32_t*>(eidx) + hy + j + 1) << 32;
+                        x = (uint32_t)(two >> r) & ((1u << w) - 1u);
+                    }
+                }
+                const unsigned jprev = __shfl_up_sync(kFull, jx, 1);
+                const unsigned heads = __ballot_sync(kFull, lane == 0 || jx != jprev);
+                const unsigned rs = 31 - __clz(heads & ((2u << lane) - 1u));
+#pragma unroll
+                for (unsigned d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, x, d);
+                    if (lane >= rs + d) x += y;
+                }
+                if (rs == 0 && __shfl_sync(kFull, i, 0) > 0) x += carry;
+                carry = __shfl_sync(kFull, x, 31);
+                b = act ? x >> k : 0xFFFFFFFFu;
+            } else {
+                b = act ? __ldg(eidx + st + (e - ex)) >> k : 0xFFFFFFFFu;
+            }
             const uint32_t word = b >> 5;
             const uint32_t bit = act ? 1u << (b & 31) : 0u;
             const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
@@ -317,7 +398,7 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
     if (X.standalone_k >= 0) {
         bm = X.bm_in;
         r = X.rec;
-        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X), &r->npieces, tid >> 5, nth >> 5);
         ws.stop(X, tid >> 5, 0);
         return;
     } else {
@@ -328,13 +409,13 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
         r = X.rec + it;
         if (r->mode == 0) return;
         if (r->nlist == r->nfront) {
-            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, X.pieces, &r->npieces,
+            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, piece_out(X), &r->npieces,
                             tid >> 5, nth >> 5);
             return;
         }
         bm = (it & 1) ? X.bm[1] : X.bm[0];
     }
-    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, X.pieces, &r->npieces, tid >> 5, nth >> 5);
+    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X), &r->npieces, tid >> 5, nth >> 5);
 }
 
 __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
@@ -360,7 +441,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     WarpStamp ws;
     ws.start(X);
-    xform_expand_pieces(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+    if (X.zhdr)
+        xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+    else
+        xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
     if (X.standalone_k >= 0) ws.stop(X, gw, 1);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();

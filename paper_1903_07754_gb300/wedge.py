@@ -53,13 +53,13 @@ class wedge_iter_record(ctypes.Structure):
 
 class wedge_tuning(ctypes.Structure):
     _fields_ = [("dense_loader", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("edge_index", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class wedge_graph_info(ctypes.Structure):
     _fields_ = [("V", ctypes.c_uint32), ("nz_dst", ctypes.c_uint32), ("E", ctypes.c_uint64),
                 ("nchunks", ctypes.c_uint64), ("eidx_len", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("eidx_bytes", ctypes.c_uint64), ("eidx_z_bytes", ctypes.c_uint64)]
 
 
 EXPORTS = [
@@ -283,17 +283,18 @@ def wedge_get_trace(handle, cap=1 << 16):
     return [{f: getattr(buf[i], f) for f, _ in wedge_iter_record._fields_} for i in range(min(n.value, cap))]
 
 
-def wedge_graph_set_tuning(handle, dense_loader=0, blocks_per_sm=0):
+def wedge_graph_set_tuning(handle, dense_loader=0, blocks_per_sm=0, edge_index=0):
     t = wedge_tuning()
     t.dense_loader = int(dense_loader)
     t.blocks_per_sm = int(blocks_per_sm)
+    t.edge_index = int(edge_index)
     _check(load().wedge_graph_set_tuning(handle, ctypes.byref(t)))
 
 
 def wedge_graph_get_tuning(handle) -> dict:
     t = wedge_tuning()
     _check(load().wedge_graph_get_tuning(handle, ctypes.byref(t)))
-    return {"dense_loader": t.dense_loader, "blocks_per_sm": t.blocks_per_sm}
+    return {"dense_loader": t.dense_loader, "blocks_per_sm": t.blocks_per_sm, "edge_index": t.edge_index}
 
 
 def wedge_run_bfs_batch(handle, roots, root_query, nqueries, levels, opts=None, want_stats=True, stream=None):
