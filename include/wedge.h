@@ -205,6 +205,8 @@ typedef struct {
     uint64_t eidx_z_bytes;/* the compressed edge index (block headers, packed
                            * differences, first block of each row); 0 until
                            * built (wedge_tuning.edge_index) */
+    uint64_t eidx_z_blocks;/* its blocks (0 until built) */
+    uint64_t eidx_z_words; /* its packed 32-bit words (0 until built) */
 } wedge_graph_info;
 
 wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out);
@@ -213,6 +215,17 @@ wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out);
  * buffers provided by the caller. */
 wedge_status wedge_graph_copy_edge_index(wedge_graph_t g, uint32_t* d_eidx_off, uint32_t* d_eidx,
                                          wedge_stream_t stream);
+
+/* Copies the compressed edge index (built by wedge_graph_set_tuning with
+ * edge_index = 1) into device buffers of the caller: d_zbo[V+1] (first block
+ * of each row; row u's blocks hold its eidx_len entries in ascending order,
+ * 32 per block, the last one ragged), d_zhdr[2 * eidx_z_blocks] (per block:
+ * first entry | w << 27, index of its first word) and
+ * d_zwords[eidx_z_words] (entry i >= 1 of a block minus entry i-1, in w
+ * bits at bit (i-1)*w of the block's words, little-endian).
+ * Errors: INVALID_ARG (NULL, index not built), CUDA. */
+wedge_status wedge_graph_copy_edge_index_z(wedge_graph_t g, uint32_t* d_zbo, uint32_t* d_zhdr, uint32_t* d_zwords,
+                                           wedge_stream_t stream);
 
 /* The frontier transformation (Sections 3.3, 4): from the vertex frontier
  * d_vertex_bitmap (ceil(V/32) words, device) to the Wedge Frontier at

@@ -657,6 +657,22 @@ wedge_status wedge_graph_get_info(wedge_graph_t g, wedge_graph_info* out) {
     out->device = g->device;
     out->eidx_bytes = ((uint64_t)g->V + 1) * 4 + g->eidx_len * 4;
     out->eidx_z_bytes = g->zpieces ? g->z_bytes : 0;
+    out->eidx_z_blocks = g->zpieces ? g->zblocks : 0;
+    out->eidx_z_words = g->zpieces ? g->zwords_len : 0;
+    return WEDGE_OK;
+}
+
+wedge_status wedge_graph_copy_edge_index_z(wedge_graph_t g, uint32_t* d_zbo, uint32_t* d_zhdr, uint32_t* d_zwords,
+                                           wedge_stream_t stream) {
+    if (!g || !d_zbo || !d_zhdr || !d_zwords) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (!g->zpieces) return set_error(WEDGE_ERR_INVALID_ARG, "the compressed edge index is not built");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(d_zbo, g->zbo, ((uint64_t)g->V + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (g->zblocks)
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(d_zhdr, g->zhdr, g->zblocks * sizeof(uint2), cudaMemcpyDeviceToDevice, s));
+    if (g->zwords_len)
+        WEDGE_TRY_CUDA(cudaMemcpyAsync(d_zwords, g->zwords, g->zwords_len * 4, cudaMemcpyDeviceToDevice, s));
     return WEDGE_OK;
 }
 

@@ -256,6 +256,10 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         }
         const unsigned total = __shfl_sync(kFull, incl, 31);
         const unsigned excl = incl - plen;
+        // a task holds at most 32 pieces of at most 32 entries: anything else
+        // is a corrupt piece, skipped rather than walked (its lengths' sum
+        // could wrap the round counter below)
+        if (total > 32u * 32u) continue;
         uint32_t carry = 0;  // Z: last decoded entry of the previous round
         for (unsigned e0 = 0; e0 < total; e0 += 32) {
             const unsigned e = e0 + lane;

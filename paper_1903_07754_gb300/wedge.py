@@ -59,7 +59,8 @@ class wedge_tuning(ctypes.Structure):
 class wedge_graph_info(ctypes.Structure):
     _fields_ = [("V", ctypes.c_uint32), ("nz_dst", ctypes.c_uint32), ("E", ctypes.c_uint64),
                 ("nchunks", ctypes.c_uint64), ("eidx_len", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("device", ctypes.c_int), ("eidx_bytes", ctypes.c_uint64), ("eidx_z_bytes", ctypes.c_uint64)]
+                ("device", ctypes.c_int), ("eidx_bytes", ctypes.c_uint64), ("eidx_z_bytes", ctypes.c_uint64),
+                ("eidx_z_blocks", ctypes.c_uint64), ("eidx_z_words", ctypes.c_uint64)]
 
 
 EXPORTS = [
@@ -70,7 +71,7 @@ EXPORTS = [
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
-    "wedge_frontier_transform_profile",
+    "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "wedge_frontier_transform": (st, [P, P, u32, P, P, P]),
         "wedge_frontier_transform_noalloc": (st, [u32, u64, P, P, P, u32, P, P, P]),
         "wedge_frontier_transform_profile": (st, [P, P, u32, u32, P, P, P, u32, ctypes.POINTER(u32), P]),
+        "wedge_graph_copy_edge_index_z": (st, [P, P, P, P, P]),
         "wedge_pull_iterate": (st, [P, i32, P, u32, P, P, P, u32, P, P, P, P]),
         "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
@@ -188,6 +190,10 @@ def wedge_graph_get_info(handle) -> dict:
 
 def wedge_graph_copy_edge_index(handle, eidx_off, eidx, stream=None):
     _check(load().wedge_graph_copy_edge_index(handle, _ptr(eidx_off), _ptr(eidx), _stream(stream)))
+
+
+def wedge_graph_copy_edge_index_z(handle, zbo, zhdr, zwords, stream=None):
+    _check(load().wedge_graph_copy_edge_index_z(handle, _ptr(zbo), _ptr(zhdr), _ptr(zwords), _stream(stream)))
 
 
 def wedge_frontier_transform(handle, vertex_bitmap, log2_coarsen, chunk_list, chunk_count, stream=None):

@@ -40,6 +40,43 @@ def _transform(G, front, k):
     return np.sort(got)
 
 
+def _decode(zbo, zhdr, zwords, eo):
+    """Rows of the compressed index, decoded on the host from its documented
+    layout (include/wedge.h, wedge_graph_copy_edge_index_z)."""
+    rows = []
+    for u in range(len(eo) - 1):
+        n_row = int(eo[u + 1] - eo[u])
+        out = []
+        for b in range(int(zbo[u]), int(zbo[u + 1])):
+            hx, hy = int(zhdr[2 * b]), int(zhdr[2 * b + 1])
+            w, x = hx >> 27, hx & 0x7FFFFFF
+            n = min(32, n_row - len(out))
+            vals = [x]
+            for i in range(1, n):
+                bit = (i - 1) * w
+                j, r = bit >> 5, bit & 31
+                two = int(zwords[hy + j]) | ((int(zwords[hy + j + 1]) << 32) if hy + j + 1 < len(zwords) else 0)
+                vals.append(vals[-1] + ((two >> r) & ((1 << w) - 1)))
+            out += vals
+        rows.append(out)
+    return rows
+
+
+def test_compressed_index_decodes_to_the_rows(g16, G16):
+    info = wedge.wedge_graph_get_info(G16.handle)
+    zbo = empty_u32(G16.V + 1)
+    zhdr = empty_u32(2 * info["eidx_z_blocks"])
+    zwords = empty_u32(info["eidx_z_words"])
+    wedge.wedge_graph_copy_edge_index_z(G16.handle, zbo, zhdr, zwords)
+    zbo, zhdr, zwords = u32(zbo)[: G16.V + 1], u32(zhdr), u32(zwords)[: info["eidx_z_words"]]
+    eo, ei = oracle.edge_index(g16, 32)
+    nb = (np.diff(eo.astype(np.int64)) + 31) // 32
+    np.testing.assert_array_equal(zbo.astype(np.int64), np.concatenate([[0], np.cumsum(nb)]))
+    rows = _decode(zbo, zhdr, zwords, eo)
+    for u in range(G16.V):
+        assert rows[u] == [int(x) for x in ei[eo[u]:eo[u + 1]]], u
+
+
 def test_compressed_index_is_smaller(G16):
     info = wedge.wedge_graph_get_info(G16.handle)
     assert wedge.wedge_graph_get_tuning(G16.handle)["edge_index"] == 1
