@@ -304,7 +304,8 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
                     const uint32_t y = __shfl_up_sync(kFull, x, d);
                     if (lane >= rs + d) x += y;
                 }
-                if (rs == 0 && __shfl_sync(kFull, i, 0) > 0) x += carry;
+                const unsigned i_lane0 = __shfl_sync(kFull, i, 0);  // by every lane
+                if (rs == 0 && i_lane0 > 0) x += carry;
                 carry = __shfl_sync(kFull, x, 31);
                 b = act ? x >> k : 0xFFFFFFFFu;
             } else {
