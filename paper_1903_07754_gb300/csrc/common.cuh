@@ -75,7 +75,8 @@ struct IterRec {
     unsigned long long t_pull0, t_pull1;    // globaltimer stamps of pull t
     unsigned long long t_xf0, t_xf1;        // and of the transformation for t
     unsigned int nlist;           // F_t vertices written to the frontier list
-    unsigned int pad_;            // (the list is complete iff nlist == nfront)
+                                  // (the list is complete iff nlist == nfront)
+    unsigned int nlong;           // F_t's long edge-index rows listed for the transformation
 };
 static_assert(sizeof(IterRec) == 72, "IterRec layout");
 constexpr int kListCap = 1024;  // frontier-list entries a pull block stages in shared memory
@@ -139,6 +140,7 @@ struct wedge_graph {
     uint32_t* wb = nullptr;        // Wedge Frontier bitmap, ceil(NC/32) words
     uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries
     uint2* pieces = nullptr;       // transformation work pieces
+    uint32_t* longs = nullptr;     // the transformation's long rows (kLongCap entries)
     uint32_t* flist[2] = {nullptr, nullptr};  // frontier vertex lists by iteration parity
     uint32_t* visk = nullptr;      // BFS: visited destinations by index into vid, ceil(NZ/32)+1 words
     wedge::BlockStat* bstat = nullptr;  // per-block results of the last pull

@@ -544,10 +544,10 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
             reinterpret_cast<unsigned*>(P.rec + nit + 1)[threadIdx.x] = 0u;
         if (sparse) {
             if (__ldcg(&P.rec[nit].nlist) == nf)
-                xform_scan_list((nit & 1) ? P.flist[1] : P.flist[0], nf, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr}, &P.rec[nit].npieces,
+                xform_scan_list((nit & 1) ? P.flist[1] : P.flist[0], nf, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr, nullptr, nullptr}, &P.rec[nit].npieces,
                                 gw, nw);
             else
-                xform_scan_words(next, X.V, words, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr}, &P.rec[nit].npieces, gw, nw);
+                xform_scan_words(next, X.V, words, X.eidx_off, PieceOut{X.pieces, nullptr, nullptr, nullptr, nullptr, nullptr}, &P.rec[nit].npieces, gw, nw);
         }
         if (!grid_sync(bar, &C->status)) break;
         if (sparse)
@@ -782,6 +782,7 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, ((NC + 31) / 32 + 1) * 4, s));
     WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->longs, (uint64_t)kLongCap * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[1], (V + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->visk, visk_words(g) * 4));
@@ -873,6 +874,7 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.trace = trace;
     X.wstat = nullptr;
     X.slice_ctr = nullptr;
+    X.longs = g->longs;
     const bool z = g->tuning.edge_index == 1 && g->zpieces;
     X.zhdr = z ? g->zhdr : nullptr;
     X.zwords = z ? g->zwords : nullptr;
@@ -1052,7 +1054,8 @@ static wedge_status build_hybrid_graph(wedge_graph* g, int app) {
         XformParams X = xform_params(g, 0);
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
-        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows
+        X.longs = nullptr;
         launch_hybrid_body(g, app, P, X, push_params(g), cs);
     }, &g->loop_exec_push[app]);
 }
@@ -1115,7 +1118,8 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     if (push) {
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
-        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows
+        X.longs = nullptr;
         const PushParams Q = push_params(g);
         WEDGE_TRY_CUDA(cudaGetLastError());
         if (!trace && g->loop_exec_push[app])
@@ -1165,7 +1169,8 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     P.levels = levels;
     P.Q = Q;
     XformParams X = xform_params(g, 0);
-    X.zhdr = nullptr;  // batched runs read the plain edge index
+    X.zhdr = nullptr;  // batched runs read the plain edge index, all rows as pieces
+    X.longs = nullptr;
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);
     launch_xform(g, X, s);

@@ -28,6 +28,7 @@ struct XformParams {
     // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
     unsigned long long* wstat;
     unsigned* slice_ctr;         // the paper's schedule: next frontier slice
+    uint32_t* longs;             // long rows of the transformation (nullptr: none listed)
     // compressed edge index (zhdr == nullptr: the plain index)
     const uint2* zhdr;
     const uint32_t* zwords;
@@ -54,20 +55,40 @@ struct XformParams {
 // row (a hub's) is written by the whole warp.
 // Where the scan writes the pieces: plain pieces {first entry, length}, or,
 // with the compressed edge index, {block header .x, .y, length, 0}.
+// Rows longer than kLongRow entries are not cut into pieces by the scan
+// (one warp writing a hub's thousands of pieces held the whole scan): they
+// are listed, and their 32-entry units are spread over every warp of the
+// expansion instead.
+constexpr unsigned kLongRow = 32u * 64u;
+constexpr unsigned kLongCap = 1u << 14;  // long rows listed per transformation (more: pieces)
+
 struct PieceOut {
     uint2* pieces;
     uint4* zpieces;         // non-null: compressed edge index
     const uint32_t* zbo;    // first block of each row
     const uint2* zhdr;      // block headers
+    uint32_t* longs;        // non-null: long rows go to this list (kLongCap entries)
+    unsigned* nlong;        // ... and its count
 };
 
-__device__ __forceinline__ PieceOut piece_out(const XformParams& X) {
+__device__ __forceinline__ PieceOut piece_out(const XformParams& X, unsigned* nlong) {
     PieceOut po;
     po.pieces = X.pieces;
     po.zpieces = X.zhdr ? X.zpieces : nullptr;
     po.zbo = X.zbo;
     po.zhdr = X.zhdr;
+    po.longs = X.longs;
+    po.nlong = nlong;
     return po;
+}
+
+// Lists vertex u's row as a long row if it is one and the list has room.
+__device__ __forceinline__ bool list_long_row(const PieceOut& po, uint32_t u, uint32_t len) {
+    if (!po.longs || len <= kLongRow) return false;
+    const unsigned slot = atomicAdd(po.nlong, 1u);
+    if (slot >= kLongCap) return false;
+    po.longs[slot] = u;
+    return true;
 }
 
 __device__ __forceinline__ void write_pieces(const PieceOut& po, unsigned slot0, unsigned total, uint32_t rb,
@@ -108,9 +129,13 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
         uint32_t word = wi < words ? __ldcg(bm + wi) : 0u;
         if (wi == words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
         unsigned np = 0;
+        uint32_t longmask = 0;  // active vertices whose rows went to the long list
         for (uint32_t w = word; w; w &= w - 1) {
-            const uint32_t u = (uint32_t)(wi * 32 + __ffs(w) - 1);
-            np += (__ldg(eidx_off + u + 1) - __ldg(eidx_off + u) + 31u) >> 5;
+            const unsigned bpos = __ffs(w) - 1;
+            const uint32_t u = (uint32_t)(wi * 32 + bpos);
+            const uint32_t len = __ldg(eidx_off + u + 1) - __ldg(eidx_off + u);
+            if (list_long_row(po, u, len)) longmask |= 1u << bpos;
+            else np += (len + 31u) >> 5;
         }
         unsigned incl = np;
 #pragma unroll
@@ -128,10 +153,11 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
         while (__any_sync(kFull, rem != 0)) {
             uint32_t rb = 0, rl = 0, zb = 0;
             if (rem) {
-                const uint32_t u = (uint32_t)(wi * 32 + __ffs(rem) - 1);
+                const unsigned bpos = __ffs(rem) - 1;
+                const uint32_t u = (uint32_t)(wi * 32 + bpos);
                 rem &= rem - 1;
                 rb = __ldg(eidx_off + u);
-                rl = __ldg(eidx_off + u + 1) - rb;
+                rl = ((longmask >> bpos) & 1u) ? 0u : __ldg(eidx_off + u + 1) - rb;
                 if (po.zpieces) zb = __ldg(po.zbo + u);
             }
             const unsigned p = (rl + 31u) >> 5;
@@ -160,6 +186,7 @@ __device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n
             const uint32_t u = __ldcg(list + i);
             rb = __ldg(eidx_off + u);
             rl = __ldg(eidx_off + u + 1) - rb;
+            if (list_long_row(po, u, rl)) rl = 0;
             if (po.zpieces) zb = __ldg(po.zbo + u);
         }
         const unsigned np = (rl + 31u) >> 5;
@@ -221,18 +248,99 @@ __device__ __forceinline__ void flush_staged(uint32_t* list, unsigned* count, co
     __syncwarp();
 }
 
-// With Z, the pieces are compressed blocks {header .x, .y, length, 0} and
-// each lane decodes its entry: the block's first entry plus the prefix sum
-// of the packed differences over the lanes of its block (a block cut by a
-// round boundary carries its last decoded entry into the next round).
+// One round of 32 entries (lane: entry b, act = it holds one): Wedge bitmap
+// bits set with one atomicOr per run of lanes on a word (neighbouring lanes
+// often share a word: always for a hub's row at coarse precision); within a
+// run the first lane holding an entry owns it, fresh if the word did not
+// have its bit before; fresh entries are staged (or appended) to the list.
+__device__ __forceinline__ void expand_round(uint32_t b, bool act, uint32_t* wb, uint32_t* list, unsigned* count,
+                                             uint32_t* stage, unsigned& staged) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t word = b >> 5;
+    const uint32_t bit = act ? 1u << (b & 31) : 0u;
+    const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
+    const unsigned starts = __ballot_sync(kFull, lane == 0 || word != wprev);
+    const unsigned rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
+    const unsigned above = starts & ~(lt_mask | (1u << lane));
+    const unsigned re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
+    uint32_t bits = bit;
+#pragma unroll
+    for (unsigned d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, bits, d);
+        if (lane >= rs + d) bits |= y;
+    }
+    uint32_t old = 0;
+    if (lane == re && act) old = atomicOr(wb + word, bits);
+    old = __shfl_sync(kFull, old, re);
+    const unsigned run = (re == 31 ? kFull : ((2u << re) - 1u)) & ~((1u << rs) - 1u);
+    const unsigned same = __match_any_sync(kFull, b) & run;
+    const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
+    const unsigned m = __ballot_sync(kFull, fresh);
+    if (m && stage) {
+        const unsigned nm = __popc(m);
+        if (staged + nm > kAppendStage) {
+            flush_staged(list, count, stage, staged);
+            staged = 0;
+        }
+        if (fresh) stage[staged + __popc(m & lt_mask)] = b;
+        staged += nm;
+    } else if (m) {
+        const unsigned leader = __ffs(m) - 1;
+        unsigned slot = 0;
+        if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
+        slot = __shfl_sync(kFull, slot, leader);
+        if (fresh) list[slot + __popc(m & lt_mask)] = b;
+    }
+}
+
+// Entry value x of a compressed block's lane: the first entry (i == 0) or
+// the packed difference i (w bits at bit (i-1)*w of the block's words).
+__device__ __forceinline__ uint32_t z_raw(bool act, unsigned i, uint32_t hx, uint32_t hy,
+                                          const uint32_t* __restrict__ zwords) {
+    const unsigned w = hx >> 27;
+    if (!act) return 0u;
+    if (i == 0) return hx & 0x7FFFFFFu;
+    if (!w) return 0u;
+    const unsigned bit = (i - 1) * w, j = bit >> 5, r = bit & 31u;
+    unsigned long long two = __ldg(zwords + hy + j);
+    if (r + w > 32u) two |= (unsigned long long)__ldg(zwords + hy + j + 1) << 32;
+    return (uint32_t)(two >> r) & ((1u << w) - 1u);
+}
+
+// Inclusive sum of x over runs of lanes with equal `key` (the lanes of one
+// block), plus `carry` on the run that starts at lane 0 when that run
+// continues a block from the previous round (cont).
+__device__ __forceinline__ uint32_t z_scan(uint32_t x, unsigned key, bool cont, uint32_t carry) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned kprev = __shfl_up_sync(kFull, key, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || key != kprev);
+    const unsigned rs = 31 - __clz(heads & ((2u << lane) - 1u));
+#pragma unroll
+    for (unsigned d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, d);
+        if (lane >= rs + d) x += y;
+    }
+    if (rs == 0 && cont) x += carry;
+    return x;
+}
+
+// Warp-level expansion of n pieces (and of the long rows): with Z, the
+// pieces are compressed blocks {header .x, .y, length, 0}, and each lane
+// decodes its entry, the block's first entry plus the prefix sum of the
+// packed differences over the block's lanes (a block cut by a round
+// boundary carries its last decoded entry into the next round).  The next
+// round's entries are loaded before the current round's atomics.
 template <bool Z>
 __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw,
-                                                    uint32_t* stage = nullptr) {
+                                                    uint32_t* stage = nullptr, const uint32_t* longs = nullptr,
+                                                    unsigned nlong = 0, const uint32_t* __restrict__ eidx_off = nullptr,
+                                                    const uint32_t* __restrict__ zbo = nullptr,
+                                                    const uint2* __restrict__ zhdr = nullptr) {
     unsigned staged = 0;  // warp-uniform
     const unsigned lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned long long per = (unsigned long long)n / nw;
     const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
     for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
@@ -260,8 +368,9 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         // is a corrupt piece, skipped rather than walked (its lengths' sum
         // could wrap the round counter below)
         if (total > 32u * 32u) continue;
-        uint32_t carry = 0;  // Z: last decoded entry of the previous round
-        for (unsigned e0 = 0; e0 < total; e0 += 32) {
+        // entry value of every lane in the round starting at e0 (Z: decoded,
+        // `carry` = the previous round's lane-31 value)
+        auto fetch = [&](unsigned e0, uint32_t carry) -> uint32_t {
             const unsigned e = e0 + lane;
             const bool act = e < total;
             unsigned jx = 0;
@@ -273,79 +382,44 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
             }
             const unsigned st = __shfl_sync(kFull, pc.x, jx);
             const unsigned ex = __shfl_sync(kFull, excl, jx);
-            // Lanes are runs of consecutive rows' entries, so neighbouring
-            // lanes often hit the same bitmap word (always for a hub's row
-            // at coarse precision).  Each run of lanes on one word sets its
-            // bits with one atomicOr by the run's last lane; within the
-            // run, the first lane holding an entry owns it, and it is fresh
-            // if the word did not have its bit before.
-            uint32_t b;
             if constexpr (Z) {
-                // st = header .x (first entry | width << 27), .y = first word
                 const unsigned i = e - ex;
-                const unsigned w = st >> 27;
                 const unsigned hy = __shfl_sync(kFull, pc.y, jx);
-                uint32_t x = 0;
-                if (act) {
-                    if (i == 0) {
-                        x = st & 0x7FFFFFFu;
-                    } else if (w) {
-                        const unsigned bit = (i - 1) * w, j = bit >> 5, r = bit & 31u;
-                        unsigned long long two = __ldg(static_cast<const uint32_t*>(eidx) + hy + j);
-                        if (r + w > 32u) two |= (unsigned long long)__ldg(static_cast<const uint32_t*>(eidx) + hy + j + 1) << 32;
-                        x = (uint32_t)(two >> r) & ((1u << w) - 1u);
-                    }
-                }
-                const unsigned jprev = __shfl_up_sync(kFull, jx, 1);
-                const unsigned heads = __ballot_sync(kFull, lane == 0 || jx != jprev);
-                const unsigned rs = 31 - __clz(heads & ((2u << lane) - 1u));
-#pragma unroll
-                for (unsigned d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFull, x, d);
-                    if (lane >= rs + d) x += y;
-                }
                 const unsigned i_lane0 = __shfl_sync(kFull, i, 0);  // by every lane
-                if (rs == 0 && i_lane0 > 0) x += carry;
-                carry = __shfl_sync(kFull, x, 31);
-                b = act ? x >> k : 0xFFFFFFFFu;
+                return z_scan(z_raw(act, i, st, hy, eidx), jx, i_lane0 > 0, carry);
             } else {
-                b = act ? __ldg(eidx + st + (e - ex)) >> k : 0xFFFFFFFFu;
+                return act ? __ldg(eidx + st + (e - ex)) : 0u;
             }
-            const uint32_t word = b >> 5;
-            const uint32_t bit = act ? 1u << (b & 31) : 0u;
-            const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
-            const unsigned starts = __ballot_sync(kFull, lane == 0 || word != wprev);
-            const unsigned rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
-            const unsigned above = starts & ~(lt_mask | (1u << lane));
-            const unsigned re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
-            uint32_t bits = bit;
-#pragma unroll
-            for (unsigned d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, bits, d);
-                if (lane >= rs + d) bits |= y;
+        };
+        uint32_t x = fetch(0, 0u);
+        for (unsigned e0 = 0; e0 < total; e0 += 32) {
+            uint32_t xn = 0;
+            if (e0 + 32 < total) xn = fetch(e0 + 32, __shfl_sync(kFull, x, 31));
+            const bool act = e0 + lane < total;
+            expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
+            x = xn;
+        }
+    }
+    // long rows: unit q of the i-th long row is unit U_i + q of their
+    // concatenation, taken by warp (U_i + q) mod nw
+    unsigned long long U = 0;
+    for (unsigned r = 0; r < nlong; ++r) {
+        const uint32_t u = __ldcg(longs + r);
+        const uint32_t rb = __ldg(eidx_off + u), len = __ldg(eidx_off + u + 1) - rb;
+        const unsigned long long units = (len + 31u) >> 5;
+        unsigned long long q = (gw + nw - (U % nw)) % nw;
+        U += units;
+        for (; q < units; q += nw) {
+            const unsigned n_u = min(32u, len - (unsigned)q * 32u);
+            const bool act = lane < n_u;
+            uint32_t x;
+            if constexpr (Z) {
+                const uint2 h = __ldg(zhdr + __ldg(zbo + u) + q);
+                x = z_scan(z_raw(act, lane, h.x, h.y, eidx), 0u, false, 0u);
+            } else {
+                x = act ? __ldg(eidx + rb + q * 32u + lane) : 0u;
             }
-            uint32_t old = 0;
-            if (lane == re && act) old = atomicOr(wb + word, bits);
-            old = __shfl_sync(kFull, old, re);
-            const unsigned run = (re == 31 ? kFull : ((2u << re) - 1u)) & ~((1u << rs) - 1u);
-            const unsigned same = __match_any_sync(kFull, b) & run;
-            const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
-            const unsigned m = __ballot_sync(kFull, fresh);
-            if (m && stage) {
-                const unsigned nm = __popc(m);
-                if (staged + nm > kAppendStage) {
-                    flush_staged(list, count, stage, staged);
-                    staged = 0;
-                }
-                if (fresh) stage[staged + __popc(m & lt_mask)] = b;
-                staged += nm;
-            } else if (m) {
-                const unsigned leader = __ffs(m) - 1;
-                unsigned slot = 0;
-                if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
-                slot = __shfl_sync(kFull, slot, leader);
-                if (fresh) list[slot + __popc(m & lt_mask)] = b;
-            }
+            expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
         }
     }
     if (stage && staged) flush_staged(list, count, stage, staged);
@@ -403,7 +477,8 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
     if (X.standalone_k >= 0) {
         bm = X.bm_in;
         r = X.rec;
-        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X), &r->npieces, tid >> 5, nth >> 5);
+        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X, &r->nlong), &r->npieces, tid >> 5,
+                         nth >> 5);
         ws.stop(X, tid >> 5, 0);
         return;
     } else {
@@ -414,13 +489,14 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
         r = X.rec + it;
         if (r->mode == 0) return;
         if (r->nlist == r->nfront) {
-            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, piece_out(X), &r->npieces,
+            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, piece_out(X, &r->nlong),
+                            &r->npieces,
                             tid >> 5, nth >> 5);
             return;
         }
         bm = (it & 1) ? X.bm[1] : X.bm[0];
     }
-    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X), &r->npieces, tid >> 5, nth >> 5);
+    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X, &r->nlong), &r->npieces, tid >> 5, nth >> 5);
 }
 
 __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
@@ -428,8 +504,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     unsigned n, k;
     unsigned* count;
     unsigned it = 0;
+    unsigned nlong;
     if (X.standalone_k >= 0) {
         n = __ldcg(&X.rec[0].npieces);
+        nlong = __ldcg(&X.rec[0].nlong);
         k = (unsigned)X.standalone_k;
         count = X.count_out;
     } else {
@@ -438,18 +516,23 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
         const IterRec* r = X.rec + it;
         if (r->mode == 0) return;
         n = r->npieces;
+        nlong = r->nlong;
         k = r->k;
         count = &X.rec[it].nchunks;
     }
+    if (!X.longs) nlong = 0;
+    if (nlong > kLongCap) nlong = kLongCap;
     __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     WarpStamp ws;
     ws.start(X);
     if (X.zhdr)
-        xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+        xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
+                                  X.longs, nlong, X.eidx_off, X.zbo, X.zhdr);
     else
-        xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5]);
+        xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
+                                   X.longs, nlong, X.eidx_off);
     if (X.standalone_k >= 0) ws.stop(X, gw, 1);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
