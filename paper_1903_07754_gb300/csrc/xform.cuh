@@ -60,7 +60,7 @@ struct XformParams {
 // are listed, and their 32-entry units are spread over every warp of the
 // expansion instead.
 constexpr unsigned kLongRow = 32u * 64u;
-constexpr unsigned kLongCap = 1u << 14;  // long rows listed per transformation (more: pieces)
+constexpr unsigned kLongCap = 2048;  // long rows listed per transformation (more: pieces)
 
 struct PieceOut {
     uint2* pieces;
@@ -82,13 +82,32 @@ __device__ __forceinline__ PieceOut piece_out(const XformParams& X, unsigned* nl
     return po;
 }
 
-// Lists vertex u's row as a long row if it is one and the list has room.
-__device__ __forceinline__ bool list_long_row(const PieceOut& po, uint32_t u, uint32_t len) {
-    if (!po.longs || len <= kLongRow) return false;
-    const unsigned slot = atomicAdd(po.nlong, 1u);
-    if (slot >= kLongCap) return false;
-    po.longs[slot] = u;
-    return true;
+// Reserves list slots for the long rows a lane holds (the vertices at the
+// bits of `cand` in bitmap word wi), one atomic per warp; rows that find no
+// slot (the list is full) stay pieces.  Returns the bits of the rows listed.
+__device__ __forceinline__ uint32_t list_long_rows(const PieceOut& po, unsigned long long wi, uint32_t cand) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned nl = __popc(cand);
+    unsigned incl = nl;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (unsigned)d) incl += y;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    if (!total) return 0u;
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(po.nlong, total);
+    base = __shfl_sync(kFull, base, 31);
+    unsigned slot = base + incl - nl;
+    uint32_t listed = 0;
+    for (uint32_t c = cand; c; c &= c - 1, ++slot) {
+        if (slot >= kLongCap) break;
+        const unsigned bpos = __ffs(c) - 1;
+        po.longs[slot] = (uint32_t)(wi * 32 + bpos);
+        listed |= 1u << bpos;
+    }
+    return listed;
 }
 
 __device__ __forceinline__ void write_pieces(const PieceOut& po, unsigned slot0, unsigned total, uint32_t rb,
@@ -128,14 +147,20 @@ __device__ __forceinline__ void xform_scan_words(const uint32_t* bm, uint32_t V,
         const unsigned long long wi = base + lane;
         uint32_t word = wi < words ? __ldcg(bm + wi) : 0u;
         if (wi == words - 1 && (V & 31)) word &= (1u << (V & 31)) - 1u;
+        uint32_t cand = 0;  // active vertices with long rows
         unsigned np = 0;
-        uint32_t longmask = 0;  // active vertices whose rows went to the long list
         for (uint32_t w = word; w; w &= w - 1) {
             const unsigned bpos = __ffs(w) - 1;
             const uint32_t u = (uint32_t)(wi * 32 + bpos);
             const uint32_t len = __ldg(eidx_off + u + 1) - __ldg(eidx_off + u);
-            if (list_long_row(po, u, len)) longmask |= 1u << bpos;
+            if (po.longs && len > kLongRow) cand |= 1u << bpos;
             else np += (len + 31u) >> 5;
+        }
+        // rows that went to the long list; the others stay pieces
+        const uint32_t longmask = (po.longs && __any_sync(kFull, cand != 0)) ? list_long_rows(po, wi, cand) : 0u;
+        for (uint32_t c = cand & ~longmask; c; c &= c - 1) {
+            const uint32_t u = (uint32_t)(wi * 32 + __ffs(c) - 1);
+            np += (__ldg(eidx_off + u + 1) - __ldg(eidx_off + u) + 31u) >> 5;
         }
         unsigned incl = np;
 #pragma unroll
@@ -182,12 +207,26 @@ __device__ __forceinline__ void xform_scan_list(const uint32_t* list, unsigned n
     for (unsigned long long base = gw * 32; base < n; base += nw * 32) {
         const unsigned long long i = base + lane;
         uint32_t rb = 0, rl = 0, zb = 0;
+        uint32_t u = 0;
         if (i < n) {
-            const uint32_t u = __ldcg(list + i);
+            u = __ldcg(list + i);
             rb = __ldg(eidx_off + u);
             rl = __ldg(eidx_off + u + 1) - rb;
-            if (list_long_row(po, u, rl)) rl = 0;
             if (po.zpieces) zb = __ldg(po.zbo + u);
+        }
+        if (po.longs) {
+            const bool lg = rl > kLongRow;
+            const unsigned lm = __ballot_sync(kFull, lg);
+            if (lm) {
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(po.nlong, (unsigned)__popc(lm));
+                base = __shfl_sync(kFull, base, 0);
+                const unsigned slot = base + __popc(lm & ((1u << lane) - 1u));
+                if (lg && slot < kLongCap) {
+                    po.longs[slot] = u;
+                    rl = 0;
+                }
+            }
         }
         const unsigned np = (rl + 31u) >> 5;
         unsigned incl = np;
@@ -335,8 +374,9 @@ template <bool Z>
 __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw,
-                                                    uint32_t* stage = nullptr, const uint32_t* longs = nullptr,
-                                                    unsigned nlong = 0, const uint32_t* __restrict__ eidx_off = nullptr,
+                                                    uint32_t* stage = nullptr, const uint32_t* s_lu = nullptr,
+                                                    const uint32_t* s_lpre = nullptr, unsigned nlong = 0,
+                                                    const uint32_t* __restrict__ eidx_off = nullptr,
                                                     const uint32_t* __restrict__ zbo = nullptr,
                                                     const uint2* __restrict__ zhdr = nullptr) {
     unsigned staged = 0;  // warp-uniform
@@ -400,27 +440,30 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
             x = xn;
         }
     }
-    // long rows: unit q of the i-th long row is unit U_i + q of their
-    // concatenation, taken by warp (U_i + q) mod nw
-    unsigned long long U = 0;
-    for (unsigned r = 0; r < nlong; ++r) {
-        const uint32_t u = __ldcg(longs + r);
-        const uint32_t rb = __ldg(eidx_off + u), len = __ldg(eidx_off + u + 1) - rb;
-        const unsigned long long units = (len + 31u) >> 5;
-        unsigned long long q = (gw + nw - (U % nw)) % nw;
-        U += units;
-        for (; q < units; q += nw) {
-            const unsigned n_u = min(32u, len - (unsigned)q * 32u);
-            const bool act = lane < n_u;
-            uint32_t x;
-            if constexpr (Z) {
-                const uint2 h = __ldg(zhdr + __ldg(zbo + u) + q);
-                x = z_scan(z_raw(act, lane, h.x, h.y, eidx), 0u, false, 0u);
-            } else {
-                x = act ? __ldg(eidx + rb + q * 32u + lane) : 0u;
-            }
-            expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
+    // long rows: the block's table holds their vertices (s_lu) and the
+    // exclusive prefix of their 32-entry unit counts (s_lpre); unit t of the
+    // concatenation goes to warp t mod nw
+    const unsigned long long lunits = nlong ? s_lpre[nlong] : 0ull;
+    for (unsigned long long t = gw; t < lunits; t += nw) {
+        unsigned lo = 0, hi = nlong;  // s_lpre[lo] <= t < s_lpre[hi]
+        while (hi - lo > 1) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (s_lpre[mid] <= t) lo = mid;
+            else hi = mid;
         }
+        const uint32_t u = s_lu[lo];
+        const unsigned q = (unsigned)(t - s_lpre[lo]);
+        const uint32_t rb = __ldg(eidx_off + u), len = __ldg(eidx_off + u + 1) - rb;
+        const unsigned n_u = min(32u, len - q * 32u);
+        const bool act = lane < n_u;
+        uint32_t x;
+        if constexpr (Z) {
+            const uint2 h = __ldg(zhdr + __ldg(zbo + u) + q);
+            x = z_scan(z_raw(act, lane, h.x, h.y, eidx), 0u, false, 0u);
+        } else {
+            x = act ? __ldg(eidx + rb + q * 32u + lane) : 0u;
+        }
+        expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
     }
     if (stage && staged) flush_staged(list, count, stage, staged);
 }
@@ -523,16 +566,55 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     if (!X.longs) nlong = 0;
     if (nlong > kLongCap) nlong = kLongCap;
     __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
+    // the long rows' table: vertices and the exclusive prefix of their unit
+    // counts (each thread sums a run of kLongCap / blockDim entries)
+    __shared__ uint32_t s_lu[kLongCap];
+    __shared__ uint32_t s_lpre[kLongCap + 1];
+    __shared__ uint32_t s_part[kXformThreads / 32];
+    if (nlong) {
+        constexpr unsigned per = kLongCap / kXformThreads;
+        const unsigned r0 = threadIdx.x * per;
+        uint32_t sum = 0, cnt[per];
+#pragma unroll
+        for (unsigned j = 0; j < per; ++j) {
+            cnt[j] = 0;
+            if (r0 + j < nlong) {
+                const uint32_t u = __ldcg(X.longs + r0 + j);
+                s_lu[r0 + j] = u;
+                cnt[j] = (__ldg(X.eidx_off + u + 1) - __ldg(X.eidx_off + u) + 31u) >> 5;
+            }
+            sum += cnt[j];
+        }
+        const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        if (lane == 31) s_part[warp] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (unsigned w = 0; w < warp; ++w) wbase += s_part[w];
+        uint32_t run = wbase + incl - sum;
+#pragma unroll
+        for (unsigned j = 0; j < per; ++j) {
+            if (r0 + j <= nlong) s_lpre[r0 + j] = run;
+            run += cnt[j];
+        }
+        if (threadIdx.x == kXformThreads - 1 && nlong == kLongCap) s_lpre[kLongCap] = run;
+        __syncthreads();
+    }
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     WarpStamp ws;
     ws.start(X);
     if (X.zhdr)
         xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                  X.longs, nlong, X.eidx_off, X.zbo, X.zhdr);
+                                  s_lu, s_lpre, nlong, X.eidx_off, X.zbo, X.zhdr);
     else
         xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                   X.longs, nlong, X.eidx_off);
+                                   s_lu, s_lpre, nlong, X.eidx_off);
     if (X.standalone_k >= 0) ws.stop(X, gw, 1);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
