@@ -287,34 +287,52 @@ __device__ __forceinline__ void flush_staged(uint32_t* list, unsigned* count, co
     __syncwarp();
 }
 
-// One round of 32 entries (lane: entry b, act = it holds one): Wedge bitmap
-// bits set with one atomicOr per run of lanes on a word (neighbouring lanes
-// often share a word: always for a hub's row at coarse precision); within a
-// run the first lane holding an entry owns it, fresh if the word did not
-// have its bit before; fresh entries are staged (or appended) to the list.
-__device__ __forceinline__ void expand_round(uint32_t b, bool act, uint32_t* wb, uint32_t* list, unsigned* count,
-                                             uint32_t* stage, unsigned& staged) {
+// One round of 32 entries (lane: entry b, act = it holds one), in two
+// halves so that a warp keeps two rounds' atomics in flight:
+//  round_issue: Wedge bitmap bits set with one atomicOr per run of lanes on
+//    a word (neighbouring lanes often share a word: always for a hub's row
+//    at coarse precision);
+//  round_finish: within a run the first lane holding an entry owns it, fresh
+//    if the word did not have its bit before; fresh entries are staged (or
+//    appended) to the list.
+struct Round {
+    uint32_t b, bit, old;
+    unsigned rs, re;
+    bool act;
+};
+
+__device__ __forceinline__ Round round_issue(uint32_t b, bool act, uint32_t* wb) {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    Round r;
+    r.b = b;
+    r.act = act;
     const uint32_t word = b >> 5;
-    const uint32_t bit = act ? 1u << (b & 31) : 0u;
+    r.bit = act ? 1u << (b & 31) : 0u;
     const uint32_t wprev = __shfl_up_sync(kFull, word, 1);
     const unsigned starts = __ballot_sync(kFull, lane == 0 || word != wprev);
-    const unsigned rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
+    r.rs = 31 - __clz(starts & (lt_mask | (1u << lane)));      // run start
     const unsigned above = starts & ~(lt_mask | (1u << lane));
-    const unsigned re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
-    uint32_t bits = bit;
+    r.re = above ? (unsigned)__ffs(above) - 2 : 31u;           // run end
+    uint32_t bits = r.bit;
 #pragma unroll
     for (unsigned d = 1; d < 32; d <<= 1) {
         const uint32_t y = __shfl_up_sync(kFull, bits, d);
-        if (lane >= rs + d) bits |= y;
+        if (lane >= r.rs + d) bits |= y;
     }
-    uint32_t old = 0;
-    if (lane == re && act) old = atomicOr(wb + word, bits);
-    old = __shfl_sync(kFull, old, re);
-    const unsigned run = (re == 31 ? kFull : ((2u << re) - 1u)) & ~((1u << rs) - 1u);
-    const unsigned same = __match_any_sync(kFull, b) & run;
-    const bool fresh = act && (unsigned)(__ffs(same) - 1) == lane && !(old & bit);
+    r.old = 0;
+    if (lane == r.re && act) r.old = atomicOr(wb + word, bits);
+    return r;
+}
+
+__device__ __forceinline__ void round_finish(const Round& r, uint32_t* list, unsigned* count, uint32_t* stage,
+                                             unsigned& staged) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t old = __shfl_sync(kFull, r.old, r.re);
+    const unsigned run = (r.re == 31 ? kFull : ((2u << r.re) - 1u)) & ~((1u << r.rs) - 1u);
+    const unsigned same = __match_any_sync(kFull, r.b) & run;
+    const bool fresh = r.act && (unsigned)(__ffs(same) - 1) == lane && !(old & r.bit);
     const unsigned m = __ballot_sync(kFull, fresh);
     if (m && stage) {
         const unsigned nm = __popc(m);
@@ -322,14 +340,14 @@ __device__ __forceinline__ void expand_round(uint32_t b, bool act, uint32_t* wb,
             flush_staged(list, count, stage, staged);
             staged = 0;
         }
-        if (fresh) stage[staged + __popc(m & lt_mask)] = b;
+        if (fresh) stage[staged + __popc(m & lt_mask)] = r.b;
         staged += nm;
     } else if (m) {
         const unsigned leader = __ffs(m) - 1;
         unsigned slot = 0;
         if (lane == leader) slot = atomicAdd(count, (unsigned)__popc(m));
         slot = __shfl_sync(kFull, slot, leader);
-        if (fresh) list[slot + __popc(m & lt_mask)] = b;
+        if (fresh) list[slot + __popc(m & lt_mask)] = r.b;
     }
 }
 
@@ -431,19 +449,25 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
                 return act ? __ldg(eidx + st + (e - ex)) : 0u;
             }
         };
+        // round r's atomics are issued before round r - 1's results are used
         uint32_t x = fetch(0, 0u);
+        Round pend;
         for (unsigned e0 = 0; e0 < total; e0 += 32) {
+            const bool act = e0 + lane < total;
+            const Round cur = round_issue(act ? x >> k : 0xFFFFFFFFu, act, wb);
             uint32_t xn = 0;
             if (e0 + 32 < total) xn = fetch(e0 + 32, __shfl_sync(kFull, x, 31));
-            const bool act = e0 + lane < total;
-            expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
+            if (e0) round_finish(pend, list, count, stage, staged);
+            pend = cur;
             x = xn;
         }
+        if (total) round_finish(pend, list, count, stage, staged);
     }
     // long rows: the block's table holds their vertices (s_lu) and the
     // exclusive prefix of their 32-entry unit counts (s_lpre); unit t of the
     // concatenation goes to warp t mod nw
     const unsigned long long lunits = nlong ? s_lpre[nlong] : 0ull;
+    Round lpend;
     for (unsigned long long t = gw; t < lunits; t += nw) {
         unsigned lo = 0, hi = nlong;  // s_lpre[lo] <= t < s_lpre[hi]
         while (hi - lo > 1) {
@@ -463,8 +487,11 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         } else {
             x = act ? __ldg(eidx + rb + q * 32u + lane) : 0u;
         }
-        expand_round(act ? x >> k : 0xFFFFFFFFu, act, wb, list, count, stage, staged);
+        const Round cur = round_issue(act ? x >> k : 0xFFFFFFFFu, act, wb);
+        if (t != gw) round_finish(lpend, list, count, stage, staged);
+        lpend = cur;
     }
+    if (gw < lunits) round_finish(lpend, list, count, stage, staged);
     if (stage && staged) flush_staged(list, count, stage, staged);
 }
 
