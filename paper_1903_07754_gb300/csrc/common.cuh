@@ -141,6 +141,7 @@ struct wedge_graph {
     uint32_t* clist = nullptr;     // Wedge Frontier list, NC entries
     uint2* pieces = nullptr;       // transformation work pieces
     uint32_t* longs = nullptr;     // the transformation's long rows (kLongCap entries)
+    unsigned* xf_task = nullptr;   // the expansion's task counter
     uint32_t* flist[2] = {nullptr, nullptr};  // frontier vertex lists by iteration parity
     uint32_t* visk = nullptr;      // BFS: visited destinations by index into vid, ceil(NZ/32)+1 words
     wedge::BlockStat* bstat = nullptr;  // per-block results of the last pull

@@ -783,6 +783,7 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
     WEDGE_TRY(dev_alloc(g, (void**)&g->longs, (uint64_t)kLongCap * 4));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->xf_task, 16));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[1], (V + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->visk, visk_words(g) * 4));
@@ -875,6 +876,7 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.wstat = nullptr;
     X.slice_ctr = nullptr;
     X.longs = g->longs;
+    X.task_ctr = g->xf_task;
     const bool z = g->tuning.edge_index == 1 && g->zpieces;
     X.zhdr = z ? g->zhdr : nullptr;
     X.zwords = z ? g->zwords : nullptr;

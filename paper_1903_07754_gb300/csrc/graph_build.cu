@@ -328,6 +328,7 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->clist);
     dev_free(g->pieces);
     dev_free(g->longs);
+    dev_free(g->xf_task);
     dev_free(g->flist[0]);
     dev_free(g->flist[1]);
     dev_free(g->visk);

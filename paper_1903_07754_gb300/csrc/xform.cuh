@@ -29,6 +29,7 @@ struct XformParams {
     unsigned long long* wstat;
     unsigned* slice_ctr;         // the paper's schedule: next frontier slice
     uint32_t* longs;             // long rows of the transformation (nullptr: none listed)
+    unsigned* task_ctr;          // the expansion's next task (zeroed by the scan; nullptr: static tasks)
     // compressed edge index (zhdr == nullptr: the plain index)
     const uint2* zhdr;
     const uint32_t* zwords;
@@ -396,12 +397,24 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
                                                     const uint32_t* s_lpre = nullptr, unsigned nlong = 0,
                                                     const uint32_t* __restrict__ eidx_off = nullptr,
                                                     const uint32_t* __restrict__ zbo = nullptr,
-                                                    const uint2* __restrict__ zhdr = nullptr) {
+                                                    const uint2* __restrict__ zhdr = nullptr,
+                                                    unsigned* task_ctr = nullptr) {
     unsigned staged = 0;  // warp-uniform
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long per = (unsigned long long)n / nw;
     const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
-    for (unsigned long long base = gw * ppt; base < n; base += nw * ppt) {
+    // tasks of ppt pieces: taken from *task_ctr (zeroed by the scan) as
+    // warps become free, or else task gw, gw + nw, ...
+    unsigned long long task = gw;
+    for (;;) {
+        if (task_ctr) {
+            unsigned t = 0;
+            if (lane == 0) t = atomicAdd(task_ctr, 1u);
+            task = __shfl_sync(kFull, t, 0);
+        }
+        const unsigned long long base = task * ppt;
+        if (base >= n) break;
+        task += nw;
         const unsigned long long idx = base + lane;
         const bool have = lane < ppt && idx < n;
         uint2 pc;        // plain: {first entry, length}; Z: {header .x, header .y}
@@ -544,6 +557,7 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
     const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
     WarpStamp ws;
     ws.start(X);
+    if (X.task_ctr && tid == 0) *X.task_ctr = 0u;  // the expansion after this kernel takes tasks from it
     if (X.standalone_k >= 0) {
         bm = X.bm_in;
         r = X.rec;
@@ -638,10 +652,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     ws.start(X);
     if (X.zhdr)
         xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                  s_lu, s_lpre, nlong, X.eidx_off, X.zbo, X.zhdr);
+                                  s_lu, s_lpre, nlong, X.eidx_off, X.zbo, X.zhdr, X.task_ctr);
     else
         xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                   s_lu, s_lpre, nlong, X.eidx_off);
+                                   s_lu, s_lpre, nlong, X.eidx_off, nullptr, nullptr, X.task_ctr);
     if (X.standalone_k >= 0) ws.stop(X, gw, 1);
     if (X.trace && X.standalone_k < 0) {
         __syncthreads();
