@@ -200,6 +200,13 @@ struct wedge_graph {
     int pull_blocks_app[4] = {0, 0, 0, 0};     // direct-load pulls
     int pull_blocks_tma[4] = {0, 0, 0, 0};     // bulk-copy staged dense pulls
     wedge_tuning tuning{};
+    // edge index in 8-edge units (the finer precisions; built on first use)
+    uint32_t* eidx8_off = nullptr;
+    uint32_t* eidx8 = nullptr;
+    uint64_t eidx8_len = 0, npieces8_max = 0;
+    uint64_t wb_words = 0;          // Wedge bitmap words allocated
+    uint64_t clist_cap = 0;         // Wedge list entries allocated
+    uint64_t pieces_cap = 0;        // work pieces allocated
     // compressed edge index (built when the tuning asks for it; eidx_z.cu)
     uint2* zhdr = nullptr;          // per block: {first entry | width << 27, first word}
     uint32_t* zwords = nullptr;     // packed differences
@@ -256,6 +263,8 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s);
 
 // The compressed edge index (eidx_z.cu), built once on request.
 wedge_status build_eidx_z(wedge_graph* g, cudaStream_t s);
+// The edge index in 8-edge units (graph_build.cu), built once on request.
+wedge_status build_eidx8(wedge_graph* g, cudaStream_t s);
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

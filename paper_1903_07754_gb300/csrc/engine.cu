@@ -782,6 +782,9 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, ((NC + 31) / 32 + 1) * 4, s));
     WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
+    g->wb_words = (NC + 31) / 32 + 1;
+    g->clist_cap = NC + 1;
+    g->pieces_cap = g->npieces_max + 1;
     WEDGE_TRY(dev_alloc(g, (void**)&g->longs, (uint64_t)kLongCap * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->xf_task, 16));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
@@ -871,7 +874,10 @@ static XformParams xform_params(wedge_graph* g, int trace) {
     X.V = g->V;
     X.bm_words = ((uint64_t)g->V + 31) / 32;
     X.count_out = nullptr;
-    X.standalone_k = -1;
+    X.standalone = 0;
+    X.standalone_k = 0;
+    X.eidx8 = g->eidx8;
+    X.eidx8_off = g->eidx8_off;
     X.trace = trace;
     X.wstat = nullptr;
     X.slice_ctr = nullptr;
@@ -942,8 +948,69 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
     }, &g->loop_exec[app]);
 }
 
+// A precision k as the ABI passes it (uint32): 0 .. 7, or -1 / -2 for
+// entries of 16 / 8 edges.
+static bool valid_precision(uint32_t k) { return (int)k >= -2 && (int)k <= (int)kMaxCoarsen; }
+
+// Wedge Frontier entries of the graph at precision k: ceil(E / (32 * 2^k)).
+static uint64_t entries_at(const wedge_graph* g, int k) {
+    const unsigned sh = (unsigned)(5 + k);
+    return (g->E + (1ull << sh) - 1) >> sh;
+}
+
+// Finer precisions than one chunk need the 8-edge-unit edge index and a
+// Wedge bitmap, list and piece buffer sized for 8-edge entries: built and
+// grown on first use (the cached loop graphs hold the old buffers and are
+// dropped).
+static wedge_status ensure_fine(wedge_graph* g, cudaStream_t s) {
+    WEDGE_TRY(build_eidx8(g, s));
+    const uint64_t nu = entries_at(g, -2);
+    const uint64_t wbw = (nu + 31) / 32 + 1, cl = nu + 1;
+    const uint64_t pc = std::max(g->npieces_max, g->npieces8_max) + 1;
+    if (wbw <= g->wb_words && cl <= g->clist_cap && pc <= g->pieces_cap) return WEDGE_OK;
+    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+    WEDGE_TRY_CUDA(cudaDeviceSynchronize());
+    if (wbw > g->wb_words) {
+        dev_free(g->wb);
+        g->wb = nullptr;
+        WEDGE_TRY(dev_alloc(g, (void**)&g->wb, wbw * 4));
+        WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, wbw * 4, s));
+        g->wb_words = wbw;
+    }
+    if (cl > g->clist_cap) {
+        dev_free(g->clist);
+        g->clist = nullptr;
+        WEDGE_TRY(dev_alloc(g, (void**)&g->clist, cl * 4));
+        g->clist_cap = cl;
+    }
+    if (pc > g->pieces_cap) {
+        dev_free(g->pieces);
+        g->pieces = nullptr;
+        WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, pc * sizeof(uint2)));
+        g->pieces_cap = pc;
+    }
+    for (auto& x : g->loop_exec)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    for (auto& x : g->loop_exec_push)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    if (g->ms_exec) {
+        cudaGraphExecDestroy(g->ms_exec);
+        g->ms_exec = nullptr;
+    }
+    g->loop_failed = false;
+    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+    return WEDGE_OK;
+}
+
 static wedge_status check_opts(const wedge_opts* o) {
-    if (o->log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
+    if (!valid_precision(o->log2_coarsen))
+        return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be 0..7, or -1 / -2 (16- / 8-edge entries)");
     if (o->switch_mode > WEDGE_SWITCH_ALWAYS_SPARSE) return set_error(WEDGE_ERR_INVALID_ARG, "bad switch_mode");
     if (o->reserved[0]) return set_error(WEDGE_ERR_INVALID_ARG, "reserved option fields must be zero");
     return WEDGE_OK;
@@ -967,7 +1034,7 @@ static wedge_status fill_stats(wedge_graph* g, cudaStream_t s, wedge_stats* stat
         } else if (r[t].mode) {
             stats->sparse_iters++;
             stats->chunks_listed += r[t].nchunks;
-            const uint64_t e = (uint64_t)r[t].nchunks << (5 + r[t].k);
+            const uint64_t e = (uint64_t)r[t].nchunks << (5 + (int)r[t].k);
             stats->edges_pulled += e < g->E ? e : g->E;
         } else {
             stats->edges_pulled += g->E;
@@ -1081,13 +1148,14 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     init.tau_bp = o.tau_bp;
     init.k = o.log2_coarsen;
     init.E = g->E;
-    const uint64_t wb_words = (g->NC + 31) / 32 + 1;
+    const uint64_t wb_words = g->wb_words;
     const bool sync = o.synchronous && app != kBFS;
     const bool push = o.sparse_push != 0;
     if (push && o.synchronous) return set_error(WEDGE_ERR_INVALID_ARG, "sparse_push and synchronous exclude each other");
     if (push && init.switch_mode == WEDGE_SWITCH_LEARNED) init.switch_mode = WEDGE_SWITCH_THRESHOLD;
     if (sync && !g->vals_sync) WEDGE_TRY(dev_alloc(g, (void**)&g->vals_sync, (uint64_t)g->V * 4));
     if (push) WEDGE_TRY(build_csr(g, s));
+    if (!push && (int)o.log2_coarsen < 0) WEDGE_TRY(ensure_fine(g, s));
     if (push && !trace && !g->loop_exec_push[app] && !g->loop_failed) {
         if (build_hybrid_graph(g, app) != WEDGE_OK) {
             g->loop_failed = true;
@@ -1158,7 +1226,7 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
                                   bool sssp, cudaStream_t s) {
     WEDGE_TRY_CUDA(cudaMemsetAsync(levels, 0xFF, (size_t)g->V * Q * 4, s));
     k_msbfs_clear<<<g->num_sms * 4, 256, 0, s>>>(g->V, g->ms_fb[0], g->ms_fb[1], g->ms_seen, g->bm[0], g->bm[1], g->wb,
-                                                 (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->ms_bar);
+                                                 g->wb_words, g->rec, g->ctl, init, g->ms_bar);
     k_msbfs_roots<<<(nroots + 255) / 256, 256, 0, s>>>(g->ms_roots, g->ms_roots + g->ms_cap, nroots, Q, g->ms_fb[0],
                                                        g->ms_seen, levels, g->bm[0]);
     PullParams P = pull_params(g, 0, kBFS);
@@ -1388,6 +1456,8 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
     if (opts_in) o = *opts_in;
     else wedge_default_opts(sssp ? WEDGE_SSSP : WEDGE_BFS, &o);
     WEDGE_TRY(check_opts(&o));
+    if ((int)o.log2_coarsen < 0)
+        return set_error(WEDGE_ERR_INVALID_ARG, "batched runs take log2_coarsen 0..7 (entries of whole chunks)");
     if (classify(d_levels) != PtrKind::Device) return set_error(WEDGE_ERR_INVALID_ARG, "levels must be device memory");
     DeviceGuard dg(g->device);
     // roots and their queries, checked on the host
@@ -1471,15 +1541,18 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
                                       uint32_t* d_chunk_list, uint32_t* d_chunk_count, wedge_stream_t stream) {
     if (!g || !d_vertex_bitmap || !d_chunk_list || !d_chunk_count)
         return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
-    if (log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
+    if (!valid_precision(log2_coarsen))
+        return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be 0..7, or -1 / -2 (16- / 8-edge entries)");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if ((int)log2_coarsen < 0) WEDGE_TRY(ensure_fine(g, s));
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, sizeof(IterRec), s));
     WEDGE_TRY_CUDA(cudaMemsetAsync(d_chunk_count, 0, 4, s));
     XformParams X = xform_params(g, 0);
     X.bm_in = d_vertex_bitmap;
     X.clist = d_chunk_list;
     X.count_out = d_chunk_count;
+    X.standalone = 1;
     X.standalone_k = (int)log2_coarsen;
     launch_xform(g, X, s);
     k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
@@ -1499,9 +1572,11 @@ wedge_status wedge_frontier_transform_profile(wedge_graph_t g, const uint32_t* d
     if (!d_warp_stats) return WEDGE_OK;
     if (!d_vertex_bitmap || !d_chunk_list || !d_chunk_count) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
     if (cap_warps < nw) return set_error(WEDGE_ERR_INVALID_ARG, "d_warp_stats holds fewer warps than the launch");
-    if (log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
+    if (!valid_precision(log2_coarsen))
+        return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be 0..7, or -1 / -2 (16- / 8-edge entries)");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if ((int)log2_coarsen < 0) WEDGE_TRY(ensure_fine(g, s));
     if (!g->slice_ctr) WEDGE_TRY(dev_alloc(g, (void**)&g->slice_ctr, 16));
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, sizeof(IterRec), s));
     WEDGE_TRY_CUDA(cudaMemsetAsync(d_chunk_count, 0, 4, s));
@@ -1511,6 +1586,7 @@ wedge_status wedge_frontier_transform_profile(wedge_graph_t g, const uint32_t* d
     X.bm_in = d_vertex_bitmap;
     X.clist = d_chunk_list;
     X.count_out = d_chunk_count;
+    X.standalone = 1;
     X.standalone_k = (int)log2_coarsen;
     X.wstat = reinterpret_cast<unsigned long long*>(d_warp_stats);
     X.slice_ctr = g->slice_ctr;
@@ -1537,12 +1613,13 @@ wedge_status wedge_pull_iterate(wedge_graph_t g, wedge_app app, uint32_t* d_valu
     if (app == WEDGE_BFS && !d_cur_bitmap) return set_error(WEDGE_ERR_INVALID_ARG, "BFS needs the current frontier");
     if (app == WEDGE_SSSP && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
     if (d_chunk_list && !d_chunk_count) return set_error(WEDGE_ERR_INVALID_ARG, "chunk list without count");
-    if (log2_coarsen > kMaxCoarsen) return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be <= 7");
+    if (!valid_precision(log2_coarsen))
+        return set_error(WEDGE_ERR_INVALID_ARG, "log2_coarsen must be 0..7, or -1 / -2 (16- / 8-edge entries)");
     if (iter + 2 >= g->rec_cap) return set_error(WEDGE_ERR_INVALID_ARG, "iter too large");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned sparse = d_chunk_list ? 1u : 0u;
-    const unsigned cap = (unsigned)((g->NC + (1ull << log2_coarsen) - 1) >> log2_coarsen);
+    const unsigned cap = (unsigned)entries_at(g, (int)log2_coarsen);
     k_standalone_prep<<<1, 32, 0, s>>>(g->rec, g->ctl, iter, sparse, log2_coarsen, d_chunk_count, cap);
     PullParams P = pull_params(g, 0);
     P.decide = 0;  // one pull: k_standalone_out reduces the block slots
@@ -1627,7 +1704,7 @@ wedge_status wedge_trace_candidates(wedge_graph_t g, wedge_app app, uint32_t roo
     P.mlp = nullptr;
     XformParams X = xform_params(g, 0);
     k_run_init<<<g->num_sms * 4, 256, 0, s>>>(app, g->V, root, g->vals, g->bm[0], g->bm[1], g->wb,
-                                              (g->NC + 31) / 32 + 1, g->rec, g->ctl, init, g->flist[0], g->visk,
+                                              g->wb_words, g->rec, g->ctl, init, g->flist[0], g->visk,
                                               visk_words(g));
     k_frontier_stats<<<g->num_sms * 4, 256, 0, s>>>(g->bm[0], g->V, g->outdeg, g->eidx_off, g->rec, g->ctl, nullptr,
                                                     P.gf);

@@ -172,6 +172,35 @@ __global__ void k_eidx_pass(const uint32_t* __restrict__ src, uint64_t E, uint64
     }
 }
 
+// The edge index at the paper's finer precisions (Section 3.4, "Frontier
+// Precision"): row u lists, once each, the 8-edge units (position >> 3)
+// holding u's out-edges.  One warp per 32 positions (four units); the
+// sources of each unit are made distinct with __match_any_sync on (source,
+// unit).  COUNT: one atomic per distinct source and unit on its row length;
+// otherwise the unit is appended to the row at the row's cursor.
+template <bool COUNT>
+__global__ void k_eidx8_pass(const uint32_t* __restrict__ src, uint64_t E, uint64_t NC, uint32_t* __restrict__ cnt,
+                             uint32_t* __restrict__ eidx8) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = warp; c < NC; c += nwarps) {
+        const uint64_t p = c * 32 + lane;
+        const bool valid = p < E;
+        const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
+        if (!valid) continue;
+        const uint32_t s = src[p];
+        const unsigned same = __match_any_sync(vmask, ((unsigned long long)s << 2) | (lane >> 3));
+        if ((unsigned)(__ffs(same) - 1) != lane) continue;
+        if (COUNT) {
+            atomicAdd(&cnt[s], 1u);
+        } else {
+            const uint32_t pos = atomicAdd(&cnt[s], 1u);
+            eidx8[pos] = (uint32_t)(p >> 3);
+        }
+    }
+}
+
 // Row lengths (low words) and out-degrees (high words) of the count pass.
 __global__ void k_split_counts(const unsigned long long* __restrict__ counts, uint32_t V,
                                uint32_t* __restrict__ rowlen, uint32_t* __restrict__ outdeg) {
@@ -350,6 +379,8 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->ms_bar);
     dev_free(g->slice_ctr);
     dev_free(g->zhdr);
+    dev_free(g->eidx8);
+    dev_free(g->eidx8_off);
     dev_free(g->zwords);
     dev_free(g->zbo);
     dev_free(g->zpieces);
@@ -533,6 +564,54 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
     if (e != cudaSuccess) return cuda_error(e, "edge index build");
     g->npieces_max = total;
     WEDGE_TRY_CUDA(cudaGetLastError());
+    return WEDGE_OK;
+}
+
+// The 8-edge-unit edge index, built on the first run or transformation at
+// a finer precision than one 32-edge chunk.
+wedge_status build_eidx8(wedge_graph* g, cudaStream_t s) {
+    if (g->eidx8) return WEDGE_OK;
+    const uint32_t V = g->V;
+    const uint64_t E = g->E, NC = g->NC;
+    const int sms = g->num_sms;
+    uint32_t* cnt = nullptr;
+    WEDGE_TRY(dev_alloc(nullptr, (void**)&cnt, ((uint64_t)V + 1) * 4));
+    struct Free {
+        uint32_t* p;
+        cudaStream_t s;
+        ~Free() { dev_free_async(p, s); }
+    } free_cnt{cnt, s};
+    WEDGE_TRY(dev_alloc(g, (void**)&g->eidx8_off, ((uint64_t)V + 1) * 4));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((uint64_t)V + 1) * 4, s));
+    const unsigned eg = grid_for(NC * 32, 256, sms);
+    if (NC) {
+        k_eidx8_pass<true><<<eg, 256, 0, s>>>(g->src, E, NC, cnt, nullptr);
+        count_launch();
+    }
+    WEDGE_TRY(exclusive_scan_u32(cnt, g->eidx8_off, V, nullptr, s));
+    uint32_t len = 0;
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(&len, g->eidx8_off + V, 4, cudaMemcpyDeviceToHost, s));
+    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->eidx8, (uint64_t)(len ? len : 1) * 4));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(cnt, g->eidx8_off, ((uint64_t)V + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (NC) {
+        k_eidx8_pass<false><<<eg, 256, 0, s>>>(g->src, E, NC, cnt, g->eidx8);
+        count_launch();
+    }
+    // work pieces bound: sum ceil(|row| / 32)
+    k_rowlen_from_off<<<grid_for(V, 256, sms), 256, 0, s>>>(g->eidx8_off, V, cnt);
+    unsigned long long* d_total = nullptr;
+    WEDGE_TRY(dev_alloc(nullptr, (void**)&d_total, 8));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(d_total, 0, 8, s));
+    k_pieces_total<<<grid_for(V, 256, sms), 256, 0, s>>>(cnt, V, d_total);
+    count_launch(2);
+    unsigned long long total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free_async(d_total, s);
+    if (e != cudaSuccess) return cuda_error(e, "8-edge edge index build");
+    g->eidx8_len = len;
+    g->npieces8_max = total;
     return WEDGE_OK;
 }
 

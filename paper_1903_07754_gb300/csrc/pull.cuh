@@ -288,8 +288,11 @@ __device__ __forceinline__ void stage_list(bool act, uint32_t v, unsigned* s_lcn
 }
 
 // ------------------------------------------------------------------------
-// One warp slice of the pull (K1/K4 + K5): kSliceC chunks, kEPL = 8 edges
-// per lane (lane L holds edges 8*(L&3) .. +7 of slice chunk L>>2).
+// One warp slice of the pull (K1/K4 + K5): kEPL = 8 consecutive edges per
+// lane, edges o .. o+7 of the lane's chunk c (dense pulls: lane L holds
+// edges 8*(L&3) .. +7 of slice chunk L>>2; sparse pulls: the lanes' 8-edge
+// units as listed).  lane_break: the previous lane does not hold the 8
+// edges just before this lane's (a run of lanes starts here).
 //
 // Destinations come from the chunk's head mask (bit i: position 32c+i is
 // the first in-edge of its destination) and the index of the destination of
@@ -310,16 +313,16 @@ template <int APP>
 __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, const uint32_t* cur, uint32_t* next,
                                               const uint32_t (&sv)[kEPL], const uint32_t (&wv)[kEPL], int nvalid,
                                               uint32_t live, unsigned long long c, uint2 meta, unsigned next_head,
-                                              bool contig,
+                                              unsigned o, bool lane_break,
                                               uint32_t* s_kid, typename Traits<APP>::T* s_val, Stats& st,
                                               unsigned* s_lcnt, uint32_t* s_list) {
     using Tr = Traits<APP>;
     using T = typename Tr::T;
-    const unsigned lane = threadIdx.x & 31, sub = lane & 3, o = 8 * sub;
+    const unsigned lane = threadIdx.x & 31;
     const uint32_t heads = meta.x;
     const uint32_t vmask = (nvalid >= 8) ? 0xFFu : ((1u << nvalid) - 1u);
     const uint32_t hb = (heads >> o) & vmask;
-    const uint32_t brk = (hb | ((sub == 0 && !contig) ? 1u : 0u)) & vmask;
+    const uint32_t brk = (hb | (lane_break ? 1u : 0u)) & vmask;
     live &= vmask;
 
     T inc[kEPL];
@@ -358,7 +361,7 @@ __device__ __forceinline__ void process_slice(const PullParams& P, unsigned it, 
     const bool tail_close = nvalid > 0 && (nvalid < kEPL || !nx_valid || (nb0 & up) != 0);
     const bool next_past_end = c * 32 + o + kEPL >= P.E;
     const bool tail_real = nvalid < kEPL || next_past_end ||
-                           ((sub == 3) ? (next_head != 0) : (((heads >> (o + kEPL)) & 1u) != 0));
+                           ((o == 32 - kEPL) ? (next_head != 0) : (((heads >> (o + kEPL)) & 1u) != 0));
     // record positions: every break b >= 1 closes a segment at b-1; plus the tail
     uint32_t R = brk >> 1;
     if (tail_close) R |= 1u << (nvalid - 1);
@@ -630,40 +633,47 @@ __device__ __forceinline__ void pull_dense_direct(const PullParams& P, unsigned 
         const uint32_t clive = live;
         const unsigned long long cc = c;
         fetch(sl + nw);
-        process_slice<APP>(P, it, cur, next, cs, cw, cnv, clive, cc, cmeta, cnh, q > 0, my_kid, my_val, st, s_lcnt,
-                           s_list);
+        process_slice<APP>(P, it, cur, next, cs, cw, cnv, clive, cc, cmeta, cnh, 8 * sub, lane == 0, my_kid, my_val,
+                           st, s_lcnt, s_list);
     }
 }
 
-// Pull over the Wedge Frontier list: slices of 8 listed chunks (list entry
-// b at coarsening k stands for chunks b*2^k .. b*2^k + 2^k - 1), loaded
-// directly; the Wedge bitmap words of the entries are zeroed as consumed.
+// Pull over the Wedge Frontier list.  A list entry b at precision k covers
+// 32 * 2^k edges: the 8-edge units b * 2^(k+2) .. (b+1) * 2^(k+2) - 1
+// (k >= -2: k = -2, -1 are entries of 8 and 16 edges, the paper's finer
+// precisions, Section 3.4 "Frontier Precision").  Slices of 32 listed units,
+// one per lane, loaded directly; contiguous units continue each other's
+// segments.  The Wedge bitmap words of the entries are zeroed as consumed.
 template <int APP>
-__device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, unsigned k, unsigned nchunks,
+__device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, int k, unsigned nentries,
                                             const uint32_t* cur, uint32_t* next, uint32_t* my_kid,
                                             typename Traits<APP>::T* my_val, Stats& st, unsigned long long gw,
                                             unsigned long long nw, unsigned* s_lcnt, uint32_t* s_list) {
-    const unsigned lane = threadIdx.x & 31, q = lane >> 2, sub = lane & 3;
-    const unsigned long long nunits = (unsigned long long)nchunks << k;
-    const unsigned long long nslices = (nunits + kSliceC - 1) / kSliceC;
-    const unsigned long long kmask = (1ull << k) - 1;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned ls = (unsigned)(k + 2);  // log2 of 8-edge units per entry
+    const unsigned long long nunits = (unsigned long long)nentries << ls;
+    const unsigned long long nslices = (nunits + 31) / 32;
+    const unsigned long long umask = (1ull << ls) - 1;
+    const unsigned long long NU = (P.E + kEPL - 1) / kEPL;
     // a small pull is bound by its chain of dependent loads: the visited
     // check would add one more link than the gathers it saves
-    const bool skip_visited = nunits >= kSkipVisitedMinChunks;
+    const bool skip_visited = (nunits >> 2) >= kSkipVisitedMinChunks;
     for (unsigned long long sl = gw; sl < nslices; sl += nw) {
-        const unsigned long long j = sl * kSliceC + q;
+        const unsigned long long j = sl * 32 + lane;
         bool uvalid = j < nunits;
-        unsigned long long c = 0;
+        unsigned long long id = 0;  // the lane's 8-edge unit
         if (uvalid) {
-            const uint32_t b = __ldcg(P.clist + (j >> k));
-            c = ((unsigned long long)b << k) | (j & kmask);
-            uvalid = c < P.NC;
-            if (uvalid && P.wb && sub == 0 && (j & kmask) == 0) P.wb[b >> 5] = 0u;
+            const uint32_t b = __ldcg(P.clist + (j >> ls));
+            id = ((unsigned long long)b << ls) | (j & umask);
+            uvalid = id < NU;
+            if (uvalid && P.wb && (j & umask) == 0) P.wb[b >> 5] = 0u;
         }
-        const unsigned long long cprev = __shfl_up_sync(kFull, c, 4);
-        const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 4);
-        const bool contig = q > 0 && pvalid && uvalid && c == cprev + 1;
-        const unsigned long long e_lane = c * 32 + 8 * sub;
+        const unsigned long long idprev = __shfl_up_sync(kFull, id, 1);
+        const unsigned pvalid = __shfl_up_sync(kFull, (unsigned)uvalid, 1);
+        const bool contig = lane > 0 && pvalid && uvalid && id == idprev + 1;
+        const unsigned long long c = id >> 2;
+        const unsigned o = kEPL * (unsigned)(id & 3);
+        const unsigned long long e_lane = c * 32 + o;
         int nvalid = 0;
         uint2 meta = make_uint2(0u, 0u);
         unsigned next_head = 1u;
@@ -671,13 +681,13 @@ __device__ __forceinline__ void pull_sparse(const PullParams& P, unsigned it, un
             const long long left = (long long)P.E - (long long)e_lane;
             nvalid = left >= kEPL ? kEPL : (left > 0 ? (int)left : 0);
             meta = __ldg(P.cmeta + c);
-            next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
+            if (o == 32 - kEPL) next_head = __ldg(&P.cmeta[c + 1].x) & 1u;
         }
-        const uint32_t live = lane_live<APP>(P, meta, 8 * sub, nvalid, skip_visited);
+        const uint32_t live = lane_live<APP>(P, meta, o, nvalid, skip_visited);
         uint32_t sv[kEPL], wv[kEPL];
         load_lane_edges<APP>(P, e_lane, nvalid, live, sv, wv);
-        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, contig, my_kid, my_val, st,
-                           s_lcnt, s_list);
+        process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, o, !contig, my_kid, my_val,
+                           st, s_lcnt, s_list);
     }
 }
 
@@ -757,7 +767,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     const unsigned it = C->it;
     const unsigned mode = P.rec[it].mode;
     if (P.hybrid && mode != 0) return;  // the push serves this iteration
-    const unsigned k = P.rec[it].k;
+    const int k = (int)P.rec[it].k;  // precision: -2 .. 7
     const unsigned nchunks = P.rec[it].nchunks;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // layout: [records: values, ids][stages: barriers, src, w, metadata]
@@ -876,7 +886,8 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + s);
                 const uint32_t live = lane_live<APP>(P, meta, 8 * (lane & 3), nvalid);
-                process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, q > 0, my_kid,
+                process_slice<APP>(P, it, cur, next, sv, wv, nvalid, live, c, meta, next_head, 8 * (lane & 3), lane == 0,
+                                   my_kid,
                                    my_val, st, &s_lcnt, s_list);
             }
         }

@@ -22,7 +22,10 @@ struct XformParams {
     uint32_t V;
     unsigned long long bm_words;
     unsigned int* count_out;     // standalone mode: list count (else rec[it].nchunks)
-    int standalone_k;            // >= 0: standalone transformation at this coarsening
+    int standalone;              // nonzero: a standalone transformation (not a run's)
+    int standalone_k;            // ... at this precision (-2 .. 7)
+    const uint32_t* eidx8;       // the edge index in 8-edge units (precisions k < 0)
+    const uint32_t* eidx8_off;
     int trace;
     // load-balance accounting of a standalone transformation (nullptr: off):
     // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
@@ -72,10 +75,36 @@ struct PieceOut {
     unsigned* nlong;        // ... and its count
 };
 
-__device__ __forceinline__ PieceOut piece_out(const XformParams& X, unsigned* nlong) {
+// The edge index a transformation at precision kk reads: chunk ids shifted
+// by kk (kk >= 0; compressed when the graph's tuning asks for it), or
+// 8-edge-unit ids shifted by kk + 2 (kk = -2, -1: entries of 8 or 16 edges).
+struct IndexSel {
+    const uint32_t* eoff;
+    const uint32_t* ei;
+    unsigned shift;
+    bool z;
+};
+
+__device__ __forceinline__ IndexSel select_index(const XformParams& X, int kk) {
+    IndexSel r;
+    if (kk < 0) {
+        r.eoff = X.eidx8_off;
+        r.ei = X.eidx8;
+        r.shift = (unsigned)(kk + 2);
+        r.z = false;
+    } else {
+        r.eoff = X.eidx_off;
+        r.ei = X.eidx;
+        r.shift = (unsigned)kk;
+        r.z = X.zhdr != nullptr;
+    }
+    return r;
+}
+
+__device__ __forceinline__ PieceOut piece_out(const XformParams& X, unsigned* nlong, bool z) {
     PieceOut po;
     po.pieces = X.pieces;
-    po.zpieces = X.zhdr ? X.zpieces : nullptr;
+    po.zpieces = z ? X.zpieces : nullptr;
     po.zbo = X.zbo;
     po.zhdr = X.zhdr;
     po.longs = X.longs;
@@ -558,41 +587,42 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
     WarpStamp ws;
     ws.start(X);
     if (X.task_ctr && tid == 0) *X.task_ctr = 0u;  // the expansion after this kernel takes tasks from it
-    if (X.standalone_k >= 0) {
+    if (X.standalone) {
         bm = X.bm_in;
         r = X.rec;
-        xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X, &r->nlong), &r->npieces, tid >> 5,
+        const IndexSel ix = select_index(X, X.standalone_k);
+        xform_scan_words(bm, X.V, X.bm_words, ix.eoff, piece_out(X, &r->nlong, ix.z), &r->npieces, tid >> 5,
                          nth >> 5);
         ws.stop(X, tid >> 5, 0);
         return;
-    } else {
-        if (C->done) return;
-        const unsigned it = C->it;
-        if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
-        prepare_iteration(X, it, tid, nth);
-        r = X.rec + it;
-        if (r->mode == 0) return;
-        if (r->nlist == r->nfront) {
-            xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, X.eidx_off, piece_out(X, &r->nlong),
-                            &r->npieces,
-                            tid >> 5, nth >> 5);
-            return;
-        }
-        bm = (it & 1) ? X.bm[1] : X.bm[0];
     }
-    xform_scan_words(bm, X.V, X.bm_words, X.eidx_off, piece_out(X, &r->nlong), &r->npieces, tid >> 5, nth >> 5);
+    if (C->done) return;
+    const unsigned it = C->it;
+    if (X.trace && blockIdx.x == 0 && threadIdx.x == 0) X.rec[it].t_xf0 = global_timer();
+    prepare_iteration(X, it, tid, nth);
+    r = X.rec + it;
+    if (r->mode == 0) return;
+    const IndexSel ix = select_index(X, (int)r->k);
+    if (r->nlist == r->nfront) {
+        xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, ix.eoff, piece_out(X, &r->nlong, ix.z),
+                        &r->npieces, tid >> 5, nth >> 5);
+        return;
+    }
+    bm = (it & 1) ? X.bm[1] : X.bm[0];
+    xform_scan_words(bm, X.V, X.bm_words, ix.eoff, piece_out(X, &r->nlong, ix.z), &r->npieces, tid >> 5, nth >> 5);
 }
 
 __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParams X) {
     RunCtl* C = X.ctl;
-    unsigned n, k;
+    unsigned n;
+    int k;
     unsigned* count;
     unsigned it = 0;
     unsigned nlong;
-    if (X.standalone_k >= 0) {
+    if (X.standalone) {
         n = __ldcg(&X.rec[0].npieces);
         nlong = __ldcg(&X.rec[0].nlong);
-        k = (unsigned)X.standalone_k;
+        k = X.standalone_k;
         count = X.count_out;
     } else {
         if (C->done) return;
@@ -601,9 +631,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
         if (r->mode == 0) return;
         n = r->npieces;
         nlong = r->nlong;
-        k = r->k;
+        k = (int)r->k;
         count = &X.rec[it].nchunks;
     }
+    const IndexSel ix = select_index(X, k);
     if (!X.longs) nlong = 0;
     if (nlong > kLongCap) nlong = kLongCap;
     __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
@@ -622,7 +653,7 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
             if (r0 + j < nlong) {
                 const uint32_t u = __ldcg(X.longs + r0 + j);
                 s_lu[r0 + j] = u;
-                cnt[j] = (__ldg(X.eidx_off + u + 1) - __ldg(X.eidx_off + u) + 31u) >> 5;
+                cnt[j] = (__ldg(ix.eoff + u + 1) - __ldg(ix.eoff + u) + 31u) >> 5;
             }
             sum += cnt[j];
         }
@@ -650,14 +681,15 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     WarpStamp ws;
     ws.start(X);
-    if (X.zhdr)
-        xform_expand_pieces<true>(X.zpieces, n, k, X.zwords, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                  s_lu, s_lpre, nlong, X.eidx_off, X.zbo, X.zhdr, X.task_ctr);
+    if (ix.z)
+        xform_expand_pieces<true>(X.zpieces, n, ix.shift, X.zwords, X.wb, X.clist, count, gw, nw,
+                                  s_stage[threadIdx.x >> 5], s_lu, s_lpre, nlong, ix.eoff, X.zbo, X.zhdr, X.task_ctr);
     else
-        xform_expand_pieces<false>(X.pieces, n, k, X.eidx, X.wb, X.clist, count, gw, nw, s_stage[threadIdx.x >> 5],
-                                   s_lu, s_lpre, nlong, X.eidx_off, nullptr, nullptr, X.task_ctr);
-    if (X.standalone_k >= 0) ws.stop(X, gw, 1);
-    if (X.trace && X.standalone_k < 0) {
+        xform_expand_pieces<false>(X.pieces, n, ix.shift, ix.ei, X.wb, X.clist, count, gw, nw,
+                                   s_stage[threadIdx.x >> 5], s_lu, s_lpre, nlong, ix.eoff, nullptr, nullptr,
+                                   X.task_ctr);
+    if (X.standalone) ws.stop(X, gw, 1);
+    if (X.trace && !X.standalone) {
         __syncthreads();
         if (threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
     }
@@ -676,7 +708,8 @@ constexpr unsigned kStaticSliceWords = 8;  // 256 vertices per piece
 __global__ void __launch_bounds__(kXformThreads) k_xform_static(const XformParams X) {
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned k = (unsigned)X.standalone_k;
+    const IndexSel ix = select_index(X, X.standalone_k);
+    const unsigned k = ix.shift;
     const unsigned long long nslices = (X.bm_words + kStaticSliceWords - 1) / kStaticSliceWords;
     WarpStamp ws;
     ws.start(X);
@@ -691,13 +724,13 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_static(const XformParam
             if (wi == X.bm_words - 1 && (X.V & 31)) word &= (1u << (X.V & 31)) - 1u;
             for (; word; word &= word - 1) {
                 const uint32_t u = (uint32_t)(wi * 32 + __ffs(word) - 1);
-                const uint32_t rb = __ldg(X.eidx_off + u), re = __ldg(X.eidx_off + u + 1);
+                const uint32_t rb = __ldg(ix.eoff + u), re = __ldg(ix.eoff + u + 1);
                 for (uint32_t e0 = rb; e0 < re; e0 += 32) {
                     const uint32_t e = e0 + lane;
                     bool fresh = false;
                     uint32_t b = 0;
                     if (e < re) {
-                        b = __ldg(X.eidx + e) >> k;
+                        b = __ldg(ix.ei + e) >> k;
                         const uint32_t bit = 1u << (b & 31);
                         fresh = (atomicOr(X.wb + (b >> 5), bit) & bit) == 0;
                     }

@@ -3,7 +3,7 @@
 Each case draws a graph (uniform random, small R-MAT with a random skew, or
 a rewired grid; sizes from a handful of vertices to ~2^15, weights from 1 to
 near 2^32 so that SSSP saturates), a root, and run options (threshold and
-precision, always dense / always sparse, the push/pull hybrid, synchronous
+precision from 8-edge entries to 32 * 2^7 edges, always dense / always sparse, the push/pull hybrid, synchronous
 pulls), and checks BFS, SSSP and CC bit for bit and PageRank within L1 1e-6."""
 import numpy as np
 import pytest
@@ -40,7 +40,7 @@ def _opts(app, rng):
     o = wedge.wedge_default_opts(app)
     o.switch_mode = int(rng.choice(SWITCHES))
     o.tau_bp = int(rng.choice([0, 1, 100, 2000, 10000]))
-    o.log2_coarsen = int(rng.integers(0, 8))
+    o.log2_coarsen = int(rng.integers(-2, 8)) & 0xFFFFFFFF  # -1 / -2: entries of 16 / 8 edges
     mode = int(rng.integers(0, 3)) if app != "bfs" else int(rng.integers(0, 2))
     if mode == 1:
         o.sparse_push = 1
