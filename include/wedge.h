@@ -18,10 +18,16 @@
  *    order.  E < 2^32-256.  wedge_graph_create checks offsets and source
  *    ids on the device and rejects malformed input.
  *  - A chunk is 32 consecutive CSC positions: chunk c holds positions
- *    32c .. 32c+31 (the last one may be short).  With coarsening k
+ *    32c .. 32c+31 (the last one may be short).  With precision k
  *    (log2_coarsen, 0..7) one Wedge Frontier bit / list entry b stands for
  *    the 2^k chunks b*2^k .. b*2^k + 2^k - 1, i.e. 32*2^k edges
- *    (Section 3.4, "Frontier Precision").  NC = ceil(E/32).
+ *    (Section 3.4, "Frontier Precision").  k may also be -1 or -2, passed
+ *    as uint32 (0xFFFFFFFF, 0xFFFFFFFE): entries of 16 or 8 consecutive
+ *    positions (b*16 .., b*8 ..), the paper's finer settings; the first use
+ *    builds an edge index in 8-edge units (4 bytes per distinct source and
+ *    unit) and grows the Wedge bitmap and list to 8-edge entries.
+ *    NC = ceil(E/32); a list at precision k holds up to ceil(E / (32*2^k))
+ *    entries.
  *  - Vertex bitmaps are uint32 words, bit (v & 31) of word v >> 5, with
  *    ceil(V/32) words.
  *  - Pointers: arguments named d_* may point to device memory of the graph's
@@ -81,7 +87,8 @@ typedef enum {
 
 typedef struct {
     uint32_t tau_bp;       /* fullness threshold in basis points of E (100 = 1%) */
-    uint32_t log2_coarsen; /* k: one Wedge bit per 32 << k edges, 0..7 */
+    uint32_t log2_coarsen; /* k: one Wedge bit per 32 * 2^k edges, 0..7, or -1 / -2
+                            * (as uint32) for 16 / 8 edges; batched runs take 0..7 */
     uint32_t switch_mode;  /* wedge_switch */
     uint32_t max_iters;    /* 0 = default (2^20) */
     uint32_t trace;        /* nonzero: keep per-iteration records for wedge_get_trace */
@@ -127,7 +134,7 @@ typedef struct {
     uint64_t fullness;  /* sum of out-degrees of the frontier F_t pulled at t */
     uint32_t nfront;    /* |F_t| */
     uint32_t mode;      /* 0 = dense pull, 1 = pull over the Wedge Frontier */
-    uint32_t log2_coarsen;
+    uint32_t log2_coarsen; /* precision of the entries (as in wedge_opts) */
     uint32_t nchunks;   /* Wedge Frontier entries pulled at t (mode 1) */
     uint32_t rowsum;    /* sum over F_t of edge-index row lengths (chunks at k=0) */
     uint32_t npieces;   /* work pieces handed to the transformation */
@@ -229,9 +236,10 @@ wedge_status wedge_graph_copy_edge_index_z(wedge_graph_t g, uint32_t* d_zbo, uin
 
 /* The frontier transformation (Sections 3.3, 4): from the vertex frontier
  * d_vertex_bitmap (ceil(V/32) words, device) to the Wedge Frontier at
- * coarsening log2_coarsen, written as a list of entries b (each standing for
- * chunks b*2^k .. b*2^k+2^k-1) into d_chunk_list (device, capacity
- * ceil(NC / 2^k)) with the count in *d_chunk_count (device).  Entries are
+ * precision log2_coarsen, written as a list of entries b (each standing for
+ * chunks b*2^k .. b*2^k+2^k-1, or for 16 / 8 positions at k = -1 / -2) into
+ * d_chunk_list (device, capacity ceil(E / (32*2^k))) with the count in
+ * *d_chunk_count (device).  Entries are
  * distinct; their order is unspecified.  Errors: INVALID_ARG, CUDA. */
 wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_bitmap,
                                       uint32_t log2_coarsen, uint32_t* d_chunk_list,
@@ -291,8 +299,8 @@ wedge_status wedge_frontier_transform_noalloc(uint32_t V, uint64_t E, const uint
  *  reached vertices).  d_cur_bitmap: the frontier consumed (BFS only; NULL
  *  otherwise).  d_chunk_list / d_chunk_count: the Wedge Frontier to pull
  *  over at coarsening log2_coarsen, or d_chunk_list = NULL for a dense pull
- *  over all edges; entries must be distinct, entries >= ceil(NC/2^k) are
- *  ignored and the count is clamped to ceil(NC/2^k).  Outputs: bits of the vertices whose value changed are
+ *  over all edges; entries must be distinct, entries >= ceil(E/(32*2^k)) are
+ *  ignored and the count is clamped to ceil(E/(32*2^k)).  Outputs: bits of the vertices whose value changed are
  *  ORed into d_next_bitmap (device, ceil(V/32) words; the caller zeroes it),
  *  *d_fullness (device uint64) = sum of their out-degrees, *d_nfront
  *  (device) = their number.
