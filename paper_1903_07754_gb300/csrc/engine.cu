@@ -1123,8 +1123,10 @@ static wedge_status build_hybrid_graph(wedge_graph* g, int app) {
         XformParams X = xform_params(g, 0);
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
-        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows
-        X.longs = nullptr;
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows,
+        X.longs = nullptr; // and read from the CSR at every precision
+        X.eidx8_off = X.eidx_off;
+        X.eidx8 = nullptr;
         launch_hybrid_body(g, app, P, X, push_params(g), cs);
     }, &g->loop_exec_push[app]);
 }
@@ -1188,8 +1190,10 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
     if (push) {
         X.eidx_off = g->csr_off;
         X.pieces = g->push_pieces;
-        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows
-        X.longs = nullptr;
+        X.zhdr = nullptr;  // pieces of out-edge rows: never compressed, never listed as long rows,
+        X.longs = nullptr; // and read from the CSR at every precision
+        X.eidx8_off = X.eidx_off;
+        X.eidx8 = nullptr;
         const PushParams Q = push_params(g);
         WEDGE_TRY_CUDA(cudaGetLastError());
         if (!trace && g->loop_exec_push[app])
