@@ -117,9 +117,9 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 # settings the autotuner tries for the step (direct loads, all blocks per SM)
 STEP_TUNE_GRID = {
-    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "bfs": {"k": (-2, -1, 0, 1), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "cc": {"k": (-2, -1, 0, 1), "tau_bp": (500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "sssp": {"k": (-2, -1, 0, 1), "tau_bp": (100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
 }
 
 
@@ -144,7 +144,7 @@ def tune_step(wedge, G, S, g):
 
 def step_opts(wedge, app, tuned):
     o = wedge.wedge_default_opts(app)
-    o.log2_coarsen, o.tau_bp = tuned[app]["k"], tuned[app]["tau_bp"]
+    o.log2_coarsen, o.tau_bp = tuned[app]["k"] & 0xFFFFFFFF, tuned[app]["tau_bp"]
     return o
 
 
@@ -702,8 +702,10 @@ def bench_studies(args, wedge, torch, dev, world):
                               "transform": sum(x["t_xform_ns"] for x in tr) / 1e6}
         # Fig. 9: every iteration timed dense and as a Wedge Frontier at the
         # default precision, from the same state
-        feat, ms, chosen = wedge.wedge_trace_candidates(H.handle, app, 0, None, 64, 4096)
-        kdef = wedge.wedge_default_opts(app).log2_coarsen
+        oc = wedge.wedge_default_opts(app)
+        oc.log2_coarsen = 0  # the timed candidates are chunk precisions
+        feat, ms, chosen = wedge.wedge_trace_candidates(H.handle, app, 0, oc, 64, 4096)
+        kdef = 0
         # feature 3 of the cost model is the fullness over |E|: the active share of edges
         r["per_iteration"] = [{"t": t, "active_edges_pct": 100.0 * float(feat[t, 0, 2]),
                                "dense_ms": float(ms[t, 0]), "wedge_ms": float(ms[t, 1 + kdef]),
@@ -718,21 +720,22 @@ def bench_studies(args, wedge, torch, dev, world):
         o = wedge.wedge_default_opts(app)
         o.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
         r["tau_sweep_ms"]["always_transform"] = _events(torch, lambda: run(H.handle, o), 5)
-        # Fig. 11: precision, 32 * 2^k edges per Wedge Frontier entry
+        # Fig. 11: precision, 32 * 2^k edges per Wedge Frontier entry (k = -2,
+        # -1: entries of 8 and 16 edges, the paper's finest settings)
         r["precision_sweep_ms"] = {}
-        for k in range(0, 5):
+        for k in range(-2, 5):
             o = wedge.wedge_default_opts(app)
-            o.log2_coarsen = k
+            o.log2_coarsen = k & 0xFFFFFFFF
             r["precision_sweep_ms"][f"k{k}"] = _events(torch, lambda: run(H.handle, o), 5)
         # multi-hop propagation (Section 5.2): iterations with in-place
         # updates vs every pull reading the previous iteration's values
         if app != "bfs":
             r["multi_hop"] = {}
-            for k in (0, 2, 4):
+            for k in (-2, 0, 2, 4):
                 row = {}
                 for name, sync in (("in_place", 0), ("synchronous", 1)):
                     o = wedge.wedge_default_opts(app)
-                    o.log2_coarsen = k
+                    o.log2_coarsen = k & 0xFFFFFFFF
                     o.synchronous = sync
                     st = {"cc": lambda: wedge.wedge_run_cc(H.handle, out, o),
                           "sssp": lambda: wedge.wedge_run_sssp(H.handle, 0, out, o)}[app]()
@@ -781,9 +784,9 @@ def bench_grid(args, wedge, torch, dev, world):
     G = wedge.Graph.from_csc(g)
     out = torch.empty(g.V, dtype=torch.int32, device=dev)
     study = {}
-    for k in (0, 2, 4, 6):
+    for k in (-2, 0, 2, 4, 6):
         o = wedge.wedge_default_opts("sssp")
-        o.log2_coarsen = k
+        o.log2_coarsen = k & 0xFFFFFFFF
         o.switch_mode = wedge.SWITCH_ALWAYS_SPARSE
         t = _events(torch, lambda: wedge.wedge_run_sssp(G.handle, 0, out, o, False), 2)
         st = wedge.wedge_run_sssp(G.handle, 0, out, o)

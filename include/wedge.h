@@ -117,7 +117,8 @@ typedef struct {
  * Threshold" and "Frontier Precision"): BFS tau = 1% with 8 edge vectors per
  * bit, CC/SSSP tau = 20% with 4 vectors per bit.  A vector holds up to 4
  * edges of one destination (Section 2.2), so a bit covers up to 32 / 16
- * edges; the finest entry here is one 32-edge chunk, k = 0, for both. */
+ * edges: k = 0 (one 32-edge chunk) for BFS, k = -1 (16-edge entries) for CC
+ * and SSSP. */
 void wedge_default_opts(wedge_app app, wedge_opts* out);
 
 typedef struct {

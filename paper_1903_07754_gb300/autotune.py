@@ -1,7 +1,7 @@
 """Autotuner for the pull schedule (not in the paper).
 
 For one graph and application it times a grid of settings -- Wedge Frontier
-precision k (chunk of 32*2^k edges), fullness threshold tau, dense loader
+precision k (entries of 32*2^k edges; k = -1, -2: 16 and 8 edges), fullness threshold tau, dense loader
 (direct streaming loads or bulk-copy staging), pull blocks per SM and the
 edge index the transformation reads (plain or compressed) -- with CUDA
 events, and returns the fastest.  Every setting computes the same
@@ -19,11 +19,11 @@ import os
 from . import wedge
 
 DEFAULT_GRID = {
-    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,),
+    "bfs": {"k": (-2, -1, 0, 1, 2, 3), "tau_bp": (50, 100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,),
             "edge_index": (0,)},
-    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
+    "cc": {"k": (-2, -1, 0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
            "edge_index": (0,)},
-    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
+    "sssp": {"k": (-2, -1, 0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0, 1), "blocks_per_sm": (0,),
              "edge_index": (0,)},
     "bfs_batch": {"k": (0, 1, 2, 3, 4), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,),
                   "blocks_per_sm": (0,), "edge_index": (0,)},
@@ -61,7 +61,7 @@ def tune(handle, app, V, root=0, roots=None, nqueries=64, grid=None, reps=3):
                                                          grid["blocks_per_sm"], grid["edge_index"]):
             wedge.wedge_graph_set_tuning(handle, loader, bps, ei)
             o = wedge.wedge_default_opts(base_app)
-            o.log2_coarsen, o.tau_bp = k, tau
+            o.log2_coarsen, o.tau_bp = k & 0xFFFFFFFF, tau
             if app == "bfs":
                 fns = [lambda r=r: wedge.wedge_run_bfs(handle, r, out, o, False) for r in tune_roots]
             elif app == "cc":
@@ -87,7 +87,7 @@ def apply(handle, best):
 
 def opts_for(app, best):
     o = wedge.wedge_default_opts("bfs" if app == "bfs_batch" else app)
-    o.log2_coarsen, o.tau_bp = best["k"], best["tau_bp"]
+    o.log2_coarsen, o.tau_bp = best["k"] & 0xFFFFFFFF, best["tau_bp"]
     return o
 
 

@@ -24,6 +24,11 @@ def collect(handle, app, roots, opts=None, max_iters=256, cap=4096):
     """Traces of `app` from each root: list of (features [n,6,12], ms [n,6],
     threshold choice [n])."""
     out = []
+    if opts is not None and opts.log2_coarsen > 7:
+        # the candidates are dense and k = 0..4: trace at chunk precision
+        import copy
+        opts = copy.copy(opts)
+        opts.log2_coarsen = 0
     for r in roots:
         feat, ms, chosen = wedge.wedge_trace_candidates(handle, app, int(r), opts, max_iters, cap)
         if len(ms):

@@ -185,7 +185,7 @@ void wedge_default_opts(wedge_app app, wedge_opts* out) {
         out->log2_coarsen = 0; // 8 edge vectors of <= 4 edges: one 32-edge chunk
     } else {
         out->tau_bp = 2000;    // 20%
-        out->log2_coarsen = 0; // 4 vectors (<= 16 edges): the finest entry, one chunk
+        out->log2_coarsen = 0xFFFFFFFFu; // -1: 4 vectors of <= 4 edges, 16-edge entries
     }
     out->max_iters = 0;
     out->trace = 0;

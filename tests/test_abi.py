@@ -72,7 +72,7 @@ def test_host_only_entry_points(lib):
     o = wedge.wedge_default_opts("bfs")
     assert (o.tau_bp, o.log2_coarsen, o.switch_mode) == (100, 0, wedge.SWITCH_THRESHOLD)
     o = wedge.wedge_default_opts("sssp")
-    assert (o.tau_bp, o.log2_coarsen) == (2000, 0)
+    assert (o.tau_bp, o.log2_coarsen) == (2000, 0xFFFFFFFF)  # 16-edge entries
     assert isinstance(wedge.wedge_kernel_launches(), int)
 
 
