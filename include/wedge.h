@@ -88,7 +88,8 @@ typedef enum {
 typedef struct {
     uint32_t tau_bp;       /* fullness threshold in basis points of E (100 = 1%) */
     uint32_t log2_coarsen; /* k: one Wedge bit per 32 * 2^k edges, 0..7, or -1 / -2
-                            * (as uint32) for 16 / 8 edges; batched runs take 0..7 */
+                            * (as uint32) for 16 / 8 edges; batched runs list whole
+                            * chunks (-1 / -2 act as 0 there) */
     uint32_t switch_mode;  /* wedge_switch */
     uint32_t max_iters;    /* 0 = default (2^20) */
     uint32_t trace;        /* nonzero: keep per-iteration records for wedge_get_trace */

@@ -1460,8 +1460,7 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
     if (opts_in) o = *opts_in;
     else wedge_default_opts(sssp ? WEDGE_SSSP : WEDGE_BFS, &o);
     WEDGE_TRY(check_opts(&o));
-    if ((int)o.log2_coarsen < 0)
-        return set_error(WEDGE_ERR_INVALID_ARG, "batched runs take log2_coarsen 0..7 (entries of whole chunks)");
+    if ((int)o.log2_coarsen < 0) o.log2_coarsen = 0;  // batched runs list whole chunks
     if (classify(d_levels) != PtrKind::Device) return set_error(WEDGE_ERR_INVALID_ARG, "levels must be device memory");
     DeviceGuard dg(g->device);
     // roots and their queries, checked on the host

@@ -178,6 +178,10 @@ def test_invalid_precisions(G16):
         wedge.wedge_run_bfs(G16.handle, 0, out, opts("bfs", k=_u(-3)))
     with pytest.raises(wedge.WedgeError):
         wedge.wedge_run_bfs(G16.handle, 0, out, opts("bfs", k=8))
-    lv = empty_u32(G16.V * 64)
-    with pytest.raises(wedge.WedgeError):
-        wedge.wedge_run_bfs_batch(G16.handle, np.arange(4, dtype=np.uint32), None, 4, lv, opts("bfs", k=_u(-1)))
+    # batched runs list whole chunks: -1 acts as 0
+    lv = empty_u32(G16.V * 4)
+    roots = np.array([0, 9, 300, 4000], dtype=np.uint32)
+    wedge.wedge_run_bfs_batch(G16.handle, roots, None, 4, lv, opts("bfs", k=_u(-1)))
+    a = u32(lv)[: G16.V * 4].copy()
+    wedge.wedge_run_bfs_batch(G16.handle, roots, None, 4, lv, opts("bfs", k=0))
+    np.testing.assert_array_equal(u32(lv)[: G16.V * 4], a)
