@@ -424,7 +424,15 @@ def main():
         t_s = time_fn(lambda: fn(sparse[name]))
         t_p = time_fn(lambda: fn(wedge.wedge_default_opts(name)))
         sd = stat_fn[name](odn)
+        # the Wedge Frontier's precision at the tuned threshold: entries of
+        # 8, 16 and 32 edges (k = -2, -1, 0; Section 3.4 "Frontier Precision")
+        by_k = {}
+        for k in (-2, -1, 0):
+            ok = step_opts(wedge, name, tuned)
+            ok.log2_coarsen = k & 0xFFFFFFFF
+            by_k[f"k{k}"] = time_fn(lambda: fn(ok))
         per_app[name] = {"ms": t_w, "gteps": edges[name] / (t_w / 1e3) / 1e9, "tuned": tuned[name],
+                         "precision_ms": by_k,
                          "paper_settings_ms": t_p, "dense_pull_ms": t_d,
                          "speedup_vs_dense_pull": t_d / t_w, "always_sparse_ms": t_s,
                          "speedup_vs_always_sparse": t_s / t_w,

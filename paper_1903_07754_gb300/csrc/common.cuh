@@ -204,6 +204,7 @@ struct wedge_graph {
     uint32_t* eidx8_off = nullptr;
     uint32_t* eidx8 = nullptr;
     uint64_t eidx8_len = 0, npieces8_max = 0;
+    uint64_t npieces_outdeg_bound = 0;  // sum ceil(outdeg / 32): bounds the pieces of either index
     uint64_t wb_words = 0;          // Wedge bitmap words allocated
     uint64_t clist_cap = 0;         // Wedge list entries allocated
     uint64_t pieces_cap = 0;        // work pieces allocated

@@ -778,13 +778,17 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     WEDGE_TRY(dev_alloc(g, (void**)&g->vals, V * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->bm[0], words * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->bm[1], words * 4));
-    WEDGE_TRY(dev_alloc(g, (void**)&g->wb, ((NC + 31) / 32 + 1) * 4));
-    WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, ((NC + 31) / 32 + 1) * 4, s));
-    WEDGE_TRY(dev_alloc(g, (void**)&g->clist, (NC + 1) * 4));
-    WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, (g->npieces_max + 1) * sizeof(uint2)));
-    g->wb_words = (NC + 31) / 32 + 1;
-    g->clist_cap = NC + 1;
-    g->pieces_cap = g->npieces_max + 1;
+    // the Wedge bitmap, list and pieces are sized for the finest entries
+    // (8 edges), so that a finer precision never reallocates them
+    const uint64_t NU8 = (g->E + 7) / 8;
+    g->wb_words = (NU8 + 31) / 32 + 1;
+    g->clist_cap = NU8 + 1;
+    g->pieces_cap = std::max(g->npieces_max, g->npieces_outdeg_bound) + 1;
+    WEDGE_TRY(dev_alloc(g, (void**)&g->wb, g->wb_words * 4));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, g->wb_words * 4, s));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->clist, g->clist_cap * 4));
+    WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, g->pieces_cap * sizeof(uint2)));
+
     WEDGE_TRY(dev_alloc(g, (void**)&g->longs, (uint64_t)kLongCap * 4));
     WEDGE_TRY(dev_alloc(g, (void**)&g->xf_task, 16));
     WEDGE_TRY(dev_alloc(g, (void**)&g->flist[0], (V + 1) * 4));
@@ -958,37 +962,20 @@ static uint64_t entries_at(const wedge_graph* g, int k) {
     return (g->E + (1ull << sh) - 1) >> sh;
 }
 
-// Finer precisions than one chunk need the 8-edge-unit edge index and a
-// Wedge bitmap, list and piece buffer sized for 8-edge entries: built and
-// grown on first use (the cached loop graphs hold the old buffers and are
-// dropped).
+// Finer precisions than one chunk need the edge index in 8-edge units,
+// built on first use (the Wedge bitmap, list and pieces are allocated for
+// them already).  Loop graphs captured before it existed hold a null index
+// and are dropped then.
 static wedge_status ensure_fine(wedge_graph* g, cudaStream_t s) {
+    if (g->eidx8) return WEDGE_OK;
     WEDGE_TRY(build_eidx8(g, s));
-    const uint64_t nu = entries_at(g, -2);
-    const uint64_t wbw = (nu + 31) / 32 + 1, cl = nu + 1;
-    const uint64_t pc = std::max(g->npieces_max, g->npieces8_max) + 1;
-    if (wbw <= g->wb_words && cl <= g->clist_cap && pc <= g->pieces_cap) return WEDGE_OK;
+    if (g->npieces8_max + 1 > g->pieces_cap) return set_error(WEDGE_ERR_CUDA, "8-edge index exceeds its piece bound");
+    bool cached = g->ms_exec != nullptr;
+    for (auto x : g->loop_exec) cached |= x != nullptr;
+    for (auto x : g->loop_exec_push) cached |= x != nullptr;
+    if (!cached) return WEDGE_OK;
     WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
-    WEDGE_TRY_CUDA(cudaDeviceSynchronize());
-    if (wbw > g->wb_words) {
-        dev_free(g->wb);
-        g->wb = nullptr;
-        WEDGE_TRY(dev_alloc(g, (void**)&g->wb, wbw * 4));
-        WEDGE_TRY_CUDA(cudaMemsetAsync(g->wb, 0, wbw * 4, s));
-        g->wb_words = wbw;
-    }
-    if (cl > g->clist_cap) {
-        dev_free(g->clist);
-        g->clist = nullptr;
-        WEDGE_TRY(dev_alloc(g, (void**)&g->clist, cl * 4));
-        g->clist_cap = cl;
-    }
-    if (pc > g->pieces_cap) {
-        dev_free(g->pieces);
-        g->pieces = nullptr;
-        WEDGE_TRY(dev_alloc(g, (void**)&g->pieces, pc * sizeof(uint2)));
-        g->pieces_cap = pc;
-    }
+    if (g->last_stream) WEDGE_TRY_CUDA(cudaStreamSynchronize(g->last_stream));
     for (auto& x : g->loop_exec)
         if (x) {
             cudaGraphExecDestroy(x);
@@ -1004,7 +991,6 @@ static wedge_status ensure_fine(wedge_graph* g, cudaStream_t s) {
         g->ms_exec = nullptr;
     }
     g->loop_failed = false;
-    WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
     return WEDGE_OK;
 }
 

@@ -551,18 +551,22 @@ static wedge_status build(wedge_graph* g, const uint32_t* user_eoff, const uint3
         dev_free_async(d_max, s);
         if (e != cudaSuccess) return cuda_error(e, "max out-degree");
     }
-    // work pieces bound: sum ceil(|row| / 32)
+    // work pieces bound: sum ceil(|row| / 32); and sum ceil(outdeg / 32),
+    // which also bounds the pieces of the 8-edge-unit index (a row there
+    // lists at most one unit per out-edge)
     unsigned long long* d_total = nullptr;
-    WEDGE_TRY(dev_alloc(nullptr, (void**)&d_total, 8));
-    WEDGE_TRY_CUDA(cudaMemsetAsync(d_total, 0, 8, s));
+    WEDGE_TRY(dev_alloc(nullptr, (void**)&d_total, 16));
+    WEDGE_TRY_CUDA(cudaMemsetAsync(d_total, 0, 16, s));
     k_pieces_total<<<grid_for(V, 256, sms), 256, 0, s>>>(tmp, V, d_total);
-    count_launch();
-    unsigned long long total = 0;
-    cudaError_t e = cudaMemcpyAsync(&total, d_total, 8, cudaMemcpyDeviceToHost, s);
+    k_pieces_total<<<grid_for(V, 256, sms), 256, 0, s>>>(g->outdeg, V, d_total + 1);
+    count_launch(2);
+    unsigned long long total[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(total, d_total, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free_async(d_total, s);
     if (e != cudaSuccess) return cuda_error(e, "edge index build");
-    g->npieces_max = total;
+    g->npieces_max = total[0];
+    g->npieces_outdeg_bound = total[1];
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
 }
