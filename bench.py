@@ -115,11 +115,15 @@ class ClockSampler:
 
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
-# settings the autotuner tries for the step (direct loads, all blocks per SM)
+# settings the autotuner tries for the step (direct loads, all blocks per SM).
+# Entries of whole chunks only: 8- and 16-edge entries make the resident runs
+# 1-3% faster at R-MAT s22 (per_app.precision_ms), but their edge index
+# costs about as much to build as the chunk index, once per graph, which
+# the end-to-end step (two graph creations) would pay every step.
 STEP_TUNE_GRID = {
-    "bfs": {"k": (-2, -1, 0, 1), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "cc": {"k": (-2, -1, 0, 1), "tau_bp": (500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
-    "sssp": {"k": (-2, -1, 0, 1), "tau_bp": (100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "bfs": {"k": (0, 1, 2, 3), "tau_bp": (100, 500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "cc": {"k": (0, 1, 2), "tau_bp": (500, 2000, 5000), "dense_loader": (0,), "blocks_per_sm": (0,)},
+    "sssp": {"k": (0, 1, 2), "tau_bp": (100, 500, 2000), "dense_loader": (0,), "blocks_per_sm": (0,)},
 }
 
 
