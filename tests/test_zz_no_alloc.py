@@ -4,13 +4,14 @@ It serves callers that cannot call cudaMalloc (a framework that owns the
 device memory pool, latency-critical loops, fixed device footprints).  Its
 result must equal wedge_frontier_transform's on the same inputs, on two calls
 in a row (the second call reuses the library's fixed scratch array left by
-the first).  This file sorts last so a run that stops at its first failure
+the first), and the Wedge Frontier's definition computed by the oracle.  This file sorts last so a run that stops at its first failure
 has already run every other test."""
 import numpy as np
 import pytest
 import torch
 
 import graphgen as gg
+import oracle
 from paper_1903_07754_gb300 import wedge
 
 
@@ -53,6 +54,8 @@ def test_noalloc_transform_matches_transform_twice():
             n, m = int(_host(want_n)[0]), int(_host(got_n)[0])
             assert m == n and n > 0
             np.testing.assert_array_equal(np.sort(_host(got_list)[:m]), np.sort(_host(want_list)[:n]))
+            np.testing.assert_array_equal(np.sort(_host(got_list)[:m]).astype(np.uint64),
+                                          oracle.wedge_groups_scan(g, mask, 32 << k))
     finally:
         G.close()
 
