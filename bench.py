@@ -1207,7 +1207,38 @@ def cpu_baseline(g, s, od):
             "sample": "full-size BFS (push), CC (union-find), SSSP (Dijkstra) and 2 of 20 PageRank "
                       f"iterations (FP64 pull) on the same graphs; {secs:.1f} s on 1 host core",
             "seconds": {"bfs": t1 - t0, "cc": t2 - t1, "sssp": t3 - t2, "pr2": t4 - t3},
-            "host_cores_available": os.cpu_count()}
+            "host_cores_available": os.cpu_count(), "all_cores": cpu_baseline_all_cores(g, s, od)}
+
+
+def cpu_baseline_all_cores(g, s, od):
+    """The oracle's pull variants with their destination loop shared among
+    every host core (OpenMP; the same results as the single-threaded pulls):
+    BFS, CC (HCC) and SSSP (Bellman-Ford) by dense pulls until the frontier
+    is empty, and 2 of the 20 PageRank iterations; the median of 3 runs of
+    each, credited with the step's edges."""
+    import oracle
+    secs = {}
+    lvl = dist = None
+    for name, fn in (("bfs", lambda: oracle.dense_pull_omp("bfs", g, 0)),
+                     ("cc", lambda: oracle.dense_pull_omp("cc", s, 0)),
+                     ("sssp", lambda: oracle.dense_pull_omp("sssp", g, 0)),
+                     ("pr2", lambda: oracle.pr_pull_omp(g, DAMPING, 2))):
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            r = fn()
+            ts.append(time.perf_counter() - t0)
+        secs[name] = float(np.median(ts))
+        if name == "bfs":
+            lvl = r[0]
+        elif name == "sssp":
+            dist = r[0]
+    edges = credited_edges(od, lvl != 0xFFFFFFFF) + s.E + credited_edges(od, dist != 0xFFFFFFFF) + 2 * g.E
+    total = sum(secs.values())
+    return {"value": edges / total / 1e9, "unit": "GTEPS", "cores": oracle.omp_threads(), "kind": "oracle",
+            "sample": "dense pulls (BFS, HCC, Bellman-Ford until the frontier is empty) and 2 of 20 PageRank "
+                      f"iterations, destinations shared among {oracle.omp_threads()} threads; median of 3 runs "
+                      f"each, {total:.2f} s", "seconds": secs}
 
 
 if __name__ == "__main__":

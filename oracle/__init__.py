@@ -31,12 +31,16 @@ APPS = {"bfs": BFS, "cc": CC, "sssp": SSSP}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c (plain C11, -O2, single-threaded) into _oracle.so."""
+    """Compile oracle.c (plain C11, -O2) into _oracle.so.  Everything is
+    single-threaded except the *_omp timing variants, which share their
+    destination loop among OpenMP threads when gcc has -fopenmp."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"],
-                   check=True, capture_output=True)
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(base[:5] + ["-fopenmp"] + base[5:], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(base, check=True, capture_output=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,6 +65,9 @@ def _load():
             "or_wedge_groups_index": (u64, [u32, p, p, p, u64, p]),
             "or_fullness": (u64, [u32, p, p]),
             "or_wedge_run": (u64, [i32, u32, u64, p, p, p, u32, i32, u32, u64, u64, p, p, u64]),
+            "or_omp_threads": (i32, []),
+            "or_dense_pull_omp": (u64, [i32, u32, p, p, p, u32, p]),
+            "or_pr_pull_omp": (None, [u32, p, p, p, dbl, u32, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -235,3 +242,29 @@ def cc_pull(g) -> np.ndarray:
 
 def sssp_pull(g, root: int) -> np.ndarray:
     return wedge_run("sssp", g, root, POLICY_ALWAYS_DENSE)[0]
+
+
+# ---- all-cores timing variants (the CPU baseline's multi-threaded leg) ----
+
+def omp_threads() -> int:
+    """Threads the *_omp variants use (1 without OpenMP)."""
+    return int(_load().or_omp_threads())
+
+
+def dense_pull_omp(app, g, root: int = 0) -> tuple[np.ndarray, int]:
+    """BFS/CC/SSSP by dense pulls, destinations shared among threads:
+    (values, pulls); the values equal the single-threaded pull's."""
+    a = APPS[app] if isinstance(app, str) else int(app)
+    V, off, src = _graph(g)
+    w = _c(g.w, np.uint32) if a == SSSP else np.zeros(1, dtype=np.uint32)
+    vals = np.empty(V, dtype=np.uint32)
+    it = _load().or_dense_pull_omp(a, V, _P(off), _P(src), _P(w), root, _P(vals))
+    return vals, int(it)
+
+
+def pr_pull_omp(g, damping: float = 0.85, iters: int = 20) -> np.ndarray:
+    V, off, src = _graph(g)
+    od = outdeg(g)
+    pr = np.empty(V, dtype=np.float64)
+    _load().or_pr_pull_omp(V, _P(off), _P(src), _P(od), damping, iters, _P(pr))
+    return pr

@@ -485,3 +485,104 @@ uint64_t or_wedge_run(int app, uint32_t V, uint64_t E, const uint32_t* off, cons
     free(gmask);
     return t;
 }
+
+/* ------------------------------------------------------------------ */
+/* All-cores timing variants (the CPU baseline's multi-threaded leg):   */
+/* the same dense pulls, every iteration over all in-edges (Section 2.1,*/
+/* pull), with the loop over destinations shared among OpenMP threads.  */
+/* Each destination is computed by one thread in CSC order, from the    */
+/* previous iteration's values, so the results are the single-threaded  */
+/* functions' bit for bit.  Built with -fopenmp when the compiler has   */
+/* it; otherwise these run on one thread.                               */
+/* ------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_omp_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* BFS, CC or SSSP by dense pulls until the frontier is empty; returns the
+ * number of pulls.  Same values as or_wedge_run(..., ALWAYS_DENSE, ...). */
+uint64_t or_dense_pull_omp(int app, uint32_t V, const uint32_t* off, const uint32_t* src, const uint32_t* w,
+                           uint32_t root, uint32_t* val) {
+    uint32_t* old = (uint32_t*)malloc(sizeof(uint32_t) * (V ? V : 1));
+    uint8_t* front = (uint8_t*)calloc(V ? V : 1, 1);
+    uint8_t* next = (uint8_t*)calloc(V ? V : 1, 1);
+    for (uint32_t v = 0; v < V; ++v) {
+        val[v] = (app == OR_CC) ? v : INF32;
+        front[v] = (app == OR_CC);
+    }
+    if (app != OR_CC && root < V) {
+        val[root] = 0;
+        front[root] = 1;
+    }
+    uint64_t t = 0;
+    for (;; ++t) {
+        uint64_t nfront = 0;
+        for (uint32_t v = 0; v < V; ++v) nfront += front[v];
+        if (nfront == 0) break;
+        memcpy(old, val, sizeof(uint32_t) * V);
+        int64_t n = (int64_t)V;
+#pragma omp parallel for schedule(dynamic, 4096)
+        for (int64_t vi = 0; vi < n; ++vi) {
+            const uint32_t v = (uint32_t)vi;
+            next[v] = 0;
+            if (app == OR_BFS && old[v] != INF32) continue;
+            uint32_t best = old[v];
+            for (uint64_t p = off[v]; p < off[v + 1]; ++p) {
+                const uint32_t u = src[p];
+                if (app == OR_BFS) {
+                    if (front[u] && best == INF32) best = (uint32_t)(t + 1);
+                } else if (app == OR_CC) {
+                    if (old[u] < best) best = old[u];
+                } else if (old[u] != INF32) {
+                    uint64_t cand = (uint64_t)old[u] + w[p];
+                    if (cand > SAT32) cand = SAT32;
+                    if (cand < best) best = (uint32_t)cand;
+                }
+            }
+            val[v] = best;
+            if (best != old[v]) next[v] = 1;
+        }
+        uint8_t* tmp = front;
+        front = next;
+        next = tmp;
+    }
+    free(old);
+    free(front);
+    free(next);
+    return t;
+}
+
+/* PageRank as or_pr_pull, the destination loop shared among threads. */
+void or_pr_pull_omp(uint32_t V, const uint32_t* off, const uint32_t* src, const uint32_t* outdeg, double d,
+                    uint32_t iters, double* pr) {
+    double* contrib = (double*)malloc(sizeof(double) * (V ? V : 1));
+    for (uint32_t v = 0; v < V; ++v) pr[v] = 1.0 / V;
+    for (uint32_t t = 0; t < iters; ++t) {
+        double dangling = 0.0;
+        for (uint32_t u = 0; u < V; ++u) {
+            if (outdeg[u] == 0) {
+                dangling += pr[u];
+                contrib[u] = 0.0;
+            } else {
+                contrib[u] = pr[u] / outdeg[u];
+            }
+        }
+        int64_t n = (int64_t)V;
+#pragma omp parallel for schedule(dynamic, 4096)
+        for (int64_t vi = 0; vi < n; ++vi) {
+            const uint32_t v = (uint32_t)vi;
+            double sum = 0.0;
+            for (uint64_t p = off[v]; p < off[v + 1]; ++p) sum += contrib[src[p]];
+            pr[v] = (1.0 - d) / V + d * (sum + dangling / V);
+        }
+    }
+    free(contrib);
+}
