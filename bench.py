@@ -445,8 +445,10 @@ def main():
     from paper_1903_07754_gb300 import costmodel
     if os.path.exists(costmodel.DEFAULT_MODEL):
         params = costmodel.load_params()
-        wedge.wedge_set_cost_model(G.handle, params)
-        wedge.wedge_set_cost_model(S.handle, params)
+        band = costmodel.load_band()
+        for H in (G, S):
+            wedge.wedge_set_cost_model(H.handle, params)
+            wedge.wedge_set_learned_band(H.handle, *band)
         for name, (fn, ow, _) in runs.items():
             ol = wedge.wedge_default_opts(name)
             ol.switch_mode = wedge.SWITCH_LEARNED
@@ -455,8 +457,9 @@ def main():
             per_app[name]["speedup_learned_vs_threshold"] = per_app[name]["ms"] / t_l
             per_app[name]["speedup_learned_vs_paper_settings"] = per_app[name]["paper_settings_ms"] / t_l
             per_app[name]["speedup_learned_vs_dense_pull"] = per_app[name]["dense_pull_ms"] / t_l
-        wedge.wedge_set_cost_model(G.handle, None)
-        wedge.wedge_set_cost_model(S.handle, None)
+        for H in (G, S):
+            wedge.wedge_set_cost_model(H.handle, None)
+            wedge.wedge_set_learned_band(H.handle, *costmodel.NO_BAND)
     # the push/pull hybrid (the comparison engine: sparse iterations push
     # over the frontier's out-edges, dense ones pull), its threshold tuned
     # on the tuning roots like Wedge's settings, timed on the measured root
@@ -596,8 +599,10 @@ def bench_learned(args, wedge, torch, dev, world):
         t_thr = _events(torch, lambda: run(thr), 5)
         t_dense = _events(torch, lambda: run(dense), 5)
         wedge.wedge_set_cost_model(G.handle, params)
+        wedge.wedge_set_learned_band(G.handle, *costmodel.load_band())
         t_l = _events(torch, lambda: run(learned), 5)
         wedge.wedge_set_cost_model(G.handle, None)
+        wedge.wedge_set_learned_band(G.handle, *costmodel.NO_BAND)
         run(thr)
         torch.cuda.synchronize()
         reached = out.cpu().numpy().view(np.uint32) != 0xFFFFFFFF

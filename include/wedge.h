@@ -381,6 +381,13 @@ wedge_status wedge_mlp_adam(float* d_params, const float* d_grad, float* d_m, fl
 /* Installs (params != NULL, host or device FP32) or removes the cost model
  * used by WEDGE_SWITCH_LEARNED on g; without one the threshold decides. */
 wedge_status wedge_set_cost_model(wedge_graph_t g, const float* params);
+/* The band of fullness / E (the share of edges the frontier's out-edges
+ * make up) inside which WEDGE_SWITCH_LEARNED evaluates the cost model on g;
+ * below lo it takes the Wedge Frontier at k = 0, above hi a dense pull,
+ * without inference (the band is learned from the training traces: outside
+ * it every traced iteration's fastest candidate was that one).  Default
+ * [0, 3e38]: always evaluate.  Errors: INVALID_ARG (lo < 0, hi < lo). */
+wedge_status wedge_set_learned_band(wedge_graph_t g, float lo, float hi);
 /* Training traces: runs app (BFS, CC, SSSP) from root with the threshold
  * policy of opts (log2_coarsen <= 4), and before every pull t (t < cap and
  * t < max_iters, 0 = no limit) times each candidate c (transformation +

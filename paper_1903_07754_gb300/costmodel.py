@@ -98,12 +98,35 @@ def regret(ms, choice):
     return float((ms[np.arange(len(ms)), choice] - ms.min(axis=1)).sum())
 
 
-def evaluate(params, traces):
+NO_BAND = (0.0, 3.0e38)
+
+
+def learn_band(traces, pad=2.0):
+    """The band of fullness / E (feature 3) outside which one candidate was
+    the fastest at every traced iteration: below lo the Wedge Frontier at
+    k = 0 (candidate 1), above hi a dense pull (candidate 0).  Widened by
+    `pad` on both sides; the decision evaluates the model only inside it."""
+    x = np.concatenate([f[:, 0, 2] for f, _, _ in traces]).astype(np.float64)
+    b = np.concatenate([m.argmin(axis=1) for _, m, _ in traces])
+    lo = float(x[b != 1].min()) / pad if np.any(b != 1) else 0.0
+    hi = float(x[b != 0].max()) * pad if np.any(b != 0) else NO_BAND[1]
+    return lo, max(hi, lo)
+
+
+def choose_in_band(params, feats, band=NO_BAND):
+    """The decision's choice with the band: the model inside it, candidate 1
+    below it, candidate 0 above it."""
+    x = feats[:, 0, 2]
+    c = choose(params, feats)
+    return np.where(x < band[0], 1, np.where(x > band[1], 0, c))
+
+
+def evaluate(params, traces, band=NO_BAND):
     """(learned regret, threshold regret, best possible total ms)."""
     lr_, th = 0.0, 0.0
     best = 0.0
     for feat, ms, chosen in traces:
-        lr_ += regret(ms, choose(params, feat))
+        lr_ += regret(ms, choose_in_band(params, feat, band))
         th += regret(ms, chosen.astype(np.int64))
         best += float(ms.min(axis=1).sum())
     return lr_, th, best
@@ -118,3 +141,15 @@ def load_params(path=DEFAULT_MODEL):
     if p.shape != (wedge.MLP_PARAMS,):
         raise ValueError("cost model must hold 5057 parameters")
     return p.astype(np.float32)
+
+
+def load_band(path=None):
+    """The band saved beside the model (cost_model.json's "band"), or no band."""
+    import json
+    path = path or os.path.join(os.path.dirname(DEFAULT_MODEL), "cost_model.json")
+    try:
+        with open(path) as f:
+            lo, hi = json.load(f)["band"]
+        return float(lo), float(hi)
+    except (OSError, KeyError, ValueError):
+        return NO_BAND

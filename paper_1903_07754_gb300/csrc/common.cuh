@@ -176,6 +176,7 @@ struct wedge_graph {
     // learned switch
     void* mlp_bf16 = nullptr;        // cost model weights (BF16)
     bool has_model = false;
+    float band_lo = 0.f, band_hi = 3.0e38f;  // fullness / E where the model is evaluated
     uint32_t max_outdeg = 0;
     uint32_t* snap_vals = nullptr;   // candidate-timing trace: value snapshot
     uint32_t* snap_visk = nullptr;   // candidate-timing trace: visited-bitmap snapshot

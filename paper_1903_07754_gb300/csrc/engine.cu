@@ -825,6 +825,8 @@ static GraphFeat graph_feat(const wedge_graph* g, int app) {
     const double mean = (double)g->E / (double)g->V;
     f.skew = (float)(std::log2(1.0 + (mean > 0 ? g->max_outdeg / mean : 0.0)) / 16.0);
     f.app = app == kBFS ? 0.f : (app == kCC ? 0.5f : 1.f);
+    f.band_lo = g->band_lo;
+    f.band_hi = g->band_hi;
     return f;
 }
 

@@ -274,6 +274,23 @@ wedge_status wedge_mlp_adam(float* d_params, const float* d_grad, float* d_m, fl
     return WEDGE_OK;
 }
 
+wedge_status wedge_set_learned_band(wedge_graph_t g, float lo, float hi) {
+    if (!g) return set_error(WEDGE_ERR_INVALID_ARG, "graph is NULL");
+    if (!(lo >= 0.f) || !(hi >= lo)) return set_error(WEDGE_ERR_INVALID_ARG, "band needs 0 <= lo <= hi");
+    DeviceGuard dg(g->device);
+    WEDGE_TRY_CUDA(cudaDeviceSynchronize());
+    // the device-loop graphs captured the previous band: rebuild them
+    for (auto& e : g->loop_exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    g->loop_failed = false;
+    g->band_lo = lo;
+    g->band_hi = hi;
+    return WEDGE_OK;
+}
+
 wedge_status wedge_set_cost_model(wedge_graph_t g, const float* params) {
     if (!g) return set_error(WEDGE_ERR_INVALID_ARG, "graph is NULL");
     DeviceGuard dg(g->device);

@@ -27,9 +27,12 @@ constexpr int kMlpB3 = kMlpW3 + kMlpHidden;                  // 5056
 constexpr int kMlpParams = kMlpB3 + 1;                       // 5057
 constexpr int kCandidates = 6;                               // dense, sparse k = 0..4
 
-// Graph statistics that enter every feature vector.
+// Graph statistics that enter every feature vector, and the band of
+// fullness / E inside which the decision evaluates the model (outside it the
+// traces' unanimous choice: the Wedge Frontier at k = 0 below, dense above).
 struct GraphFeat {
     float log2V, log2E, avg_deg, skew, app;
+    float band_lo, band_hi;
 };
 
 // Features of one candidate for the iteration that pulls frontier F_t:

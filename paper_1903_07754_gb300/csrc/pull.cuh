@@ -187,7 +187,9 @@ __device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __
     const unsigned long long F = __ldcg(&r->fullness);
     const unsigned nf = __ldcg(&r->nfront);
     const unsigned rows = __ldcg(&r->rowsum);
-    const bool learned = C->switch_mode == WEDGE_SWITCH_LEARNED && mlp_global != nullptr && nf > 0;
+    const bool model = C->switch_mode == WEDGE_SWITCH_LEARNED && mlp_global != nullptr && nf > 0;
+    const float frac = C->E ? (float)((double)F / (double)C->E) : 0.f;
+    const bool learned = model && frac >= gf.band_lo && frac <= gf.band_hi;
     float* h1 = sm;
     float* h2 = sm + kCandidates * kMlpHidden;
     float* out = sm + 2 * kCandidates * kMlpHidden;
@@ -235,6 +237,8 @@ __device__ void decide_block(IterRec* rec, RunCtl* C, unsigned it_next, const __
                 best = out[c];
                 choice = c;
             }
+    } else if (model) {
+        choice = frac < gf.band_lo ? 1 : 0;  // outside the band: no inference
     }
     unsigned sparse, k = C->k;
     if (choice >= 0) {

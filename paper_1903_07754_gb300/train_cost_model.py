@@ -5,7 +5,9 @@ Training mix: R-MAT scales 18, 20, 22 and 24 (edge factor 16) with a in
 {0.45, 0.57, 0.70} (b = c = (1-a)*0.19/0.43, d the rest), and rewired grids
 (1024^2 and 2048^2, p = 0.01), BFS and SSSP from seeded roots and CC on the
 symmetrised graph, every candidate timed at every iteration (up to 128 per
-run).  Held out: R-MAT scale 21, a = 0.57, seed 99.
+run).  Held out: R-MAT scale 21, a = 0.57, seed 99.  Also learns the band of
+fullness / E outside which the traces' fastest candidate never varied (the
+decision skips inference there).
 
     python -m paper_1903_07754_gb300.train_cost_model [--quick]
 """
@@ -66,10 +68,12 @@ def main():
     held = _graph_traces(*rmat_case(17 if quick else 21, 0.57, 99), 99)
     X, T = costmodel.dataset(train)
     params, loss = costmodel.train(X, T, steps=3000, lr=3e-3, seed=0)
-    learned, threshold, best = costmodel.evaluate(params, held)
-    learned_tr, threshold_tr, best_tr = costmodel.evaluate(params, train)
+    band = costmodel.learn_band(train)
+    learned, threshold, best = costmodel.evaluate(params, held, band)
+    learned_tr, threshold_tr, best_tr = costmodel.evaluate(params, train, band)
     costmodel.save(params)
     summary = {"rows": int(len(T)), "iterations": int(sum(len(m) for _, m, _ in train)), "train_loss": loss,
+               "band": list(band),
                "held_out": {"graph": "rmat-s%d-a0.57-seed99" % (17 if quick else 21), "regret_learned_ms": learned,
                             "regret_threshold_ms": threshold, "best_total_ms": best},
                "train": {"regret_learned_ms": learned_tr, "regret_threshold_ms": threshold_tr,

@@ -71,7 +71,7 @@ EXPORTS = [
     "wedge_frontier_transform_noalloc", "wedge_mlp_forward", "wedge_mlp_forward_bf16", "wedge_mlp_loss_grad",
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
-    "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z",
+    "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z", "wedge_set_learned_band",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "wedge_frontier_transform_noalloc": (st, [u32, u64, P, P, P, u32, P, P, P]),
         "wedge_frontier_transform_profile": (st, [P, P, u32, u32, P, P, P, u32, ctypes.POINTER(u32), P]),
         "wedge_graph_copy_edge_index_z": (st, [P, P, P, P, P]),
+        "wedge_set_learned_band": (st, [P, ctypes.c_float, ctypes.c_float]),
         "wedge_pull_iterate": (st, [P, i32, P, u32, P, P, P, u32, P, P, P, P]),
         "wedge_run_bfs": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
@@ -338,6 +339,10 @@ def wedge_mlp_loss_grad(params, x, t, n, grad, loss, stream=None):
 
 def wedge_mlp_adam(params, grad, m, v, step, lr, stream=None):
     _check(load().wedge_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)))
+
+
+def wedge_set_learned_band(handle, lo, hi):
+    _check(load().wedge_set_learned_band(handle, float(lo), float(hi)))
 
 
 def wedge_set_cost_model(handle, params):

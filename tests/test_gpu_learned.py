@@ -166,13 +166,17 @@ def test_learned_switch_gains_over_threshold_and_stays_exact(g16):
     X, T = costmodel.dataset(train_tr)
     params, loss = costmodel.train(X, T, steps=2000, lr=3e-3)
     learned, threshold, best = costmodel.evaluate(params, test_tr)
-    print(f"held-out regret: learned {learned:.3f} ms, threshold {threshold:.3f} ms, best total {best:.3f} ms, "
-          f"train loss {loss:.4f}")
+    band = costmodel.learn_band(train_tr)
+    learned_band, _, _ = costmodel.evaluate(params, test_tr, band)
+    print(f"held-out regret: learned {learned:.3f} ms (with band {band}: {learned_band:.3f} ms), "
+          f"threshold {threshold:.3f} ms, best total {best:.3f} ms, train loss {loss:.4f}")
     assert learned <= threshold
-    # learned runs reach the exact results
+    assert learned_band <= threshold
+    # learned runs reach the exact results, with and without the band
     G = graph(g16)
     try:
         wedge.wedge_set_cost_model(G.handle, params)
+        wedge.wedge_set_learned_band(G.handle, *band)
         out = empty_u32(g16.V)
         o = opts("bfs", switch=wedge.SWITCH_LEARNED)
         st = wedge.wedge_run_bfs(G.handle, 0, out, o)
@@ -181,5 +185,10 @@ def test_learned_switch_gains_over_threshold_and_stays_exact(g16):
         wedge.wedge_run_sssp(G.handle, 0, out, o)
         np.testing.assert_array_equal(u32(out)[: g16.V], oracle.sssp_dijkstra(g16, 0))
         assert st.iters > 0
+        wedge.wedge_set_learned_band(G.handle, *costmodel.NO_BAND)
+        wedge.wedge_run_sssp(G.handle, 0, out, o)
+        np.testing.assert_array_equal(u32(out)[: g16.V], oracle.sssp_dijkstra(g16, 0))
+        with pytest.raises(wedge.WedgeError):
+            wedge.wedge_set_learned_band(G.handle, 0.5, 0.1)
     finally:
         G.close()
