@@ -101,19 +101,20 @@ def regret(ms, choice):
 NO_BAND = (0.0, 3.0e38)
 
 
-def learn_band(traces, pad=2.0, rtol=0.05, atol_ms=0.002):
+def learn_band(traces, pad=2.0, rtol=0.05, atol_ms=0.002, quantile=0.0):
     """The band of fullness / E (feature 3) outside which one candidate was,
     within timing noise (rtol of the fastest plus atol_ms), the fastest at
-    every traced iteration: below lo the Wedge Frontier at k = 0
-    (candidate 1), above hi a dense pull (candidate 0).  Widened by `pad` on
-    both sides; the decision evaluates the model only inside it."""
+    every traced iteration (all but a `quantile` share of them at each end):
+    below lo the Wedge Frontier at k = 0 (candidate 1), above hi a dense
+    pull (candidate 0).  Widened by `pad` on both sides; the decision
+    evaluates the model only inside it."""
     x = np.concatenate([f[:, 0, 2] for f, _, _ in traces]).astype(np.float64)
     ms = np.concatenate([m for _, m, _ in traces])
     tol = ms.min(axis=1) * (1 + rtol) + atol_ms
     sparse0_slow = ms[:, 1] > tol   # iterations where k = 0 was clearly not the fastest
     dense_slow = ms[:, 0] > tol     # ... where a dense pull was clearly not
-    lo = float(x[sparse0_slow].min()) / pad if np.any(sparse0_slow) else NO_BAND[1]
-    hi = float(x[dense_slow].max()) * pad if np.any(dense_slow) else 0.0
+    lo = float(np.quantile(x[sparse0_slow], quantile)) / pad if np.any(sparse0_slow) else NO_BAND[1]
+    hi = float(np.quantile(x[dense_slow], 1.0 - quantile)) * pad if np.any(dense_slow) else 0.0
     if hi < lo:  # the regions meet: no fullness needs the model
         lo = hi = (lo + hi) / 2 if lo < NO_BAND[1] else hi
     return lo, hi
