@@ -533,6 +533,7 @@ def main():
     roof_cc = roofline_dense_pull(wedge, torch, G, S, g, s, stream, dev)
     balance = transform_balance(wedge, torch, G, g, stream, dev)
     zindex = compressed_index(wedge, torch, G, g, od, stream, dev, o_sssp)
+    locality = locality_study(wedge, torch, g, s, (o_bfs, o_cc, o_sssp), stream, dev, time_fn, ms_per_step)
 
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -542,7 +543,7 @@ def main():
                        "l2": "inputs larger than L2 (CSC src alone is %d MB)" % (4 * g.E >> 20),
                        "wedge_settings": "autotuned (k, tau) per app: " + json.dumps(tuned)},
             "per_app": per_app, "graph_build_ms": build_ms, "roofline": roof, "roofline_cc_dense_pull": roof_cc,
-            "transform_balance": balance, "compressed_edge_index": zindex,
+            "transform_balance": balance, "compressed_edge_index": zindex, "locality_relabel": locality,
             "gpu_launches": int(launches),
             "clocks": clk.summary()}
     if rank == 0 and not args.no_e2e:
@@ -555,6 +556,75 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def locality_study(wedge, torch, g, s, opts, stream, dev, time_fn, step_ms):
+    """The benchmark step on degree-relabelled copies of its two graphs
+    (wedge_csc_relabel_by_degree: new ids by descending out-degree, so the
+    most gathered values share cache lines; not in the paper), with the
+    same tuned options: the relabelling's device time, each application's
+    time with and without bringing its result back to the original ids,
+    the whole step, and the PageRank pull's gather rate."""
+    V = g.V
+    o_bfs, o_cc, o_sssp = opts
+    src_d = {}
+    for name, gx, wx in (("rmat", g, True), ("sym", s, False)):
+        arr = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+               for a in ((gx.offsets, gx.src, gx.w) if wx else (gx.offsets, gx.src))]
+        out = {"off": torch.empty(gx.V + 1, dtype=torch.int32, device=dev),
+               "src": torch.empty(gx.E, dtype=torch.int32, device=dev),
+               "w": torch.empty(gx.E, dtype=torch.int32, device=dev) if wx else None,
+               "o2n": torch.empty(gx.V, dtype=torch.int32, device=dev),
+               "n2o": torch.empty(gx.V, dtype=torch.int32, device=dev)}
+
+        def relabel():
+            wedge.wedge_csc_relabel_by_degree(gx.V, gx.E, arr[0], arr[1], arr[2] if wx else None, out["off"],
+                                              out["src"], out["w"], out["o2n"], out["n2o"], stream=stream)
+        out["t"] = _time_launch(torch, stream, relabel, reps=3, warm=1)
+        src_d[name] = out
+        del arr
+    R, Sd = src_d["rmat"], src_d["sym"]
+    G = wedge.Graph(wedge.wedge_graph_create(V, g.E, R["off"], R["src"], R["w"]), keep=[R["off"], R["src"], R["w"]])
+    S = wedge.Graph(wedge.wedge_graph_create(s.V, s.E, Sd["off"], Sd["src"]), keep=[Sd["off"], Sd["src"]])
+    root = int(R["o2n"][0].item())
+    a = torch.empty(V, dtype=torch.int32, device=dev)
+    b = torch.empty(V, dtype=torch.int32, device=dev)
+    c = torch.empty(V, dtype=torch.int32, device=dev)
+    r = torch.empty(V, dtype=torch.float32, device=dev)
+    rb = torch.empty(V, dtype=torch.float32, device=dev)
+    runs = {"bfs": lambda: wedge.wedge_run_bfs(G.handle, root, a, o_bfs, False),
+            "cc": lambda: wedge.wedge_run_cc(S.handle, a, o_cc, False),
+            "sssp": lambda: wedge.wedge_run_sssp(G.handle, root, a, o_sssp, False),
+            "pr": lambda: wedge.wedge_run_pr(G.handle, r, PR_ITERS, DAMPING, None, False)}
+    back = {"bfs": lambda: wedge.wedge_permute_rows(V, 1, R["o2n"], a, b),
+            "cc": lambda: wedge.wedge_cc_labels_to_original(s.V, Sd["n2o"], a, c, b),
+            "sssp": lambda: wedge.wedge_permute_rows(V, 1, R["o2n"], a, b),
+            "pr": lambda: wedge.wedge_permute_rows(V, 1, R["o2n"], r, rb)}
+    per_app = {}
+    for name in runs:
+        t = time_fn(runs[name])
+        tb = time_fn(lambda: (runs[name](), back[name]()))
+        per_app[name] = {"ms": t, "ms_with_map_back": tb}
+
+    def step():
+        for name in ("bfs", "cc", "sssp", "pr"):
+            runs[name]()
+            back[name]()
+    t_step = time_fn(step, reps=20)
+    od = torch.from_numpy(g.outdeg().astype(np.float32)).to(dev)
+    od_new = torch.empty_like(od)
+    wedge.wedge_permute_rows(V, 1, R["n2o"], od, od_new)  # out-degree of new vertex i
+    contrib = torch.where(od_new > 0, (1.0 / V) / torch.clamp(od_new, min=1.0), torch.zeros_like(od_new)).contiguous()
+    sums = torch.zeros(V, dtype=torch.int64, device=dev)
+    t_pull = _time_launch(torch, stream, lambda: wedge.wedge_pr_pull(G.handle, contrib, sums),
+                          before=lambda: sums.zero_(), reps=10)
+    G.close()
+    S.close()
+    return {"relabel_ms": {"rmat": R["t"] * 1e3, "sym": Sd["t"] * 1e3}, "per_app": per_app,
+            "step_ms_with_map_back": t_step, "speedup_step": step_ms / t_step,
+            "pr_pull_ms": t_pull * 1e3, "pr_pull_gathers_gs": g.E / t_pull / 1e9,
+            "note": "not in the paper: a locality step before graph creation; the main step runs on the "
+                    "graphs as generated"}
 
 
 def _events(torch, fn, reps):

@@ -438,6 +438,47 @@ wedge_status wedge_run_sssp_batch(wedge_graph_t g, const uint32_t* roots, const 
  * Synchronises the stream of that run. */
 wedge_status wedge_get_trace(wedge_graph_t g, wedge_iter_record* out, uint32_t cap, uint32_t* n);
 
+/* Degree-ordered relabelling (not in the paper; a locality step before
+ * wedge_graph_create).  Every pull gathers one value per in-edge, indexed by
+ * the edge's source; new ids that follow descending out-degree put the most
+ * gathered values on shared cache lines.  New vertex i is old vertex
+ * old_of_new[i], the i-th by descending out-degree, ties by ascending old
+ * id; its in-edges are old_of_new[i]'s in their original order, each source
+ * u renamed new_of_old[u] (weights carried along).
+ *  In (device): d_offsets[V+1], d_src[E], d_w[E] or NULL, a CSC as above.
+ *  Out (device, caller-owned, not overlapping the inputs): d_new_offsets[V+1],
+ *  d_new_src[E], d_new_w[E] (NULL exactly when d_w is), d_new_of_old[V],
+ *  d_old_of_new[V] (or NULL).
+ *  Validates like wedge_graph_create (offsets, source ids) and synchronises
+ *  `stream` once to read the result; the rest is stream-ordered.  Device
+ *  scratch of about 28 (V+1) + E/256 bytes comes from the library's pool.
+ *  Errors: INVALID_ARG (V == 0, E too large, NULL or host arrays, malformed
+ *  CSC), OUT_OF_MEMORY, CUDA. */
+wedge_status wedge_csc_relabel_by_degree(uint32_t V, uint64_t E, const uint32_t* d_offsets,
+                                         const uint32_t* d_src, const uint32_t* d_w,
+                                         uint32_t* d_new_offsets, uint32_t* d_new_src,
+                                         uint32_t* d_new_w, uint32_t* d_new_of_old,
+                                         uint32_t* d_old_of_new, wedge_stream_t stream);
+
+/* Results of a relabelled graph back in the original ids:
+ * d_out[v * width + c] = d_in[new_of_old[v] * width + c] for v < V, c < width
+ * (width 1: levels, distances, PageRank values as 32-bit words; width Q:
+ * the vertex-major rows of a batched run).  Device arrays, d_in != d_out;
+ * stream-ordered.  Errors: INVALID_ARG, CUDA. */
+wedge_status wedge_permute_rows(uint32_t V, uint32_t width, const uint32_t* d_new_of_old,
+                                const uint32_t* d_in, uint32_t* d_out, wedge_stream_t stream);
+
+/* Component labels of a relabelled graph back in the original ids.  A CC
+ * label names the smallest vertex id of its component; after a relabelling
+ * that is a new id, so this takes, per component, the smallest old id:
+ * d_out[old_of_new[i]] = min { old_of_new[j] : d_labels[j] == d_labels[i] }.
+ * d_scratch[V] is overwritten; all device arrays, pairwise distinct;
+ * labels >= V (which no CC run produces) are copied unchanged.
+ * Stream-ordered.  Errors: INVALID_ARG, CUDA. */
+wedge_status wedge_cc_labels_to_original(uint32_t V, const uint32_t* d_old_of_new,
+                                         const uint32_t* d_labels, uint32_t* d_scratch,
+                                         uint32_t* d_out, wedge_stream_t stream);
+
 /* Self-test of the bounded device waits (not in the paper).  Every wait in
  * the library's kernels -- mbarrier phases of the staged pull, the grid
  * barrier of the batched traversal -- gives up after 200 ms of device time

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libwedge.so")
-SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu", "sort.cu", "eidx_z.cu"]
+SOURCES = ["api.cu", "graph_build.cu", "engine.cu", "noalloc.cu", "mlp.cu", "sort.cu", "eidx_z.cu", "relabel.cu"]
 # A measurement tool for the benchmark, linked into a library of its own
 # (include/wedge_probe.h), not into the engine's.
 PROBE_SOURCES = ["probe.cu"]

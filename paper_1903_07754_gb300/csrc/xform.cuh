@@ -64,7 +64,7 @@ struct XformParams {
 // are listed, and their 32-entry units are spread over every warp of the
 // expansion instead.
 constexpr unsigned kLongRow = 32u * 64u;
-constexpr unsigned kLongCap = 2048;  // long rows listed per transformation (more: pieces)
+constexpr unsigned kLongCap = 1024;  // long rows listed per transformation (more: pieces)
 
 struct PieceOut {
     uint2* pieces;
@@ -422,7 +422,7 @@ template <bool Z>
 __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw,
-                                                    uint32_t* stage = nullptr, const uint32_t* s_lu = nullptr,
+                                                    uint32_t* stage = nullptr, const uint32_t* longs = nullptr,
                                                     const uint32_t* s_lpre = nullptr, unsigned nlong = 0,
                                                     const uint32_t* __restrict__ eidx_off = nullptr,
                                                     const uint32_t* __restrict__ zbo = nullptr,
@@ -430,20 +430,28 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
                                                     unsigned* task_ctr = nullptr) {
     unsigned staged = 0;  // warp-uniform
     const unsigned lane = threadIdx.x & 31;
-    const unsigned long long per = (unsigned long long)n / nw;
-    const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : (unsigned)per);
-    // tasks of ppt pieces: taken from *task_ctr (zeroed by the scan) as
-    // warps become free, or else task gw, gw + nw, ...
+    // 32-bit arithmetic: n < 2^32 pieces, nw < 2^32 warps
+    const unsigned per = n / (unsigned)nw;
+    const unsigned ppt = per >= 32 ? 32u : (per < 1 ? 1u : per);
+    // tasks of ppt pieces: warp gw takes task gw first; when there are more
+    // tasks than warps the rest come from *task_ctr (zeroed by the scan) as
+    // warps become free, else task gw + nw, gw + 2nw, ...  (A small frontier
+    // then costs no counter atomics: every warp would hit the one address.)
+    const unsigned long long ntasks = ppt == 1 ? n : (n - 1) / ppt + 1;  // n >= 1 when ppt > 1
+    const bool dyn = task_ctr != nullptr && ntasks > nw;
     unsigned long long task = gw;
-    for (;;) {
-        if (task_ctr) {
-            unsigned t = 0;
-            if (lane == 0) t = atomicAdd(task_ctr, 1u);
-            task = __shfl_sync(kFull, t, 0);
+    for (bool first = true;; first = false) {
+        if (!first) {
+            if (dyn) {
+                unsigned t = 0;
+                if (lane == 0) t = atomicAdd(task_ctr, 1u);
+                task = nw + __shfl_sync(kFull, t, 0);
+            } else {
+                task += nw;
+            }
         }
+        if (task >= ntasks) break;
         const unsigned long long base = task * ppt;
-        if (base >= n) break;
-        task += nw;
         const unsigned long long idx = base + lane;
         const bool have = lane < ppt && idx < n;
         uint2 pc;        // plain: {first entry, length}; Z: {header .x, header .y}
@@ -505,9 +513,9 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         }
         if (total) round_finish(pend, list, count, stage, staged);
     }
-    // long rows: the block's table holds their vertices (s_lu) and the
-    // exclusive prefix of their 32-entry unit counts (s_lpre); unit t of the
-    // concatenation goes to warp t mod nw
+    // long rows: the scan's list (`longs`) holds their vertices and the
+    // block's table s_lpre the exclusive prefix of their 32-entry unit
+    // counts; unit t of the concatenation goes to warp t mod nw
     const unsigned long long lunits = nlong ? s_lpre[nlong] : 0ull;
     Round lpend;
     for (unsigned long long t = gw; t < lunits; t += nw) {
@@ -517,7 +525,7 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
             if (s_lpre[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const uint32_t u = s_lu[lo];
+        const uint32_t u = __ldcg(longs + lo);
         const unsigned q = (unsigned)(t - s_lpre[lo]);
         const uint32_t rb = __ldg(eidx_off + u), len = __ldg(eidx_off + u + 1) - rb;
         const unsigned n_u = min(32u, len - q * 32u);
@@ -638,9 +646,8 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     if (!X.longs) nlong = 0;
     if (nlong > kLongCap) nlong = kLongCap;
     __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
-    // the long rows' table: vertices and the exclusive prefix of their unit
-    // counts (each thread sums a run of kLongCap / blockDim entries)
-    __shared__ uint32_t s_lu[kLongCap];
+    // the long rows' table: the exclusive prefix of their unit counts (each
+    // thread sums a run of kLongCap / blockDim entries)
     __shared__ uint32_t s_lpre[kLongCap + 1];
     __shared__ uint32_t s_part[kXformThreads / 32];
     if (nlong) {
@@ -652,7 +659,6 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
             cnt[j] = 0;
             if (r0 + j < nlong) {
                 const uint32_t u = __ldcg(X.longs + r0 + j);
-                s_lu[r0 + j] = u;
                 cnt[j] = (__ldg(ix.eoff + u + 1) - __ldg(ix.eoff + u) + 31u) >> 5;
             }
             sum += cnt[j];
@@ -683,10 +689,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     ws.start(X);
     if (ix.z)
         xform_expand_pieces<true>(X.zpieces, n, ix.shift, X.zwords, X.wb, X.clist, count, gw, nw,
-                                  s_stage[threadIdx.x >> 5], s_lu, s_lpre, nlong, ix.eoff, X.zbo, X.zhdr, X.task_ctr);
+                                  s_stage[threadIdx.x >> 5], X.longs, s_lpre, nlong, ix.eoff, X.zbo, X.zhdr, X.task_ctr);
     else
         xform_expand_pieces<false>(X.pieces, n, ix.shift, ix.ei, X.wb, X.clist, count, gw, nw,
-                                   s_stage[threadIdx.x >> 5], s_lu, s_lpre, nlong, ix.eoff, nullptr, nullptr,
+                                   s_stage[threadIdx.x >> 5], X.longs, s_lpre, nlong, ix.eoff, nullptr, nullptr,
                                    X.task_ctr);
     if (X.standalone) ws.stop(X, gw, 1);
     if (X.trace && !X.standalone) {

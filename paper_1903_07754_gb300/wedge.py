@@ -72,6 +72,7 @@ EXPORTS = [
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
     "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z", "wedge_set_learned_band",
+    "wedge_csc_relabel_by_degree", "wedge_permute_rows", "wedge_cc_labels_to_original",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -106,6 +107,9 @@ def load(path: str = LIB_PATH):
         "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_pr_pull": (st, [P, P, P, P]),
         "wedge_trim_memory": (st, [i32]),
+        "wedge_csc_relabel_by_degree": (st, [u32, u64, P, P, P, P, P, P, P, P, P]),
+        "wedge_permute_rows": (st, [u32, u32, P, P, P, P]),
+        "wedge_cc_labels_to_original": (st, [u32, P, P, P, P, P]),
         "wedge_selftest_timeout": (st, [i32]),
         "wedge_run_pr": (st, [P, P, u32, ctypes.c_float, ctypes.POINTER(wedge_opts),
                               ctypes.POINTER(wedge_stats), P]),
@@ -264,6 +268,27 @@ def wedge_run_pr(handle, rank, iters=20, damping=0.85, opts=None, want_stats=Tru
     _check(load().wedge_run_pr(handle, _ptr(rank), int(iters), float(damping), _opts(opts),
                                ctypes.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
+
+
+def wedge_csc_relabel_by_degree(V, E, offsets, src, w, new_offsets, new_src, new_w, new_of_old, old_of_new=None,
+                                stream=None):
+    """Degree-ordered relabelling of a device CSC into the caller's device
+    arrays (int32/uint32 torch tensors)."""
+    _check(load().wedge_csc_relabel_by_degree(int(V), int(E), _ptr(offsets), _ptr(src), _ptr(w), _ptr(new_offsets),
+                                              _ptr(new_src), _ptr(new_w), _ptr(new_of_old), _ptr(old_of_new),
+                                              _stream(stream)))
+
+
+def wedge_permute_rows(V, width, new_of_old, vals_in, vals_out, stream=None):
+    """vals_out[v * width + c] = vals_in[new_of_old[v] * width + c] (32-bit words)."""
+    _check(load().wedge_permute_rows(int(V), int(width), _ptr(new_of_old), _ptr(vals_in), _ptr(vals_out),
+                                     _stream(stream)))
+
+
+def wedge_cc_labels_to_original(V, old_of_new, labels, scratch, out, stream=None):
+    """Component labels of a relabelled graph named by their smallest original id."""
+    _check(load().wedge_cc_labels_to_original(int(V), _ptr(old_of_new), _ptr(labels), _ptr(scratch), _ptr(out),
+                                              _stream(stream)))
 
 
 def wedge_trim_memory(device=-1):
