@@ -895,7 +895,7 @@ def bench_grid(args, wedge, torch, dev, world):
 # that launch's ncu gpu__time_duration in us, and a digest of the device code
 # of the captured kernel (KERNEL_FILES): reported only while that code is
 # unchanged.  (None, None, None): no capture on the current code yet.
-TRAFFIC = {"pr": (321630976, 252.160, "0eb7e3a1a22c9483"), "cc": (607843072, 505.888, "0eb7e3a1a22c9483")}
+TRAFFIC = {"pr": (None, None, None), "cc": (None, None, None)}
 # The sources each captured kernel is built from.
 KERNEL_FILES = {"pr": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
                 "cc": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
@@ -1140,13 +1140,21 @@ def transform_balance(wedge, torch, G, g, stream, dev):
             rec = None
             for _ in range(3):
                 rec = wedge.wedge_frontier_transform_profile(G.handle, bm, 0, sched, clist, cnt)
-            t = _time_launch(torch, stream, lambda: wedge.wedge_frontier_transform_profile(
-                G.handle, bm, 0, sched, clist, cnt), reps=5)
+            # the library's schedule through its plain entry point; the
+            # paper's exists only in the profiling call (whose record copy
+            # adds a little host time to its 5 ms)
+            t = _time_launch(torch, stream, (lambda: wedge.wedge_frontier_transform(G.handle, bm, 0, clist, cnt))
+                             if sched == 0 else (lambda: wedge.wedge_frontier_transform_profile(
+                                 G.handle, bm, 0, sched, clist, cnt)), reps=5)
             kern = {"scan": balance_summary(rec, 0), "expand": balance_summary(rec, 1)} if sched == 0 else \
                 {"slices": balance_summary(rec, 0)}
-            res["library" if sched == 0 else "paper_static_slices"] = {"ms": t * 1e3, "kernels": kern}
+            span = sum(k["span_us"] for k in kern.values())
+            res["library" if sched == 0 else "paper_static_slices"] = {"ms": t * 1e3, "kernels": kern,
+                                                                       "kernel_span_us": span}
             res["list_entries"] = int(cnt.item())
         res["speedup_library_vs_paper"] = res["paper_static_slices"]["ms"] / res["library"]["ms"]
+        res["speedup_library_vs_paper_kernel_span"] = (res["paper_static_slices"]["kernel_span_us"] /
+                                                       res["library"]["kernel_span_us"])
         out[name] = res
     return out
 

@@ -139,7 +139,9 @@ typedef struct {
     uint32_t log2_coarsen; /* precision of the entries (as in wedge_opts) */
     uint32_t nchunks;   /* Wedge Frontier entries pulled at t (mode 1) */
     uint32_t rowsum;    /* sum over F_t of edge-index row lengths (chunks at k=0) */
-    uint32_t npieces;   /* work pieces handed to the transformation */
+    uint32_t npieces;   /* work pieces handed to the transformation (0 when it
+                         * expanded the listed rows directly: frontier listed
+                         * completely, every row <= 32 entries, k >= 0) */
     uint64_t t_pull_ns; /* device time of the pull (globaltimer), 0 if unknown */
     uint64_t t_xform_ns;/* device time of the transformation feeding t */
 } wedge_iter_record;

@@ -77,8 +77,10 @@ struct IterRec {
     unsigned int nlist;           // F_t vertices written to the frontier list
                                   // (the list is complete iff nlist == nfront)
     unsigned int nlong;           // F_t's long edge-index rows listed for the transformation
+    unsigned int rowmax;          // max |eidx row| over F_t
+    unsigned int pad_;
 };
-static_assert(sizeof(IterRec) == 72, "IterRec layout");
+static_assert(sizeof(IterRec) == 80, "IterRec layout");
 constexpr int kListCap = 1024;  // frontier-list entries a pull block stages in shared memory
 constexpr int kMaxPullBlocks = 4096;
 
@@ -89,7 +91,7 @@ struct BlockStat {
     unsigned int n;        // vertices it activated
     unsigned int row;      // their edge-index row lengths
     unsigned int lcnt;     // vertices it staged for the next frontier list (> kListCap: overflow)
-    unsigned int pad_;
+    unsigned int rowmax;   // the longest of their edge-index rows
 };
 
 // Run control block (device).

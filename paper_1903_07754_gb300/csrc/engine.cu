@@ -80,7 +80,7 @@ template <int APP>
 __global__ void __launch_bounds__(kXformThreads) k_push_expand(const PullParams P, const PushParams Q) {
     __shared__ uint32_t s_list[kListCap];
     __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row, s_lcnt;
+    __shared__ unsigned s_n, s_row, s_rmax, s_lcnt;
     RunCtl* C = P.ctl;
     if (C->done) return;
     const unsigned it = C->it;
@@ -90,12 +90,13 @@ __global__ void __launch_bounds__(kXformThreads) k_push_expand(const PullParams 
         s_F = 0;
         s_n = 0;
         s_row = 0;
+        s_rmax = 0;
         s_lcnt = 0;
         if (P.trace && blockIdx.x == 0) P.rec[it].t_pull0 = global_timer();
     }
     __syncthreads();
     uint32_t* next = P.bm[(it + 1) & 1];
-    Stats st{0ull, 0u, 0u};
+    Stats st{0ull, 0u, 0u, 0u};
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long gw = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kXformThreads) k_push_expand(const PullParams 
             stage_list(act, v, &s_lcnt, s_list);
         }
     }
-    finish_block<true>(P, it, st, &s_F, &s_n, &s_row, &s_lcnt, s_list, reinterpret_cast<float*>(s_list));
+    finish_block<true>(P, it, st, &s_F, &s_n, &s_row, &s_rmax, &s_lcnt, s_list, reinterpret_cast<float*>(s_list));
 }
 
 // Initial frontier: size, fullness and edge-index work (the transformation
@@ -142,15 +143,16 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
     __shared__ __align__(16) unsigned char dsm_bytes[kDecideSmemBytes];
     float* dsm = reinterpret_cast<float*>(dsm_bytes);
     __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row, s_last;
+    __shared__ unsigned s_n, s_row, s_rmax, s_last;
     if (threadIdx.x == 0) {
         s_F = 0;
         s_n = 0;
         s_row = 0;
+        s_rmax = 0;
     }
     __syncthreads();
     unsigned long long F = 0;
-    unsigned n = 0, row = 0;
+    unsigned n = 0, row = 0, rmax = 0;
     const unsigned long long words = ((unsigned long long)V + 31) / 32;
     for (unsigned long long wi = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; wi < words;
          wi += (unsigned long long)gridDim.x * blockDim.x) {
@@ -160,18 +162,22 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
             const uint32_t u = (uint32_t)(wi * 32 + __ffs(word) - 1);
             F += outdeg[u];
             n += 1;
-            row += eidx_off[u + 1] - eidx_off[u];
+            const uint32_t len = eidx_off[u + 1] - eidx_off[u];
+            row += len;
+            rmax = max(rmax, len);
         }
     }
     for (int d = 16; d > 0; d >>= 1) {
         F += __shfl_down_sync(kFull, F, d);
         n += __shfl_down_sync(kFull, n, d);
         row += __shfl_down_sync(kFull, row, d);
+        rmax = max(rmax, __shfl_down_sync(kFull, rmax, d));
     }
     if ((threadIdx.x & 31) == 0 && n) {
         atomicAdd(&s_F, F);
         atomicAdd(&s_n, n);
         atomicAdd(&s_row, row);
+        atomicMax(&s_rmax, rmax);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -179,6 +185,7 @@ __global__ void k_frontier_stats(const uint32_t* __restrict__ bm, uint32_t V, co
             atomicAdd(&rec->fullness, s_F);
             atomicAdd(&rec->nfront, s_n);
             atomicAdd(&rec->rowsum, s_row);
+            atomicMax(&rec->rowmax, s_rmax);
         }
         __threadfence();
         s_last = atomicAdd(&C->ticket, 1u) == gridDim.x - 1;
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
             s_lcnt = 0;
         }
         __syncthreads();
-        Stats st{0ull, 0u, 0u};
+        Stats st{0ull, 0u, 0u, 0u};
         const uint32_t* cur = (it & 1) ? P.bm[1] : P.bm[0];
         uint32_t* next = (it & 1) ? P.bm[0] : P.bm[1];
         if constexpr (SSSP)
@@ -551,7 +558,7 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
         }
         if (!grid_sync(bar, &C->status)) break;
         if (sparse)
-            xform_expand_pieces<false>(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
+            xform_expand_pieces<kSrcPieces>(X.pieces, __ldcg(&P.rec[nit].npieces), C->k, X.eidx, X.wb, X.clist,
                                 &P.rec[nit].nchunks, gw, nw);
         if (!grid_sync(bar, &C->status)) break;
         it = nit;
@@ -950,7 +957,9 @@ static wedge_status build_loop_graph(wedge_graph* g, int app) {
         PullParams P = pull_params(g, 0, app);
         P.cond = cond;
         launch_pull_app(g, app, P, cs);
-        launch_xform(g, xform_params(g, 0), cs);
+        XformParams X = xform_params(g, 0);
+        X.direct = 1;
+        launch_xform(g, X, cs);
     }, &g->loop_exec[app]);
 }
 
@@ -1174,6 +1183,7 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
                                                     P.gf);
     count_launch(2);
     XformParams X = xform_params(g, trace);
+    X.direct = push ? 0 : 1;  // the hybrid's scan cuts out-edge rows for its push
     const uint32_t* result = g->vals;
     if (push) {
         X.eidx_off = g->csr_off;

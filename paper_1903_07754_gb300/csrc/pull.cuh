@@ -266,14 +266,19 @@ struct Stats {
     unsigned long long F;
     unsigned int n;
     unsigned int row;
+    unsigned int rowmax;
 };
 
 // A vertex activated for the next frontier: its out-degree (fullness), its
-// edge-index row length (a feature of the learned switch) and the count.
+// edge-index row length (a feature of the learned switch; the longest row
+// decides whether the transformation may expand rows directly) and the
+// count.
 __device__ __forceinline__ void count_active(const PullParams& P, uint32_t v, Stats& st) {
     st.F += __ldg(P.outdeg + v);
     st.n += 1;
-    st.row += __ldg(P.eidx_off + v + 1) - __ldg(P.eidx_off + v);
+    const uint32_t len = __ldg(P.eidx_off + v + 1) - __ldg(P.eidx_off + v);
+    st.row += len;
+    st.rowmax = max(st.rowmax, len);
 }
 
 // The block's frontier list (whole warp): one shared-memory reservation per
@@ -705,7 +710,7 @@ __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nbl
 // the slots and takes the decision for the next iteration.
 template <bool DECIDE>
 __device__ __forceinline__ void finish_block(const PullParams& P, unsigned it, Stats st, unsigned long long* s_F,
-                                             unsigned* s_n, unsigned* s_row, unsigned* s_lcnt,
+                                             unsigned* s_n, unsigned* s_row, unsigned* s_rmax, unsigned* s_lcnt,
                                              const uint32_t* s_list, float* dsm) {
     __shared__ unsigned s_lbase;
     if constexpr (DECIDE) {
@@ -714,11 +719,13 @@ __device__ __forceinline__ void finish_block(const PullParams& P, unsigned it, S
             st.F += __shfl_down_sync(kFull, st.F, d);
             st.n += __shfl_down_sync(kFull, st.n, d);
             st.row += __shfl_down_sync(kFull, st.row, d);
+            st.rowmax = max(st.rowmax, __shfl_down_sync(kFull, st.rowmax, d));
         }
         if ((threadIdx.x & 31) == 0 && st.n) {
             atomicAdd(s_F, st.F);
             atomicAdd(s_n, st.n);
             atomicAdd(s_row, st.row);
+            atomicMax(s_rmax, st.rowmax);
         }
     }
     __syncthreads();
@@ -728,7 +735,7 @@ __device__ __forceinline__ void finish_block(const PullParams& P, unsigned it, S
         b.n = *s_n;
         b.row = *s_row;
         b.lcnt = *s_lcnt;
-        b.pad_ = 0;
+        b.rowmax = *s_rmax;
         P.bstat[blockIdx.x] = b;
         s_lbase = (*s_lcnt && *s_lcnt <= (unsigned)kListCap) ? atomicAdd(&P.rec[it + 1].nlist, *s_lcnt) : ~0u;
     }
@@ -757,7 +764,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     using T = typename Traits<APP>::T;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_F;
-    __shared__ unsigned s_n, s_row, s_lcnt;
+    __shared__ unsigned s_n, s_row, s_rmax, s_lcnt;
     RunCtl* C = P.ctl;
     if (C->done) {
         // nothing left to pull: end the device loop (PageRank's pulls never
@@ -792,6 +799,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
         s_F = 0;
         s_n = 0;
         s_row = 0;
+        s_rmax = 0;
         s_lcnt = 0;
         if (P.trace && blockIdx.x == 0) P.rec[it].t_pull0 = global_timer();
         if constexpr (APP == kPR) {
@@ -808,7 +816,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
     __syncthreads();
     const uint32_t* cur = P.bm[it & 1];
     uint32_t* next = P.bm[(it + 1) & 1];
-    Stats st{0ull, 0u, 0u};
+    Stats st{0ull, 0u, 0u, 0u};
     const unsigned q = lane >> 2;
 
     if constexpr (!TMA) {
@@ -900,7 +908,8 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
         pull_sparse<APP>(P, it, k, nchunks, cur, next, my_kid, my_val, st, (unsigned long long)blockIdx.x * kCW + warp,
                          (unsigned long long)gridDim.x * kCW, &s_lcnt, s_list);
 
-    finish_block<APP != kPR>(P, it, st, &s_F, &s_n, &s_row, &s_lcnt, s_list, reinterpret_cast<float*>(smem));
+    finish_block<APP != kPR>(P, it, st, &s_F, &s_n, &s_row, &s_rmax, &s_lcnt, s_list,
+                             reinterpret_cast<float*>(smem));
 }
 
 // Decision step (Section 3.4, Fig. 5), taken by the last pull block to
@@ -912,7 +921,7 @@ __global__ void __launch_bounds__(TMA ? kPullThreads : kCW * 32, TMA ? 1 : direc
 // block's record buffer, free once the block's own slices are done.
 __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nblocks, float* dsm) {
     __shared__ unsigned long long d_F;
-    __shared__ unsigned d_n, d_row;
+    __shared__ unsigned d_n, d_row, d_rmax;
     IterRec* rec = P.rec;
     RunCtl* C = P.ctl;
     // the cost model's weights load while the slots are summed
@@ -922,25 +931,29 @@ __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nbl
         d_F = 0;
         d_n = 0;
         d_row = 0;
+        d_rmax = 0;
     }
     __syncthreads();
     // the slots were written by other blocks of this launch: read through L2
     unsigned long long F = 0;
-    unsigned n = 0, row = 0;
+    unsigned n = 0, row = 0, rmax = 0;
     for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
         F += __ldcg(&P.bstat[b].F);
         n += __ldcg(&P.bstat[b].n);
         row += __ldcg(&P.bstat[b].row);
+        rmax = max(rmax, __ldcg(&P.bstat[b].rowmax));
     }
     for (int d = 16; d > 0; d >>= 1) {
         F += __shfl_down_sync(kFull, F, d);
         n += __shfl_down_sync(kFull, n, d);
         row += __shfl_down_sync(kFull, row, d);
+        rmax = max(rmax, __shfl_down_sync(kFull, rmax, d));
     }
     if ((threadIdx.x & 31) == 0 && n) {
         atomicAdd(&d_F, F);
         atomicAdd(&d_n, n);
         atomicAdd(&d_row, row);
+        atomicMax(&d_rmax, rmax);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -948,6 +961,7 @@ __device__ void decide_after_pull(const PullParams& P, unsigned it, unsigned nbl
         r->fullness = d_F;
         r->nfront = d_n;
         r->rowsum = d_row;
+        r->rowmax = d_rmax;
         if (P.trace) rec[it].t_pull1 = global_timer();
     }
     __syncthreads();

@@ -113,12 +113,30 @@ __global__ void k_rl_fill(uint32_t* p, uint32_t V, uint32_t x) {
 }
 
 // Smallest old id per component: m[label of new vertex i] <- old id of i
-// (labels >= V, which no CC run produces, are skipped).
+// (labels >= V, which no CC run produces, are skipped).  Most vertices of
+// a warp share a label (the giant component), so each distinct label of a
+// warp takes one atomicMin with the warp's minimum for it.
 __global__ void k_rl_label_min(const uint32_t* __restrict__ labels, const uint32_t* __restrict__ old_of_new,
                                uint32_t V, uint32_t* __restrict__ m) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < V; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t l = labels[i];
-        if (l < V) atomicMin(m + l, old_of_new[i]);
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); i0 < V; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        uint32_t l = 0xFFFFFFFFu, o = 0xFFFFFFFFu;
+        if (i < V) {
+            l = labels[i];
+            o = old_of_new[i];
+        }
+        const bool valid = l < V;
+        unsigned todo = __ballot_sync(kFull, valid);
+        while (todo) {  // warp-uniform: one distinct label per round
+            const unsigned src = __ffs(todo) - 1;
+            const uint32_t lab = __shfl_sync(kFull, l, src);
+            const bool mine = valid && l == lab;
+            const uint32_t lo = __reduce_min_sync(kFull, mine ? o : 0xFFFFFFFFu);
+            if (lane == src) atomicMin(m + lab, lo);
+            todo &= ~__ballot_sync(kFull, mine);
+        }
     }
 }
 

@@ -27,6 +27,7 @@ struct XformParams {
     const uint32_t* eidx8;       // the edge index in 8-edge units (precisions k < 0)
     const uint32_t* eidx8_off;
     int trace;
+    int direct;                  // run mode: rows of at most 32 entries may be expanded by the scan
     // load-balance accounting of a standalone transformation (nullptr: off):
     // per warp and kernel {start ns, end ns, busy SM cycles, SM id}
     unsigned long long* wstat;
@@ -418,7 +419,13 @@ __device__ __forceinline__ uint32_t z_scan(uint32_t x, unsigned key, bool cont, 
 // packed differences over the block's lanes (a block cut by a round
 // boundary carries its last decoded entry into the next round).  The next
 // round's entries are loaded before the current round's atomics.
-template <bool Z>
+// SRC: kSrcPieces (pieces_v: uint2 pieces), kSrcZPieces (uint4 pieces of
+// the compressed index) or kSrcRows (pieces_v: a frontier list whose every
+// edge-index row, start eidx_off[u], has at most 32 entries: each row is
+// one piece).
+constexpr int kSrcPieces = 0, kSrcZPieces = 1, kSrcRows = 2;
+
+template <int SRC>
 __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsigned n, unsigned k,
                                                     const uint32_t* __restrict__ eidx, uint32_t* wb, uint32_t* list,
                                                     unsigned* count, unsigned long long gw, unsigned long long nw,
@@ -454,12 +461,20 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         const unsigned long long base = task * ppt;
         const unsigned long long idx = base + lane;
         const bool have = lane < ppt && idx < n;
-        uint2 pc;        // plain: {first entry, length}; Z: {header .x, header .y}
+        uint2 pc;        // plain, rows: {first entry, length}; Z: {header .x, header .y}
         unsigned plen;   // piece length
-        if constexpr (Z) {
+        if constexpr (SRC == kSrcZPieces) {
             const uint4 z = have ? __ldcg(static_cast<const uint4*>(pieces_v) + idx) : make_uint4(0u, 0u, 0u, 0u);
             pc = make_uint2(z.x, z.y);
             plen = z.z;
+        } else if constexpr (SRC == kSrcRows) {
+            pc = make_uint2(0u, 0u);
+            if (have) {
+                const uint32_t u = __ldcg(static_cast<const uint32_t*>(pieces_v) + idx);
+                pc.x = __ldg(eidx_off + u);
+                pc.y = __ldg(eidx_off + u + 1) - pc.x;
+            }
+            plen = pc.y;
         } else {
             pc = have ? __ldcg(static_cast<const uint2*>(pieces_v) + idx) : make_uint2(0u, 0u);
             plen = pc.y;
@@ -490,7 +505,7 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
             }
             const unsigned st = __shfl_sync(kFull, pc.x, jx);
             const unsigned ex = __shfl_sync(kFull, excl, jx);
-            if constexpr (Z) {
+            if constexpr (SRC == kSrcZPieces) {
                 const unsigned i = e - ex;
                 const unsigned hy = __shfl_sync(kFull, pc.y, jx);
                 const unsigned i_lane0 = __shfl_sync(kFull, i, 0);  // by every lane
@@ -531,7 +546,7 @@ __device__ __forceinline__ void xform_expand_pieces(const void* pieces_v, unsign
         const unsigned n_u = min(32u, len - q * 32u);
         const bool act = lane < n_u;
         uint32_t x;
-        if constexpr (Z) {
+        if constexpr (SRC == kSrcZPieces) {
             const uint2 h = __ldg(zhdr + __ldg(zbo + u) + q);
             x = z_scan(z_raw(act, lane, h.x, h.y, eidx), 0u, false, 0u);
         } else {
@@ -586,6 +601,18 @@ struct WarpStamp {
     }
 };
 
+// A run's transformation skips the pieces when the frontier is listed
+// completely, every row has at most 32 entries (one piece each; the pull
+// recorded the longest, in the chunk index) and the plain chunk index serves
+// the precision (k >= 0): the scan kernel then expands the listed rows
+// itself, up to 32 rows per warp task, and the expansion kernel has nothing
+// to do.  Both kernels evaluate this on the same record.
+__device__ __forceinline__ bool xform_direct(const XformParams& X, const IterRec* r, const IndexSel& ix,
+                                             unsigned long long nw) {
+    return X.direct && !ix.z && (int)r->k >= 0 && r->nlist == r->nfront && r->rowmax <= 32u &&
+           (unsigned long long)r->nfront <= 32ull * nw;
+}
+
 __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams X) {
     RunCtl* C = X.ctl;
     const uint32_t* bm;
@@ -611,6 +638,13 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_scan(const XformParams 
     r = X.rec + it;
     if (r->mode == 0) return;
     const IndexSel ix = select_index(X, (int)r->k);
+    if (xform_direct(X, r, ix, nth >> 5)) {
+        __shared__ uint32_t s_stage[kXformThreads / 32][kAppendStage];
+        xform_expand_pieces<kSrcRows>((it & 1) ? X.flist[1] : X.flist[0], r->nfront, ix.shift, ix.ei, X.wb, X.clist,
+                                      &X.rec[it].nchunks, tid >> 5, nth >> 5, s_stage[threadIdx.x >> 5], nullptr,
+                                      nullptr, 0, ix.eoff);
+        return;
+    }
     if (r->nlist == r->nfront) {
         xform_scan_list((it & 1) ? X.flist[1] : X.flist[0], r->nfront, ix.eoff, piece_out(X, &r->nlong, ix.z),
                         &r->npieces, tid >> 5, nth >> 5);
@@ -637,6 +671,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
         it = C->it;
         const IterRec* r = X.rec + it;
         if (r->mode == 0) return;
+        if (xform_direct(X, r, select_index(X, (int)r->k), ((unsigned long long)gridDim.x * blockDim.x) >> 5)) {
+            if (X.trace && threadIdx.x == 0) atomicMax(&X.rec[it].t_xf1, global_timer());
+            return;  // the scan kernel expanded the rows
+        }
         n = r->npieces;
         nlong = r->nlong;
         k = (int)r->k;
@@ -688,10 +726,10 @@ __global__ void __launch_bounds__(kXformThreads) k_xform_expand(const XformParam
     WarpStamp ws;
     ws.start(X);
     if (ix.z)
-        xform_expand_pieces<true>(X.zpieces, n, ix.shift, X.zwords, X.wb, X.clist, count, gw, nw,
+        xform_expand_pieces<kSrcZPieces>(X.zpieces, n, ix.shift, X.zwords, X.wb, X.clist, count, gw, nw,
                                   s_stage[threadIdx.x >> 5], X.longs, s_lpre, nlong, ix.eoff, X.zbo, X.zhdr, X.task_ctr);
     else
-        xform_expand_pieces<false>(X.pieces, n, ix.shift, ix.ei, X.wb, X.clist, count, gw, nw,
+        xform_expand_pieces<kSrcPieces>(X.pieces, n, ix.shift, ix.ei, X.wb, X.clist, count, gw, nw,
                                    s_stage[threadIdx.x >> 5], X.longs, s_lpre, nlong, ix.eoff, nullptr, nullptr,
                                    X.task_ctr);
     if (X.standalone) ws.stop(X, gw, 1);
