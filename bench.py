@@ -249,7 +249,8 @@ def main():
     ap.add_argument("--ref-pr-iters", type=int, default=PR_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=["cc-dense", "pr", "step", "frontier-traced", "xform"],
+    ap.add_argument("--profile-case", default=None,
+                    choices=["cc-dense", "pr", "pr-relabel", "step", "frontier-traced", "xform"],
                     help="run only one small case for a profiler (no JSON line)")
     ap.add_argument("--config", default="s22", choices=["s22", "learned-s24", "batch-s26", "grid", "studies"],
                     help="s22: the benchmark line (R-MAT s22, four apps); the others print one line each "
@@ -321,11 +322,21 @@ def main():
             torch.cuda.cudart().cudaProfilerStop()
         elif args.profile_case == "xform":
             print(json.dumps(transform_case(wedge, torch, G, g, od, stream, dev)))
-        elif args.profile_case == "pr":
+        elif args.profile_case in ("pr", "pr-relabel"):
+            H = G
+            if args.profile_case == "pr-relabel":  # the same pulls on the degree-relabelled copy
+                arr = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev) for a in (g.offsets, g.src)]
+                noff = torch.empty(g.V + 1, dtype=torch.int32, device=dev)
+                nsrc = torch.empty(g.E, dtype=torch.int32, device=dev)
+                o2n = torch.empty(g.V, dtype=torch.int32, device=dev)
+                wedge.wedge_csc_relabel_by_degree(g.V, g.E, arr[0], arr[1], None, noff, nsrc, None, o2n)
+                H = wedge.Graph(wedge.wedge_graph_create(g.V, g.E, noff, nsrc), keep=[noff, nsrc])
             r = torch.empty(g.V, dtype=torch.float32, device=dev)
             for _ in range(2):
-                wedge.wedge_run_pr(G.handle, r, 3, DAMPING, None, False)
+                wedge.wedge_run_pr(H.handle, r, 3, DAMPING, None, False)
             torch.cuda.synchronize()
+            if H is not G:
+                H.close()
         else:
             # the step's frontier runs through the host-polled loop (traced
             # runs), so that a profiler sees every kernel launch
@@ -895,7 +906,7 @@ def bench_grid(args, wedge, torch, dev, world):
 # that launch's ncu gpu__time_duration in us, and a digest of the device code
 # of the captured kernel (KERNEL_FILES): reported only while that code is
 # unchanged.  (None, None, None): no capture on the current code yet.
-TRAFFIC = {"pr": (None, None, None), "cc": (None, None, None)}
+TRAFFIC = {"pr": (322008832, 250.560, "d3a1448951028afa"), "cc": (607921920, 506.624, "d3a1448951028afa")}
 # The sources each captured kernel is built from.
 KERNEL_FILES = {"pr": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
                 "cc": ("pull.cuh", "common.cuh", "tma.cuh", "mlp.cuh"),
