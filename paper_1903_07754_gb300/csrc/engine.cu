@@ -660,12 +660,22 @@ __global__ void k_ctl_init(RunCtl* C, RunCtl init) {
     if (threadIdx.x == 0) *C = init;
 }
 
+// Leaves the Wedge bitmap clear after a standalone transformation: the
+// words of the listed entries, or, for a long list, every word the
+// precision uses (`used_words`, 16-byte stores; the bitmap is allocated in
+// whole 16-byte units).
 __global__ void k_clear_listed(const uint32_t* __restrict__ list, const uint32_t* __restrict__ count,
-                               uint32_t* __restrict__ wb) {
+                               uint32_t* __restrict__ wb, unsigned long long used_words) {
     const unsigned n = *count;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        wb[list[i] >> 5] = 0u;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    if ((unsigned long long)n * 8 >= used_words) {
+        uint4* w4 = reinterpret_cast<uint4*>(wb);
+        const unsigned long long n4 = (used_words + 3) / 4;
+        for (unsigned long long i = tid; i < n4; i += nth) w4[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (unsigned long long i = tid; i < n; i += nth) wb[list[i] >> 5] = 0u;
+    }
 }
 
 __global__ void k_standalone_prep(IterRec* rec, RunCtl* C, unsigned iter, unsigned sparse, unsigned k,
@@ -788,7 +798,7 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s) {
     // the Wedge bitmap, list and pieces are sized for the finest entries
     // (8 edges), so that a finer precision never reallocates them
     const uint64_t NU8 = (g->E + 7) / 8;
-    g->wb_words = (NU8 + 31) / 32 + 1;
+    g->wb_words = ((NU8 + 31) / 32 + 1 + 3) / 4 * 4;  // whole 16-byte units (cleared with 16-byte stores)
     g->clist_cap = NU8 + 1;
     g->pieces_cap = std::max(g->npieces_max, g->npieces_outdeg_bound) + 1;
     WEDGE_TRY(dev_alloc(g, (void**)&g->wb, g->wb_words * 4));
@@ -971,6 +981,13 @@ static bool valid_precision(uint32_t k) { return (int)k >= -2 && (int)k <= (int)
 static uint64_t entries_at(const wedge_graph* g, int k) {
     const unsigned sh = (unsigned)(5 + k);
     return (g->E + (1ull << sh) - 1) >> sh;
+}
+
+// Wedge bitmap words those entries use (at most the allocated words, which
+// cover 8-edge entries and are a whole number of 16-byte units).
+static uint64_t wb_words_at(const wedge_graph* g, int k) {
+    const uint64_t w = (entries_at(g, k) + 31) / 32;
+    return w < g->wb_words ? w : g->wb_words;
 }
 
 // Finer precisions than one chunk need the edge index in 8-edge units,
@@ -1556,7 +1573,8 @@ wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_
     X.standalone = 1;
     X.standalone_k = (int)log2_coarsen;
     launch_xform(g, X, s);
-    k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
+    k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb,
+                                                  wb_words_at(g, (int)log2_coarsen));
     count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
@@ -1597,7 +1615,8 @@ wedge_status wedge_frontier_transform_profile(wedge_graph_t g, const uint32_t* d
         k_xform_static<<<g->xform_blocks, kXformThreads, 0, s>>>(X);
         count_launch();
     }
-    k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb);
+    k_clear_listed<<<g->num_sms * 4, 256, 0, s>>>(d_chunk_list, d_chunk_count, g->wb,
+                                                  wb_words_at(g, (int)log2_coarsen));
     count_launch();
     WEDGE_TRY_CUDA(cudaGetLastError());
     return WEDGE_OK;
