@@ -114,3 +114,49 @@ def test_compressed_edge_index_scale22(g22):
             np.testing.assert_array_equal(u32(out)[: g22.V], oracle.sssp_dijkstra(g22, 0))
     finally:
         G.close()
+
+
+def test_relabelled_scale22(g22):
+    """The degree relabelling of the benchmark graph (its locality study):
+    the new ids follow descending out-degree with ties by old id, the
+    relabelled CSC holds every destination's in-edges renamed, and BFS,
+    SSSP and PageRank on it, mapped back, equal the oracle on the original."""
+    from _gpu import dev_u32
+    g = g22
+    V, E = g.V, g.E
+    off, src, w = dev_u32(g.offsets), dev_u32(g.src), dev_u32(g.w)
+    noff, nsrc, nw = empty_u32(V + 1), empty_u32(E), empty_u32(E)
+    o2n, n2o = empty_u32(V), empty_u32(V)
+    wedge.wedge_csc_relabel_by_degree(V, E, off, src, w, noff, nsrc, nw, o2n, n2o)
+    od = np.bincount(g.src.astype(np.int64), minlength=V)
+    want_n2o = np.argsort(-od, kind="stable")
+    np.testing.assert_array_equal(u32(n2o)[:V], want_n2o)
+    new_of_old = np.empty(V, dtype=np.int64)
+    new_of_old[want_n2o] = np.arange(V)
+    np.testing.assert_array_equal(u32(o2n)[:V], new_of_old)
+    indeg = np.diff(g.offsets.astype(np.int64))
+    np.testing.assert_array_equal(np.diff(u32(noff)[: V + 1].astype(np.int64)), indeg[want_n2o])
+    # renamed sources: the multiset of (new destination, new source, weight) is the original's
+    dst_new = np.repeat(np.arange(V, dtype=np.int64), indeg[want_n2o])
+    got = (dst_new << 32) | u32(nsrc)[:E].astype(np.int64)
+    want = (new_of_old[g.dst().astype(np.int64)] << 32) | new_of_old[g.src.astype(np.int64)]
+    order_got, order_want = np.argsort(got, kind="stable"), np.argsort(want, kind="stable")
+    np.testing.assert_array_equal(got[order_got], want[order_want])
+    np.testing.assert_array_equal(u32(nw)[:E][order_got], g.w[order_want])
+    G = wedge.Graph.from_csc(gg.Graph(V, u32(noff)[: V + 1].copy(), u32(nsrc)[:E].copy(), u32(nw)[:E].copy()))
+    try:
+        out, back = empty_u32(V), empty_u32(V)
+        root = int(u32(o2n)[0])
+        wedge.wedge_run_bfs(G.handle, root, out)
+        wedge.wedge_permute_rows(V, 1, o2n, out, back)
+        np.testing.assert_array_equal(u32(back)[:V], oracle.bfs_push(g, 0))
+        wedge.wedge_run_sssp(G.handle, root, out)
+        wedge.wedge_permute_rows(V, 1, o2n, out, back)
+        np.testing.assert_array_equal(u32(back)[:V], oracle.sssp_dijkstra(g, 0))
+        rank = torch.empty(V, dtype=torch.float32, device="cuda")
+        rb = torch.empty_like(rank)
+        wedge.wedge_run_pr(G.handle, rank, 20, 0.85)
+        wedge.wedge_permute_rows(V, 1, o2n, rank, rb)
+        assert np.abs(rb.cpu().numpy().astype(np.float64) - oracle.pr_pull(g, 0.85, 20)).sum() <= 1e-6
+    finally:
+        G.close()
