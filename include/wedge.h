@@ -421,6 +421,18 @@ wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const u
                                  uint32_t nroots, uint32_t nqueries, uint32_t* d_levels,
                                  const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
 
+/* wedge_run_bfs_batch with 8-bit levels: d_levels (device, V * nqueries
+ * bytes, vertex-major) receives each hop distance as one byte, 0xFF if
+ * unreached -- a quarter of the 32-bit output's memory and writes, for
+ * queries whose levels stay below 255.  A pull that reaches a vertex at
+ * level 255 or more writes nothing for it and stops the run; the call then
+ * returns NOT_SUPPORTED (the levels below 255 are written and exact; use
+ * the 32-bit call).  The call waits for the run to end (it reads that check
+ * back).  Other arguments and errors as above. */
+wedge_status wedge_run_bfs_batch_u8(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
+                                    uint32_t nroots, uint32_t nqueries, uint8_t* d_levels,
+                                    const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
+
 /* Batched SSSP (not in the paper): up to 64 single-source shortest-path
  * queries in one run (multi-source Bellman-Ford), with the arguments,
  * layout and errors of wedge_run_bfs_batch:

@@ -110,6 +110,7 @@ struct RunCtl {
     unsigned int pad_;
 };
 constexpr unsigned int kStatusMaxIters = 1u;
+constexpr unsigned int kStatusLevelOverflow = 4u;  // 8-bit batched levels: a level of 255 or more was needed
 
 }  // namespace wedge
 
@@ -193,7 +194,7 @@ struct wedge_graph {
     int ms_occ_sssp = 0;             // ... and of the batched SSSP kernel
     cudaGraphExec_t ms_exec = nullptr;
     uint32_t ms_exec_q = 0, ms_exec_n = 0;
-    uint32_t* ms_exec_levels = nullptr;
+    void* ms_exec_levels = nullptr;
     uint32_t ms_exec_key[5] = {0, 0, 0, 0, 0};  // tau, k, switch, max_iters, SSSP
     bool ms_graph_failed = false;
     uint64_t device_bytes = 0;

@@ -342,13 +342,14 @@ __global__ void k_msbfs_clear(uint32_t V, unsigned long long* fb0, unsigned long
 
 __global__ void k_msbfs_roots(const uint32_t* __restrict__ roots, const uint32_t* __restrict__ rq, uint32_t nroots,
                               uint32_t Q, unsigned long long* fb0, unsigned long long* seen, uint32_t* levels,
-                              uint32_t* bm0) {
+                              uint8_t* levels8, uint32_t* bm0) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += gridDim.x * blockDim.x) {
         const uint32_t v = roots[i], q = rq[i];
         const unsigned long long bit = 1ull << q;
         atomicOr(fb0 + v, bit);
         atomicOr(seen + v, bit);
-        levels[(size_t)v * Q + q] = 0u;
+        if (levels8) levels8[(size_t)v * Q + q] = 0u;
+        else levels[(size_t)v * Q + q] = 0u;
         atomicOr(bm0 + (v >> 5), 1u << (v & 31));
     }
 }
@@ -532,14 +533,16 @@ __global__ void __launch_bounds__(kCW * 32) k_msbfs(const PullParams P, const Xf
         if (C->switch_mode == WEDGE_SWITCH_ALWAYS_DENSE) sparse = 0;
         else if (C->switch_mode == WEDGE_SWITCH_ALWAYS_SPARSE) sparse = 1;
         else sparse = (F * 10000ull < (unsigned long long)C->tau_bp * C->E) ? 1u : 0u;
-        const bool done = nf == 0 || nit >= C->max_iters;
+        // 8-bit levels: the pull found a vertex at level 255 or more
+        const bool overflow = P.levels8 != nullptr && (__ldcg(&C->status) & kStatusLevelOverflow) != 0;
+        const bool done = nf == 0 || nit >= C->max_iters || overflow;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             P.rec[nit].mode = sparse;
             P.rec[nit].k = C->k;
             C->it = nit;
             if (done) {
                 C->done = 1;
-                if (nf) C->status |= kStatusMaxIters;
+                if (nf && !overflow) C->status |= kStatusMaxIters;
             }
         }
         if (done) break;
@@ -1241,13 +1244,14 @@ static wedge_status run_frontier_app(wedge_graph* g, int app, uint32_t root, uin
 
 // Batched BFS: everything after the roots' upload, enqueued on s (also the
 // body of the captured graph).
-static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, uint32_t* levels, const RunCtl& init,
-                                  bool sssp, cudaStream_t s) {
-    WEDGE_TRY_CUDA(cudaMemsetAsync(levels, 0xFF, (size_t)g->V * Q * 4, s));
+static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, void* levels, bool u8,
+                                  const RunCtl& init, bool sssp, cudaStream_t s) {
+    WEDGE_TRY_CUDA(cudaMemsetAsync(levels, 0xFF, (size_t)g->V * Q * (u8 ? 1 : 4), s));
     k_msbfs_clear<<<g->num_sms * 4, 256, 0, s>>>(g->V, g->ms_fb[0], g->ms_fb[1], g->ms_seen, g->bm[0], g->bm[1], g->wb,
                                                  g->wb_words, g->rec, g->ctl, init, g->ms_bar);
     k_msbfs_roots<<<(nroots + 255) / 256, 256, 0, s>>>(g->ms_roots, g->ms_roots + g->ms_cap, nroots, Q, g->ms_fb[0],
-                                                       g->ms_seen, levels, g->bm[0]);
+                                                       g->ms_seen, u8 ? nullptr : static_cast<uint32_t*>(levels),
+                                                       u8 ? static_cast<uint8_t*>(levels) : nullptr, g->bm[0]);
     PullParams P = pull_params(g, 0, kBFS);
     P.mlp = nullptr;
     P.visk = nullptr;  // per-query visits live in the seen masks
@@ -1255,7 +1259,8 @@ static wedge_status msbfs_enqueue(wedge_graph* g, uint32_t nroots, uint32_t Q, u
     P.fb[0] = g->ms_fb[0];
     P.fb[1] = g->ms_fb[1];
     P.seen = g->ms_seen;
-    P.levels = levels;
+    P.levels = u8 ? nullptr : static_cast<uint32_t*>(levels);
+    P.levels8 = u8 ? static_cast<uint8_t*>(levels) : nullptr;
     P.Q = Q;
     XformParams X = xform_params(g, 0);
     X.zhdr = nullptr;  // batched runs read the plain edge index, all rows as pieces
@@ -1465,7 +1470,7 @@ wedge_status wedge_selftest_timeout(int kind) {
 namespace wedge {
 // Batched BFS (sssp = false) or SSSP (sssp = true) of up to 64 queries.
 static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, const uint32_t* root_query,
-                              uint32_t nroots, uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts_in,
+                              uint32_t nroots, uint32_t nqueries, void* d_levels, bool u8, const wedge_opts* opts_in,
                               wedge_stats* stats, cudaStream_t s) {
     if (!g || !roots || !d_levels) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
     if (sssp && !g->w && g->E) return set_error(WEDGE_ERR_INVALID_ARG, "SSSP needs edge weights");
@@ -1497,7 +1502,7 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
     init.tau_bp = o.tau_bp;
     init.k = o.log2_coarsen;
     init.E = g->E;
-    const uint32_t key[5] = {init.tau_bp, init.k, init.switch_mode, init.max_iters, sssp ? 1u : 0u};
+    const uint32_t key[5] = {init.tau_bp, init.k, init.switch_mode, init.max_iters, (sssp ? 1u : 0u) | (u8 ? 2u : 0u)};
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     const bool reuse = g->ms_exec && g->ms_exec_q == nqueries && g->ms_exec_n == nroots &&
                        g->ms_exec_levels == d_levels && !memcmp(key, g->ms_exec_key, sizeof(key));
@@ -1509,7 +1514,7 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
         wedge_status es = WEDGE_OK;
-        if (e == cudaSuccess) es = msbfs_enqueue(g, nroots, nqueries, d_levels, init, sssp, g->cap_stream);
+        if (e == cudaSuccess) es = msbfs_enqueue(g, nroots, nqueries, d_levels, u8, init, sssp, g->cap_stream);
         cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(g->cap_stream, &graph) : e;
         if (e == cudaSuccess && es == WEDGE_OK && ee == cudaSuccess &&
             cudaGraphInstantiate(&g->ms_exec, graph, 0) == cudaSuccess) {
@@ -1529,13 +1534,19 @@ static wedge_status run_batch(wedge_graph* g, bool sssp, const uint32_t* roots, 
         WEDGE_TRY_CUDA(cudaGraphLaunch(g->ms_exec, s));
         count_launch(4);
     } else {
-        WEDGE_TRY(msbfs_enqueue(g, nroots, nqueries, d_levels, init, sssp, s));
+        WEDGE_TRY(msbfs_enqueue(g, nroots, nqueries, d_levels, u8, init, sssp, s));
     }
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev1, s));
     WEDGE_TRY_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, s));
     g->last_stream = s;
     g->last_trace = false;
     g->last_push = false;
+    if (u8) {  // whether every level fit 8 bits is known only once the run ends
+        WEDGE_TRY_CUDA(cudaStreamSynchronize(s));
+        if (g->h_ctl->status & kStatusLevelOverflow)
+            return set_error(WEDGE_ERR_NOT_SUPPORTED,
+                             "a level of 255 or more: 8-bit levels do not fit; use wedge_run_bfs_batch");
+    }
     if (!stats) return WEDGE_OK;
     return fill_stats(g, s, stats);
 }
@@ -1546,13 +1557,21 @@ extern "C" {
 wedge_status wedge_run_bfs_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query, uint32_t nroots,
                                  uint32_t nqueries, uint32_t* d_levels, const wedge_opts* opts, wedge_stats* stats,
                                  wedge_stream_t stream) {
-    return run_batch(g, false, roots, root_query, nroots, nqueries, d_levels, opts, stats, (cudaStream_t)stream);
+    return run_batch(g, false, roots, root_query, nroots, nqueries, d_levels, false, opts, stats,
+                     (cudaStream_t)stream);
+}
+
+wedge_status wedge_run_bfs_batch_u8(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
+                                    uint32_t nroots, uint32_t nqueries, uint8_t* d_levels, const wedge_opts* opts,
+                                    wedge_stats* stats, wedge_stream_t stream) {
+    return run_batch(g, false, roots, root_query, nroots, nqueries, d_levels, true, opts, stats,
+                     (cudaStream_t)stream);
 }
 
 wedge_status wedge_run_sssp_batch(wedge_graph_t g, const uint32_t* roots, const uint32_t* root_query,
                                   uint32_t nroots, uint32_t nqueries, uint32_t* d_dist, const wedge_opts* opts,
                                   wedge_stats* stats, wedge_stream_t stream) {
-    return run_batch(g, true, roots, root_query, nroots, nqueries, d_dist, opts, stats, (cudaStream_t)stream);
+    return run_batch(g, true, roots, root_query, nroots, nqueries, d_dist, false, opts, stats, (cudaStream_t)stream);
 }
 
 wedge_status wedge_frontier_transform(wedge_graph_t g, const uint32_t* d_vertex_bitmap, uint32_t log2_coarsen,

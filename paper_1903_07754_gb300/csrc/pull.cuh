@@ -72,6 +72,7 @@ struct PullParams {
     unsigned long long* fb[2];   // frontier masks by iteration parity
     unsigned long long* seen;    // queries that have reached each vertex
     uint32_t* levels;            // levels[v * Q + q]
+    uint8_t* levels8;            // non-null: 8-bit batched BFS levels instead (0xFF: unreached)
     uint32_t Q;
     uint32_t* flist[2];          // frontier vertex lists by iteration parity
     BlockStat* bstat;            // per-block results
@@ -466,8 +467,15 @@ __device__ __forceinline__ void apply_records(const PullParams& P, unsigned it, 
                     fresh = m & ~atomicOr(P.seen + dv, m);
                 }
                 if (fresh) {
-                    for (unsigned long long b = fresh; b; b &= b - 1)
-                        P.levels[(size_t)dv * P.Q + (__ffsll((long long)b) - 1)] = it + 1;
+                    if (P.levels8 && it + 1 >= 255u) {
+                        atomicOr(&P.ctl->status, kStatusLevelOverflow);  // not representable: the run stops
+                    } else {
+                        for (unsigned long long b = fresh; b; b &= b - 1) {
+                            const size_t at = (size_t)dv * P.Q + (__ffsll((long long)b) - 1);
+                            if (P.levels8) P.levels8[at] = (uint8_t)(it + 1);
+                            else P.levels[at] = it + 1;
+                        }
+                    }
                     if (excl) {
                         prev = __ldcg(nxt + dv);
                         nxt[dv] = prev | fresh;

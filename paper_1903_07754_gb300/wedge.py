@@ -72,7 +72,7 @@ EXPORTS = [
     "wedge_mlp_adam", "wedge_set_cost_model", "wedge_trace_candidates", "wedge_run_bfs_batch",
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
     "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z", "wedge_set_learned_band",
-    "wedge_csc_relabel_by_degree", "wedge_permute_rows", "wedge_cc_labels_to_original",
+    "wedge_csc_relabel_by_degree", "wedge_permute_rows", "wedge_cc_labels_to_original", "wedge_run_bfs_batch_u8",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(wedge_stats), P]),
         "wedge_run_sssp_batch": (st, [P, P, P, u32, u32, P, ctypes.POINTER(wedge_opts),
                                      ctypes.POINTER(wedge_stats), P]),
+        "wedge_run_bfs_batch_u8": (st, [P, P, P, u32, u32, P, ctypes.POINTER(wedge_opts),
+                                        ctypes.POINTER(wedge_stats), P]),
         "wedge_mlp_forward": (st, [P, P, u32, P, P]),
         "wedge_mlp_forward_bf16": (st, [P, P, u32, P, P]),
         "wedge_mlp_loss_grad": (st, [P, P, P, u32, P, P, P]),
@@ -336,6 +338,16 @@ def wedge_run_bfs_batch(handle, roots, root_query, nqueries, levels, opts=None, 
     st = wedge_stats()
     _check(load().wedge_run_bfs_batch(handle, _ptr(r), _ptr(q), int(r.size), int(nqueries), _ptr(levels), _opts(opts),
                                       ctypes.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def wedge_run_bfs_batch_u8(handle, roots, root_query, nqueries, levels, opts=None, want_stats=True, stream=None):
+    """levels: device tensor of V * nqueries uint8 (vertex-major, 0xFF unreached)."""
+    r = np.ascontiguousarray(roots, dtype=np.uint32)
+    q = None if root_query is None else np.ascontiguousarray(root_query, dtype=np.uint32)
+    st = wedge_stats()
+    _check(load().wedge_run_bfs_batch_u8(handle, _ptr(r), _ptr(q), int(r.size), int(nqueries), _ptr(levels),
+                                         _opts(opts), ctypes.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
 
 

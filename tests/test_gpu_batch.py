@@ -144,3 +144,68 @@ def test_sssp_batch_needs_weights(g15_dev):
     d = torch.empty(g15_dev.V * 2, dtype=torch.int32, device="cuda")
     with pytest.raises(wedge.WedgeError):
         wedge.wedge_run_sssp_batch(g15_dev.handle, [0, 1], None, 2, d)
+
+
+def _levels8(G, V, roots, rq, Q, o=None):
+    lv = torch.empty(V * Q, dtype=torch.uint8, device="cuda")
+    st = wedge.wedge_run_bfs_batch_u8(G.handle, roots, rq, Q, lv, o)
+    return lv.cpu().numpy().reshape(V, Q), st
+
+
+def _as_u8(levels32):
+    return np.where(levels32 == INF, 0xFF, levels32).astype(np.uint8)
+
+
+@pytest.mark.parametrize("mode", ["default", "sparse0", "dense"])
+def test_u8_levels_equal_u32_levels(g15, g15_dev, mode):
+    roots = gg.roots(g15, 64, seed=11).astype(np.uint32)
+    o = {"default": opts("bfs"), "dense": opts("bfs", switch=wedge.SWITCH_ALWAYS_DENSE),
+         "sparse0": opts("bfs", switch=wedge.SWITCH_ALWAYS_SPARSE, k=0)}[mode]
+    l8, st8 = _levels8(g15_dev, g15.V, roots, None, 64, o)
+    l32, st32 = _levels(g15_dev, g15.V, roots, None, 64, o)
+    np.testing.assert_array_equal(l8, _as_u8(l32))
+    for q in (0, 31, 63):
+        np.testing.assert_array_equal(l8[:, q], _as_u8(oracle.bfs_push(g15, int(roots[q]))))
+    assert st8.iters == st32.iters
+    # the 32-bit and 8-bit runs replay their own captured graphs
+    l8b, _ = _levels8(g15_dev, g15.V, roots, None, 64, o)
+    np.testing.assert_array_equal(l8b, l8)
+
+
+def test_u8_uneven_batch():
+    graphs = [gg.rmat(8 + (i % 4), 8, seed=300 + i) for i in range(20)]
+    big, base = gg.block_diagonal(graphs)
+    G = graph(big, with_weights=False)
+    try:
+        rq = (np.arange(20) % 7).astype(np.uint32)
+        l8, _ = _levels8(G, big.V, base.astype(np.uint32), rq, 7)
+        l32, _ = _levels(G, big.V, base.astype(np.uint32), rq, 7)
+        np.testing.assert_array_equal(l8, _as_u8(l32))
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("n,fits", [(255, True), (300, False)])
+def test_u8_levels_checked_against_255(n, fits):
+    """A directed path of n vertices: levels 0 .. n-1.  Up to level 254 the
+    8-bit call returns them; a level of 255 or more makes it stop and
+    report that the levels do not fit (the levels it wrote are exact)."""
+    g = gg.from_edges(n, list(range(n - 1)), list(range(1, n)))
+    G = graph(g, with_weights=False)
+    try:
+        want = np.arange(n, dtype=np.int64)
+        if fits:
+            l8, _ = _levels8(G, n, np.array([0], dtype=np.uint32), None, 1)
+            np.testing.assert_array_equal(l8[:, 0], want.astype(np.uint8))
+        else:
+            lv = torch.empty(n, dtype=torch.uint8, device="cuda")
+            with pytest.raises(wedge.WedgeError) as e:
+                wedge.wedge_run_bfs_batch_u8(G.handle, np.array([0], dtype=np.uint32), None, 1, lv)
+            assert e.value.status == 5  # NOT_SUPPORTED
+            got = lv.cpu().numpy()
+            np.testing.assert_array_equal(got[:255], want[:255].astype(np.uint8))
+            assert np.all(got[255:] == 0xFF)
+            l32, _ = _levels(G, n, np.array([0], dtype=np.uint32), None, 1)
+            np.testing.assert_array_equal(l32[:, 0], want.astype(np.uint32))
+    finally:
+        G.close()
