@@ -280,9 +280,13 @@ def main():
     wbuild.build()
     wedge.load()
     if args.config != "s22":
-        line = {"learned-s24": bench_learned, "batch-s26": bench_batch, "grid": bench_grid,
-                "studies": bench_studies}[args.config](
-            args, wedge, torch, dev, world)
+        # clocks sampled over the whole configuration (its timed regions and
+        # the input generation between them)
+        with ClockSampler(local) as clk:
+            line = {"learned-s24": bench_learned, "batch-s26": bench_batch, "grid": bench_grid,
+                    "studies": bench_studies}[args.config](
+                args, wedge, torch, dev, world)
+        line["clocks"] = clk.summary()
         if rank == 0:
             print(json.dumps(line), flush=True)
         if world > 1:
@@ -1027,11 +1031,19 @@ def _time_launch(torch, stream, fn, before=None, reps=10, warm=2, best=False):
 
 
 def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
-    """PageRank's dense pull (k_pull<PR>) on the contributions of pr0, one
-    launch per CUDA-event pair (the sums are zeroed outside the pair)."""
+    """PageRank's dense pull (k_pull<PR>) on the contributions of pr0 as a
+    PageRank run executes it: contributions in the run's gather order
+    (`wedge_pr_order`, arranged outside the timed region) through
+    `wedge_pr_pull_ordered`, one launch per CUDA-event pair (the sums are
+    zeroed outside the pair).  The measured gather ceilings read the same
+    renamed sources and ordered contributions."""
     V, E = g.V, g.E
     od = torch.from_numpy(g.outdeg().astype(np.float32)).to(dev)
     contrib = torch.where(od > 0, (1.0 / V) / torch.clamp(od, min=1.0), torch.zeros_like(od)).contiguous()
+    order = torch.empty(V, dtype=torch.int32, device=dev)
+    wedge.wedge_pr_order(G.handle, order)
+    ordered = torch.empty_like(contrib)
+    ordered[order.long()] = contrib
     sums = torch.zeros(V, dtype=torch.int64, device=dev)
     times = []
     for r in range(12):
@@ -1039,7 +1051,7 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        wedge.wedge_pr_pull(G.handle, contrib, sums)
+        wedge.wedge_pr_pull_ordered(G.handle, ordered, sums)
         e1.record(stream)
         torch.cuda.synchronize()
         if r >= 2:
@@ -1050,9 +1062,11 @@ def roofline_pr_pull(wedge, torch, G, g, stream, dev, clocks):
     # other count takes every gather as one 32-byte sector
     alg = 4 * (V + 1) + 4 * E + 4 * V + 8 * V
     alg_sectors = 4 * (V + 1) + 4 * E + 32 * E + 8 * V
-    tp, tl = gather_ceilings(torch, stream, G.device_src, E, contrib)
-    return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22)", "pr", alg, alg_sectors, t, dev,
-                     _gather_bound(torch, dev, E, t, clocks, tp, tl))
+    src_ordered = order[G.device_src.long()].contiguous()  # the run's renamed sources
+    tp, tl = gather_ceilings(torch, stream, src_ordered, E, ordered)
+    del src_ordered
+    return _roofline("k_pull<PR> dense (PageRank in-edge pass, R-MAT s22, gather order)", "pr", alg, alg_sectors, t,
+                     dev, _gather_bound(torch, dev, E, t, clocks, tp, tl))
 
 
 def _roofline(kernel, key, alg, alg_sectors, t, dev, gather):

@@ -338,7 +338,10 @@ wedge_status wedge_run_sssp(wedge_graph_t g, uint32_t root, uint32_t* d_dist,
  * pr'(v) = (1-d)/V + d * (sum_{u->v} pr(u)/outdeg(u) + D/V), D = rank of
  * vertices with out-degree 0.  FP32 values; in-edge sums are accumulated
  * exactly in 64-bit fixed point (2^-62 units), so results do not depend
- * on the schedule. */
+ * on the schedule.  The pulls gather the contributions in the order of
+ * descending out-degree (built on the graph's first PageRank call: 4E + 4V
+ * bytes, a device radix sort of V keys), so the most gathered ones share
+ * cache lines; results are in the graph's own vertex ids. */
 wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float damping,
                           const wedge_opts* opts, wedge_stats* stats, wedge_stream_t stream);
 /* The in-edge pass of one PageRank iteration on its own (the dense pull of
@@ -348,8 +351,21 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
  * schedule.  d_contrib: V floats (device), finite, >= 0, and small enough
  * that every sum stays below 4.0 (pr(u)/outdeg(u) always is); not checked.
  * d_sums: V uint64 (device), must hold zeros on entry; vertices without
- * in-edges keep 0.  Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+ * in-edges keep 0.  Runs the pull of wedge_run_pr (the contributions are
+ * first copied into its gather order, in library memory that a concurrent
+ * wedge_run_pr on the same graph also uses).  Asynchronous on stream.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY (first call), CUDA. */
 wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums, wedge_stream_t stream);
+/* PageRank's gather order: d_order[v] (device, V uint32) = the position of
+ * vertex v's contribution in the array the pulls gather from (v's rank by
+ * descending out-degree, ties by id; built on first use).  Stream-ordered.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+wedge_status wedge_pr_order(wedge_graph_t g, uint32_t* d_order, wedge_stream_t stream);
+/* wedge_pr_pull on contributions already in the gather order:
+ * d_contrib[d_order[u]] holds u's contribution.  The pull of wedge_run_pr
+ * alone, with no copy; same sums, conditions and errors as wedge_pr_pull. */
+wedge_status wedge_pr_pull_ordered(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums,
+                                   wedge_stream_t stream);
 /* ---- Learned switch (not in the paper) --------------------------------
  * A cost model replaces the fixed fullness threshold and the fixed
  * precision of Section 3.4: before each pull it predicts ln(milliseconds)

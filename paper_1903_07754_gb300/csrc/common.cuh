@@ -153,7 +153,12 @@ struct wedge_graph {
     wedge::RunCtl* ctl = nullptr;
     wedge::RunCtl* h_ctl = nullptr;  // pinned mirror
     // PageRank scratch
-    float* contrib = nullptr;               // pr(u)/outdeg(u)
+    float* contrib = nullptr;               // pr(u)/outdeg(u), at position pr_perm[u]
+    // PageRank's gather order: pr_perm[u] = u's rank by descending
+    // out-degree (ties by id), pr_src[e] = pr_perm[src[e]]; built on the
+    // first PageRank call
+    uint32_t* pr_perm = nullptr;
+    uint32_t* pr_src = nullptr;
     unsigned long long* acc = nullptr;
     float* rank = nullptr;
     uint32_t* split_bm = nullptr;  // destinations whose in-edges cross a pull slice boundary
@@ -270,6 +275,8 @@ wedge_status ensure_run_scratch(wedge_graph* g, cudaStream_t s);
 wedge_status build_eidx_z(wedge_graph* g, cudaStream_t s);
 // The edge index in 8-edge units (graph_build.cu), built once on request.
 wedge_status build_eidx8(wedge_graph* g, cudaStream_t s);
+// PageRank's gather order (relabel.cu), built once on request.
+wedge_status build_pr_order(wedge_graph* g, cudaStream_t s);
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

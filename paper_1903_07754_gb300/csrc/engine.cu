@@ -590,14 +590,15 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
     }
 }
 
-__global__ void k_pr_init(uint32_t V, const uint32_t* __restrict__ outdeg, float* __restrict__ contrib,
-                          unsigned long long* __restrict__ acc, RunCtl* C) {
+// Contributions live in PageRank's gather order: u's at contrib[perm[u]].
+__global__ void k_pr_init(uint32_t V, const uint32_t* __restrict__ outdeg, const uint32_t* __restrict__ perm,
+                          float* __restrict__ contrib, unsigned long long* __restrict__ acc, RunCtl* C) {
     const float pr0 = 1.0f / (float)V;
     unsigned long long dang = 0;
     for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
          v += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t od = outdeg[v];
-        contrib[v] = od ? pr0 / (float)od : 0.0f;
+        contrib[perm[v]] = od ? pr0 / (float)od : 0.0f;
         acc[v] = 0ull;
         if (!od) dang += __float2ull_rn(pr0 * 0x1p62f);
     }
@@ -622,8 +623,9 @@ __device__ __forceinline__ void pr_vertex(unsigned long long a, uint32_t od, flo
 // flight to reach HBM rates).  Sums of destinations split across pull
 // slices are zeroed for the next pull's atomics.
 __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, const uint32_t* __restrict__ split_bm,
-                           unsigned long long* __restrict__ acc, float* __restrict__ contrib,
-                           float* __restrict__ out, RunCtl* C, unsigned t, int last, float base, float d) {
+                           const uint32_t* __restrict__ perm, unsigned long long* __restrict__ acc,
+                           float* __restrict__ contrib, float* __restrict__ out, RunCtl* C, unsigned t, int last,
+                           float base, float d) {
     const float dv = __ull2float_rn(__ldcg(&C->dangling[t & 1])) * 0x1p-62f / (float)V;
     unsigned long long dang = 0;
     const unsigned long long nq = V / 4;
@@ -644,8 +646,15 @@ __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, cons
         pr_vertex(a01.y, od.y, dv, base, d, last, o.y, c.y, dang);
         pr_vertex(a23.x, od.z, dv, base, d, last, o.z, c.z, dang);
         pr_vertex(a23.y, od.w, dv, base, d, last, o.w, c.w, dang);
-        if (last) reinterpret_cast<float4*>(out)[q] = o;
-        else reinterpret_cast<float4*>(contrib)[q] = c;
+        if (last) {
+            reinterpret_cast<float4*>(out)[q] = o;
+        } else {  // into the gather order
+            const uint4 pp = reinterpret_cast<const uint4*>(perm)[q];
+            contrib[pp.x] = c.x;
+            contrib[pp.y] = c.y;
+            contrib[pp.z] = c.z;
+            contrib[pp.w] = c.w;
+        }
     }
     // the tail of V mod 4 vertices
     for (unsigned long long v = 4 * nq + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V; v += stride) {
@@ -654,9 +663,17 @@ __global__ void k_pr_apply(uint32_t V, const uint32_t* __restrict__ outdeg, cons
         float o = 0.f, c = 0.f;
         pr_vertex(a, last ? 0u : outdeg[v], dv, base, d, last, o, c, dang);
         if (last) out[v] = o;
-        else contrib[v] = c;
+        else contrib[perm[v]] = c;
     }
     if (!last) block_add_u64(dang, &C->dangling[(t + 1) & 1]);
+}
+
+// A caller's contributions (by vertex) into PageRank's gather order.
+__global__ void k_pr_scatter(uint32_t V, const uint32_t* __restrict__ perm, const float* __restrict__ in,
+                             float* __restrict__ out) {
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < V;
+         v += (unsigned long long)gridDim.x * blockDim.x)
+        out[perm[v]] = in[v];
 }
 
 __global__ void k_ctl_init(RunCtl* C, RunCtl init) {
@@ -1329,15 +1346,42 @@ static wedge_status msbfs_prepare(wedge_graph* g, uint32_t nroots, bool sssp) {
 static void pr_enqueue(wedge_graph* g, uint32_t iters, float damping, cudaStream_t s) {
     const int vb = g->num_sms * 8;
     PullParams P = pull_params(g, 0, kPR);
+    P.src = g->pr_src;  // sources in the contributions' gather order
     const float base = (1.0f - damping) / (float)g->V;
     for (uint32_t t = 0; t < iters; ++t) {
         P.pr_iter = t;
         launch_pull_app(g, kPR, P, s);
         const int last = (t + 1 == iters);
-        k_pr_apply<<<vb, 256, 0, s>>>(g->V, g->outdeg, g->split_bm, g->acc, g->contrib, g->rank, g->ctl, t, last, base,
-                                      damping);
+        k_pr_apply<<<vb, 256, 0, s>>>(g->V, g->outdeg, g->split_bm, g->pr_perm, g->acc, g->contrib, g->rank, g->ctl,
+                                      t, last, base, damping);
         count_launch();
     }
+}
+
+// PageRank's dense pull as a run executes it, on contributions already in
+// the gather order (`ordered`), else first copied there from the caller's
+// by-vertex array.  A dense pull at iteration 0; the caller's zeros take
+// the place of the vertex step that clears split destinations between
+// iterations.
+static wedge_status pr_pull(wedge_graph* g, const float* d_contrib, uint64_t* d_sums, bool ordered, cudaStream_t s) {
+    if (!g || !d_contrib || !d_sums) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(g->device);
+    WEDGE_TRY(build_pr_order(g, s));
+    k_standalone_prep<<<1, 32, 0, s>>>(g->rec, g->ctl, 0, 0, 0, nullptr, 0);
+    count_launch();
+    if (!ordered) {
+        k_pr_scatter<<<g->num_sms * 8, 256, 0, s>>>(g->V, g->pr_perm, d_contrib, g->contrib);
+        count_launch();
+    }
+    PullParams P = pull_params(g, 0, kPR);
+    P.src = g->pr_src;
+    P.contrib = ordered ? d_contrib : g->contrib;
+    P.acc = reinterpret_cast<unsigned long long*>(d_sums);
+    P.pr_iter = 0;
+    launch_pull_app(g, kPR, P, s);
+    WEDGE_TRY_CUDA(cudaGetLastError());
+    g->last_stream = s;
+    return WEDGE_OK;
 }
 
 }  // namespace wedge
@@ -1373,12 +1417,13 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t V = g->V;
+    WEDGE_TRY(build_pr_order(g, s));
     WEDGE_TRY_CUDA(cudaEventRecord(g->ev0, s));
     RunCtl init{};
     init.max_iters = 0xFFFFFFFFu;
     WEDGE_TRY_CUDA(cudaMemsetAsync(g->rec, 0, 2 * sizeof(IterRec), s));
     k_ctl_init<<<1, 32, 0, s>>>(g->ctl, init);
-    k_pr_init<<<g->num_sms * 8, 256, 0, s>>>(V, g->outdeg, g->contrib, g->acc, g->ctl);
+    k_pr_init<<<g->num_sms * 8, 256, 0, s>>>(V, g->outdeg, g->pr_perm, g->contrib, g->acc, g->ctl);
     count_launch(2);
     if (iters == 0) {
         std::vector<float> h(V, 1.0f / (float)V);
@@ -1429,19 +1474,21 @@ wedge_status wedge_run_pr(wedge_graph_t g, float* d_rank, uint32_t iters, float 
 }
 
 wedge_status wedge_pr_pull(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums, wedge_stream_t stream) {
-    if (!g || !d_contrib || !d_sums) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    return pr_pull(g, d_contrib, d_sums, false, (cudaStream_t)stream);
+}
+
+wedge_status wedge_pr_pull_ordered(wedge_graph_t g, const float* d_contrib, uint64_t* d_sums,
+                                   wedge_stream_t stream) {
+    return pr_pull(g, d_contrib, d_sums, true, (cudaStream_t)stream);
+}
+
+wedge_status wedge_pr_order(wedge_graph_t g, uint32_t* d_order, wedge_stream_t stream) {
+    if (!g || !d_order) return set_error(WEDGE_ERR_INVALID_ARG, "NULL argument");
+    if (classify(d_order) != PtrKind::Device) return set_error(WEDGE_ERR_INVALID_ARG, "d_order must be device memory");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
-    // a dense pull at iteration 0; the caller's zeros take the place of the
-    // vertex step that clears split destinations between iterations
-    k_standalone_prep<<<1, 32, 0, s>>>(g->rec, g->ctl, 0, 0, 0, nullptr, 0);
-    PullParams P = pull_params(g, 0, kPR);
-    P.contrib = d_contrib;
-    P.acc = reinterpret_cast<unsigned long long*>(d_sums);
-    P.pr_iter = 0;
-    launch_pull_app(g, kPR, P, s);
-    count_launch();
-    WEDGE_TRY_CUDA(cudaGetLastError());
+    WEDGE_TRY(build_pr_order(g, s));
+    WEDGE_TRY_CUDA(cudaMemcpyAsync(d_order, g->pr_perm, (uint64_t)g->V * 4, cudaMemcpyDeviceToDevice, s));
     g->last_stream = s;
     return WEDGE_OK;
 }

@@ -366,6 +366,8 @@ static void free_graph(wedge_graph* g) {
     dev_free(g->ctl);
     pinned_small_free(g->h_ctl);
     dev_free(g->contrib);
+    dev_free(g->pr_perm);
+    dev_free(g->pr_src);
     dev_free(g->acc);
     dev_free(g->rank);
     dev_free(g->split_bm);

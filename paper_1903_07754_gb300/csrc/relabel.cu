@@ -20,6 +20,7 @@ wedge_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tkeys, u
 namespace {
 
 constexpr unsigned kPieceEdges = 1024;  // in-edges copied by one warp task
+constexpr uint32_t kPrHubDegree = 1;     // PageRank's order ranks vertices of at least this out-degree
 
 unsigned grid_of(uint64_t n, int threads, int sms) {
     const uint64_t b = (n + threads - 1) / threads;
@@ -170,7 +171,88 @@ bool all_device(std::initializer_list<const void*> ps) {
     return true;
 }
 
+// PageRank's ranking keys: vertices of out-degree >= dmin first, by
+// descending out-degree; all others after them in id order (one shared
+// key, the sort is stable).
+__global__ void k_rl_hub_keys(const uint32_t* __restrict__ deg, uint32_t V, uint32_t kmax, uint32_t dmin,
+                              uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t dg = deg[v];
+        key[v] = dg >= dmin ? kmax - dg : kmax;
+        val[v] = (uint32_t)v;
+    }
+}
+
+// pr_src[e] = perm[src[e]], 16-byte loads and stores (tail by words).
+__global__ void k_rl_rename(const uint32_t* __restrict__ src, uint64_t E, const uint32_t* __restrict__ perm,
+                            uint32_t* __restrict__ out) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = E / 4;
+    for (uint64_t q = tid; q < n4; q += nth) {
+        const uint4 s = reinterpret_cast<const uint4*>(src)[q];
+        reinterpret_cast<uint4*>(out)[q] = make_uint4(__ldg(perm + s.x), __ldg(perm + s.y), __ldg(perm + s.z),
+                                                      __ldg(perm + s.w));
+    }
+    for (uint64_t p = 4 * n4 + tid; p < E; p += nth) out[p] = __ldg(perm + src[p]);
+}
+
+// perm[old_of_new[i]] = i
+__global__ void k_rl_invert(const uint32_t* __restrict__ old_of_new, uint32_t V, uint32_t* __restrict__ perm) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < V; i += (uint64_t)gridDim.x * blockDim.x)
+        perm[old_of_new[i]] = (uint32_t)i;
+}
+
 }  // namespace
+
+// PageRank gathers one contribution per in-edge, indexed by the source;
+// stored in the order of descending out-degree (the ranking the relabelling
+// above gives), the most gathered contributions share cache lines.  Only
+// the gathers move: destinations, the chunk metadata and every result stay
+// in the graph's own ids, and the sums are the same exact fixed-point sums.
+wedge_status build_pr_order(wedge_graph* g, cudaStream_t s) {
+    if (g->pr_src) return WEDGE_OK;
+    const uint32_t V = g->V;
+    const uint64_t E = g->E;
+    const int sms = g->num_sms;
+    uint32_t* perm = nullptr;
+    uint32_t* psrc = nullptr;
+    WEDGE_TRY(dev_alloc(g, (void**)&perm, (uint64_t)V * 4));
+    wedge_status st = dev_alloc(g, (void**)&psrc, (E ? E : 4) * 4);
+    if (st != WEDGE_OK) {
+        dev_free(perm);
+        return st;
+    }
+    Scratch sc(s);
+    for (int i = 0; i < 4 && st == WEDGE_OK; ++i) st = dev_alloc(nullptr, &sc.p[i], (uint64_t)V * 4);
+    if (st == WEDGE_OK) {
+        uint32_t *key = (uint32_t*)sc.p[0], *val = (uint32_t*)sc.p[1], *tkey = (uint32_t*)sc.p[2],
+                 *tval = (uint32_t*)sc.p[3];
+        int bits = 0;
+        while (bits < 32 && (E >> bits)) ++bits;
+        const uint32_t kmax = bits >= 32 ? 0xFFFFFFFFu : (uint32_t)((1ull << bits) - 1);
+        k_rl_hub_keys<<<grid_of(V, 256, sms), 256, 0, s>>>(g->outdeg, V, kmax, kPrHubDegree, key, val);
+        count_launch();
+        bool in_tmp = false;
+        st = radix_sort_pairs(key, val, tkey, tval, V, bits, sms, s, &in_tmp);
+        if (st == WEDGE_OK) {
+            k_rl_invert<<<grid_of(V, 256, sms), 256, 0, s>>>(in_tmp ? tval : val, V, perm);
+            if (E) k_rl_rename<<<grid_of((E + 3) / 4, 256, sms), 256, 0, s>>>(g->src, E, perm, psrc);
+            count_launch(2);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = cuda_error(e, "PageRank gather order");
+        }
+    }
+    if (st != WEDGE_OK) {
+        dev_free(perm);
+        dev_free(psrc);
+        return st;
+    }
+    g->pr_perm = perm;
+    g->pr_src = psrc;
+    return WEDGE_OK;
+}
+
 }  // namespace wedge
 
 using namespace wedge;

@@ -73,6 +73,7 @@ EXPORTS = [
     "wedge_pr_pull", "wedge_trim_memory", "wedge_selftest_timeout", "wedge_run_sssp_batch",
     "wedge_frontier_transform_profile", "wedge_graph_copy_edge_index_z", "wedge_set_learned_band",
     "wedge_csc_relabel_by_degree", "wedge_permute_rows", "wedge_cc_labels_to_original", "wedge_run_bfs_batch_u8",
+    "wedge_pr_order", "wedge_pr_pull_ordered",
 ]
 MLP_FEATURES, MLP_PARAMS, MLP_CANDIDATES = 12, 5057, 6
 
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH):
         "wedge_run_cc": (st, [P, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_run_sssp": (st, [P, u32, P, ctypes.POINTER(wedge_opts), ctypes.POINTER(wedge_stats), P]),
         "wedge_pr_pull": (st, [P, P, P, P]),
+        "wedge_pr_pull_ordered": (st, [P, P, P, P]),
+        "wedge_pr_order": (st, [P, P, P]),
         "wedge_trim_memory": (st, [i32]),
         "wedge_csc_relabel_by_degree": (st, [u32, u64, P, P, P, P, P, P, P, P, P]),
         "wedge_permute_rows": (st, [u32, u32, P, P, P, P]),
@@ -308,6 +311,17 @@ def wedge_pr_pull(handle, contrib, sums, stream=None):
     """One PageRank in-edge pass: sums (int64 view of uint64, zeroed by the
     caller) = exact 2^-62 fixed-point in-edge sums of contrib (float32)."""
     _check(load().wedge_pr_pull(handle, _ptr(contrib), _ptr(sums), _stream(stream)))
+
+
+def wedge_pr_order(handle, order, stream=None):
+    """order (int32 device tensor of V): the position of each vertex's
+    contribution in PageRank's gather order."""
+    _check(load().wedge_pr_order(handle, _ptr(order), _stream(stream)))
+
+
+def wedge_pr_pull_ordered(handle, contrib, sums, stream=None):
+    """wedge_pr_pull on contributions already in the gather order."""
+    _check(load().wedge_pr_pull_ordered(handle, _ptr(contrib), _ptr(sums), _stream(stream)))
 
 
 def wedge_get_trace(handle, cap=1 << 16):

@@ -269,6 +269,29 @@ def test_pr_pull_in_sums(rmat, rmat_dev, sym, sym_dev, which):
     assert torch.equal(sums, again)
 
 
+@pytest.mark.parametrize("which", ["rmat", "sym"])
+def test_pr_gather_order(rmat, rmat_dev, sym, sym_dev, which):
+    """PageRank gathers contributions stored by rank of descending
+    out-degree (ties by id): the exported order is that ranking, and the
+    pull on contributions placed by it gives the by-vertex pull's exact
+    sums."""
+    g, G = (rmat, rmat_dev) if which == "rmat" else (sym, sym_dev)
+    order = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    wedge.wedge_pr_order(G.handle, order)
+    got = order.cpu().numpy().astype(np.int64)
+    rank = np.empty(g.V, dtype=np.int64)
+    rank[np.argsort(-g.outdeg().astype(np.int64), kind="stable")] = np.arange(g.V)
+    np.testing.assert_array_equal(got, rank)
+    x = (np.random.default_rng(8).random(g.V) / g.V).astype(np.float32)
+    xo = np.empty_like(x)
+    xo[got] = x
+    a = torch.zeros(g.V, dtype=torch.int64, device="cuda")
+    b = torch.zeros_like(a)
+    wedge.wedge_pr_pull(G.handle, torch.from_numpy(x).cuda(), a)
+    wedge.wedge_pr_pull_ordered(G.handle, torch.from_numpy(xo).cuda(), b)
+    assert torch.equal(a, b)
+
+
 def test_pull_iterate_bfs_step(rmat, rmat_dev):
     """One BFS iteration from the oracle's level-t state, dense and over the
     Wedge Frontier, yields exactly the level-(t+1) set."""
