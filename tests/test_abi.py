@@ -131,3 +131,25 @@ def test_default_opts_leave_the_extensions_off(lib):
         o = wedge.wedge_default_opts(app)
         assert (o.synchronous, o.sparse_push, o.trace, o.max_iters) == (0, 0, 0, 0)
         assert list(o.reserved) == [0]
+
+
+def test_argument_checks_before_any_device_work(lib):
+    """Malformed calls are rejected on the host with INVALID_ARG and a
+    message, before any CUDA call (so these run without a GPU)."""
+    L = lib
+    cases = [
+        (lambda: L.wedge_csc_relabel_by_degree(0, 0, None, None, None, None, None, None, None, None, None), "V must be"),
+        (lambda: L.wedge_csc_relabel_by_degree(4, 1 << 40, None, None, None, None, None, None, None, None, None),
+         "E must be"),
+        (lambda: L.wedge_permute_rows(0, 1, None, None, None, None), "V and width"),
+        (lambda: L.wedge_permute_rows(4, 0, None, None, None, None), "V and width"),
+        (lambda: L.wedge_cc_labels_to_original(0, None, None, None, None, None), "V must be"),
+        (lambda: L.wedge_pr_order(None, None, None), "NULL"),
+        (lambda: L.wedge_pr_pull_ordered(None, None, None, None), "NULL"),
+        (lambda: L.wedge_run_bfs_batch_u8(None, None, None, 1, 1, None, None, None, None), "NULL"),
+        (lambda: L.wedge_graph_create(0, 0, None, None, None, None, None, 32, None, None), "out is NULL"),
+    ]
+    for call, text in cases:
+        st = call()
+        assert st == 1, (text, st)  # WEDGE_ERR_INVALID_ARG
+        assert text in wedge.wedge_last_error(), (text, wedge.wedge_last_error())
